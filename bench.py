@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the SSP-RK3 / convex-limiting Euler stage on one GB300.
+
+Workload (default): Mach 3 forward-facing step channel [0,3]x[0,1]x[0,0.5],
+step x >= 0.6, y <= 0.2, Q1 hexahedra with h = 1/120 (2,242,909 nodes, 27-point
+stencil), interior nodes jittered by U[-0.2h, 0.2h] (seed 2007), inflow
+rho = 1.4, p = 1, u = (3,0,0), slip walls; FP64 throughout.  One benchmark
+step is one SSP-RK3 time step = three euler_steps (Alg. 1 + eq. ssprk3) over
+every node; the metric is node-stage updates per second (nodes x 3 stages /
+time).  The inputs (matrices and state, ~7 GB) are larger than L2.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own replica
+of the workload (the stage does not shard without a halo exchange, which this
+build does not have); value = all ranks' node-stage updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D Q1 node-stage updates/s & HBM GB/s: FP64 plain vs FP32-mixed/batched/adjoint"
+UNIT = "node-stage updates/s"
+
+# Algorithmic FP64 flops per stored matrix entry (nnz) of each step of Alg. 1
+# as counted for the paper's implementation (Table 3; pow and division counted
+# by their flops).  Step 5 is the limiter pass, step 6 the final update.
+FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "flux_limit": 183.0,
+                "limiter_pass": 155.0, "final": 12.0}
+# FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
+# FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s; a dependent-free DFMA
+# stream measured 1.197 TFLOP/s at 1.97 GHz on this machine).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by kernel; None until captured for the current kernel source.
+NCU_TRAFFIC_BYTES = {}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ["pci.bus_id", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv"), "w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(", ") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        if self.bus_id:
+            mine = [r for r in rows if r and r[0].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for q, name in enumerate(names):
+                if r[5 + q].strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_sample(cpu_m):
+    """The bounded CPU sample of the workload: the same channel, inflow state,
+    boundary conditions and jitter at h = 1/cpu_m, assembled by the oracle."""
+    import oracle as O
+    from paper_2007_00094_gb300 import workloads as W
+
+    O.build()
+    mesh = W.forward_step_mesh(m=cpu_m, jitter=0.2, seed=2007)
+    t0 = time.perf_counter()
+    om = O.assemble(mesh)
+    return mesh, om, W.forward_step_state(mesh), time.perf_counter() - t0
+
+
+def cpu_baseline(cpu_m, seconds_budget=20.0):
+    """The FP64 oracle, as it stands, on the host cores (OpenMP over rows, all
+    cores): euler_steps on the sample mesh until about seconds_budget."""
+    import oracle as O
+
+    mesh, om, U, t_asm = _oracle_sample(cpu_m)
+    cores = os.cpu_count() or 1
+    prm = O.default_params(n_threads=cores)
+    stages, elapsed, V = 0, 0.0, U
+    while elapsed < seconds_budget and stages < 12:
+        t0 = time.perf_counter()
+        V, tau, st, _ = O.euler_step(om, V, params=prm)
+        elapsed += time.perf_counter() - t0
+        stages += 1
+        if st != 0:
+            break
+    value = mesh.n_nodes * stages / elapsed
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{stages} euler_steps of the FP64 oracle on the same channel at h = 1/{cpu_m} "
+                      f"({mesh.n_nodes} nodes), {elapsed:.1f} s; oracle assembly {t_asm:.1f} s untimed"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores;
+    each step is one euler_step over the sample mesh of the workload."""
+    import oracle as O
+
+    mesh, om, U, _ = _oracle_sample(args.cpu_m)
+    cores = os.cpu_count() or 1
+    prm = O.default_params(n_threads=cores)
+    V = U
+    for _ in range(args.warmup):
+        V, _, _, _ = O.euler_step(om, V, params=prm)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        V, _, st, _ = O.euler_step(om, V, params=prm)
+    dt = time.perf_counter() - t0
+    value = mesh.n_nodes * args.steps / dt
+    sample = (f"each step = one euler_step of the FP64 oracle on the same channel at h = 1/{args.cpu_m} "
+              f"({mesh.n_nodes} nodes)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args.m, _channel_nodes(args.m), None, args),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT, "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _channel_nodes(m):
+    nz = m // 2 + 1
+    return (3 * m + 1) * (m + 1) * nz - (3 * m - (6 * m) // 10) * ((2 * m) // 10) * nz
+
+
+def _config(m, nodes, nnz, args):
+    return {"workload": f"mach3_forward_facing_step_h1/{m}_jitter0.2_seed2007", "nodes": nodes,
+            "nnz": nnz, "stencil": "Q1 27-point", "step": "one SSP-RK3 step = 3 euler_steps",
+            "limiter_passes": 2, "newton_steps": 2, "cfl": 0.5,
+            "l2": "inputs larger than L2 (matrices and state resident in HBM, ~7 GB)",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=120, help="cells per unit length of the channel mesh")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-m", type=int, default=60, help="mesh of the CPU oracle sample (h = 1/cpu_m)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    ws, rank, local = _dist()
+    from paper_2007_00094_gb300 import workloads as W
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2007_00094_gb300 import build
+    from paper_2007_00094_gb300.idp import Solver
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    mesh = W.forward_step_mesh(m=args.m, jitter=0.2, seed=2007)
+    U0 = W.forward_step_state(mesh)
+    stream = torch.cuda.current_stream()
+    s = Solver(mesh, stream=stream)
+    s.init_state(U0)
+    N, nnz = mesh.n_nodes, s.nnz
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    s.step(args.warmup)
+    s.synchronize()
+
+    # timed region: K SSP-RK3 steps with inputs resident in HBM
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except AttributeError:
+        pass
+    sampler = ClockSampler(bus_id=str(bus) if bus is not None else None)
+    s.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    if rank == 0:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    s.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read()
+    s.profile(False)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ws * N * 3 * args.steps / (ms_max * 1e-3)
+    launches = sum(c for _, c in prof.values())
+
+    # end-to-end through the public API with host buffers: every step copies
+    # the state in from pinned host memory and the new state back out
+    host_in = torch.from_numpy(U0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    s.init_state(host_in.numpy())
+    s.step(1)
+    s.get_state(host_out.numpy())
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.init_state(host_in.numpy())
+        s.step(1)
+        s.get_state(host_out.numpy())
+        host_in, host_out = host_out, host_in
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * N * 3 * args.e2e_steps / float(e2e_t.item())
+    state_bytes = 5 * N * 8
+
+    if rank == 0:
+        dom = max(prof, key=lambda k: prof[k][0])
+        dom_ms, dom_n = prof[dom]
+        per_launch_s = dom_ms / dom_n * 1e-3
+        achieved = FLOP_PER_NNZ[dom] * nnz / per_launch_s / 1e12
+        traffic = NCU_TRAFFIC_BYTES.get(dom)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args.m, N, nnz, args),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "FP64 pipe from unit counts and max clock (nominal 1.25 TFLOP/s)",
+                         "work": f"{FLOP_PER_NNZ[dom]:.0f} flop/nnz x {nnz} nnz per launch"},
+            "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
+            "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items()},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

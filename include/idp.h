@@ -1,0 +1,183 @@
+/*
+ * libidp: GPU (sm_103a) explicit stage of the invariant-domain preserving,
+ * second-order Q1 finite-element scheme for the compressible Euler equations
+ * with convex limiting, after Maier & Kronbichler, "Efficient parallel 3D
+ * computation of the compressible Euler equations with an invariant-domain
+ * preserving second-order finite-element scheme" (arXiv:2007.00094).
+ *
+ * One context owns one mesh, its precomputed matrices (Sec. 3.2) and all
+ * device buffers of the stage; every call returns an idp_status and no C++
+ * exception crosses this boundary.  Work is enqueued on the stream given to
+ * idp_create (NULL = the legacy default stream); calls that hand data back to
+ * the host synchronise that stream, the others do not.
+ *
+ * Conventions for every call:
+ *  - Conserved states are struct-of-arrays of float64, U[f*n + i] for the
+ *    fields f = 0..4 = (rho, m_x, m_y, m_z, E) (Sec. 2), in the caller's node
+ *    order.  The library may renumber nodes internally and always translates.
+ *  - "on_device = 0": pointers are host memory owned by the caller and only
+ *    read/written during the call.  "on_device = 1": pointers are device
+ *    memory of the context's GPU (e.g. torch tensors), borrowed for the call
+ *    and accessed in stream order on the context's stream.
+ *  - Sizes are element counts, not bytes.
+ */
+#ifndef IDP_H
+#define IDP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idp_ctx idp_ctx;
+
+typedef enum {
+  IDP_OK = 0,
+  IDP_ERR_ARG = 1,                  /* invalid argument or mesh */
+  IDP_ERR_CUDA = 2,                 /* a CUDA runtime call failed (see idp_last_error) */
+  IDP_ERR_OOM = 3,                  /* device or host allocation failed */
+  IDP_ERR_STATE_NOT_ADMISSIBLE = 4, /* rho <= 0 or epsilon <= 0 somewhere (Sec. 3.3) */
+  IDP_ERR_CFL = 5,                  /* tau of RK stage 1 exceeds min_i m_i/(-2 d_ii) of a later stage */
+  IDP_ERR_NONFINITE = 6,            /* a NaN or Inf appeared in the state */
+  IDP_ERR_BOUNDS = 7,               /* idp_check_bounds found a violated invariant */
+  IDP_ERR_TIMEOUT = 8,              /* a bounded device wait gave up */
+  IDP_ERR_STATE = 9                 /* call out of order (e.g. step before mesh and state) */
+} idp_status;
+
+enum { IDP_PRECISION_FP64 = 0, IDP_PRECISION_MIXED = 1 };
+
+/* Solver parameters (Sec. 3, Alg. 1-3). */
+typedef struct {
+  double gamma;             /* ratio of specific heats; the kernels require 7/5 (Sec. 2) */
+  double cfl;               /* c_cfl in (0, 1] of the time-step rule (Sec. 3.3) */
+  int limiter_passes;       /* passes of eq. (iterative-limiter), >= 2 (Sec. 3.5) */
+  int newton_max;           /* Newton steps of Alg. 2 */
+  double newton_tol;        /* Alg. 2 stops when Psi(t_L) <= newton_tol * rho*eps(U) */
+  double newton_eps;        /* eps of Alg. 3 */
+  int precision;            /* IDP_PRECISION_FP64 */
+  int schedule;             /* kernel schedule id; 0 = default */
+  int64_t barrier_spin_limit; /* iteration limit of any device-side wait */
+} idp_config;
+
+/* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,
+ * newton_tol 1e-10, newton_eps = DBL_EPSILON, FP64, schedule 0. */
+void idp_config_default(idp_config* cfg);
+
+/* Creates a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (may be NULL).  *out receives the context; the caller releases
+ * it with idp_destroy.  Fails with IDP_ERR_ARG for a gamma other than 7/5,
+ * cfl outside (0,1] or limiter_passes < 1. */
+idp_status idp_create(const idp_config* cfg, void* cuda_stream, idp_ctx** out);
+void idp_destroy(idp_ctx* ctx);
+const char* idp_last_error(const idp_ctx* ctx);
+const char* idp_status_string(idp_status s);
+
+/* Uploads a hexahedral Q1 mesh and precomputes the matrices of Sec. 3.1
+ * eq. (matrices): m_ij, m_i and c_ij, by exact Gauss quadrature on each
+ * trilinear cell; n_ij and b_ij are formed on the fly (Sec. 3.2).
+ *   n_nodes, n_cells : sizes
+ *   cells            : host, 8*n_cells node ids, local vertex v = a + 2b + 4c
+ *                      at reference corner (a, b, c) in {0,1}^3
+ *   cell_xyz         : host, 24*n_cells vertex positions seen from each cell
+ *                      (unwrapped across periodic seams); every cell must have
+ *                      a positive Jacobian at its Gauss points (else IDP_ERR_ARG)
+ *   node_bc          : host, n_nodes flags or NULL: bits 1, 2, 4 = slip wall
+ *                      with an x-, y-, z-normal face; 8 = inflow (Dirichlet)
+ *   inflow_state     : host, 5 conserved values used at inflow nodes, or NULL
+ * Set-up work runs on the host and is not part of a stage. */
+idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                               const double* cell_xyz, const int32_t* node_bc, const double* inflow_state);
+
+/* Number of nodes and of stored matrix entries (the stencil sizes I(i) of
+ * Sec. 3.1 summed over i). */
+idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz);
+
+/* Copies the assembled matrices back in the caller's numbering as CSR with
+ * columns sorted by the caller's node id: rowptr (n+1), col (nnz), mij (nnz),
+ * cij (3*nnz, component-major), mi (n).  Host pointers; any may be NULL. */
+idp_status idp_get_matrices(idp_ctx* ctx, int64_t* rowptr, int64_t* col, double* mij, double* cij, double* mi);
+
+/* Sets the current state U^n (5*n values).  Rejects states with rho <= 0 or
+ * epsilon <= 0 (Sec. 3.3, admissible snapshots) with
+ * IDP_ERR_STATE_NOT_ADMISSIBLE; synchronises the stream. */
+idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device);
+
+/* Copies the current state out (5*n values); synchronises the stream. */
+idp_status idp_get_state(idp_ctx* ctx, double* U, int on_device);
+
+/* Enqueues n_steps SSP-RK3 steps (Sec. 3.5 eq. ssprk3), each three
+ * euler_steps (Alg. 1) with tau_n fixed by the first one.  Returns without
+ * waiting for the GPU; device-side errors (CFL, non-finite) are latched and
+ * returned by idp_synchronize.  A step that meets a CFL violation leaves the
+ * state at its beginning and every later step of the same call is skipped. */
+idp_status idp_step(idp_ctx* ctx, int n_steps);
+
+/* One euler_step (Alg. 1 plus boundary post-processing) applied to the
+ * current state in place, U <- E(U).  tau <= 0: tau_n is computed from the
+ * CFL rule; tau > 0: tau is used and checked against min_i m_i/(-2 d_ii).
+ * With trace != 0 the intermediate fields of this stage are kept for
+ * idp_get_field.  Synchronises and returns the stage's status. */
+idp_status idp_euler_step(idp_ctx* ctx, double tau, int trace, double* tau_out);
+
+/* Waits for the context's stream and returns (then clears) the latched
+ * device status. */
+idp_status idp_synchronize(idp_ctx* ctx);
+
+/* Simulated time accumulated by idp_step and the last tau_n; synchronises. */
+idp_status idp_get_time(idp_ctx* ctx, double* t, double* last_tau);
+idp_status idp_set_time(idp_ctx* ctx, double t);
+
+/* Intermediate fields of the last traced euler_step, in caller order. */
+enum {
+  IDP_FIELD_D = 0,      /* d^L_ij, nnz CSR (diagonal = d_ii) */
+  IDP_FIELD_ALPHA = 1,  /* alpha_i, n */
+  IDP_FIELD_UL = 2,     /* low-order update, 5n */
+  IDP_FIELD_R = 3,      /* R_i, 5n */
+  IDP_FIELD_BOUNDS = 4, /* rho_min, rho_max, phi_min: 3n */
+  IDP_FIELD_P = 5,      /* P_ij of Step 4, 5*nnz field-major */
+  IDP_FIELD_L4 = 6,     /* limiter values of Step 4, nnz */
+  IDP_FIELD_U5 = 7,     /* state after limiter pass 1, 5n */
+  IDP_FIELD_L5 = 8,     /* limiter values recomputed in pass 1, nnz */
+  IDP_FIELD_ULIM = 9,   /* state after the last pass, before boundary conditions, 5n */
+  IDP_FIELD_TAU_MAX = 10 /* min_i m_i/(-2 d_ii): 1 value */
+};
+idp_status idp_get_field(idp_ctx* ctx, int which, double* out);
+
+/* Invariant check of the current state (Sec. 3.3, Sec. 3.8): counts nodes
+ * with rho <= 0, epsilon <= 0 or a non-finite value.  Synchronises.  Returns
+ * IDP_ERR_BOUNDS when any count is non-zero. */
+typedef struct {
+  int64_t n_rho_nonpositive;
+  int64_t n_eps_nonpositive;
+  int64_t n_nonfinite;
+  double rho_min;
+  double eps_min;
+} idp_bounds_report;
+idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out);
+
+/* Number of kernel launches the last idp_step/idp_euler_step enqueued. */
+int64_t idp_launch_count(const idp_ctx* ctx);
+
+/* Per-kernel timing for benchmarks.  idp_profile(ctx, 1) synchronises the
+ * stream, clears earlier records and from then on records a CUDA event pair
+ * on the context's stream around every kernel launch (Alg. 1 steps 0-6);
+ * idp_profile(ctx, 0) stops recording.  idp_profile_read synchronises and
+ * writes, per kernel id, the summed event time in milliseconds and the
+ * launch count since recording started (arrays of IDP_N_KERNELS). */
+enum {
+  IDP_KERNEL_NODE = 0,        /* Step 0: per-node quantities */
+  IDP_KERNEL_EDGE = 1,        /* Step 1: d_ij and alpha_i */
+  IDP_KERNEL_DIAG = 2,        /* Step 2: d_ii and tau */
+  IDP_KERNEL_LOW_ORDER = 3,   /* Step 3: low-order update, R_i, bounds */
+  IDP_KERNEL_FLUX_LIMIT = 4,  /* Step 4: P_ij and l_ij */
+  IDP_KERNEL_LIMITER_PASS = 5,/* Step 5: limiter pass with new l_ij */
+  IDP_KERNEL_FINAL = 6,       /* Step 6: last pass, boundary values, RK blend */
+  IDP_N_KERNELS = 7
+};
+idp_status idp_profile(idp_ctx* ctx, int enable);
+idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -294,6 +294,17 @@ static double dpsi_dt(const double* V, const double* P, double phi_min, double g
   return drho_eps - phi_min * (gamma + 1.0) * pow(V[0], gamma) * P[0];
 }
 
+/* Psi(V) >= 0 up to a relative margin of 1e-13 of its two terms: they
+ * nearly cancel where phi is close to phi_min (isentropic flow), so the sign
+ * of a Psi that small is decided by rounding.  The margin sits well above the
+ * rounding error (~1e-15) so the decision does not depend on it, and well
+ * below the tolerance of the invariant checks (Reading A10). */
+static int psi_admissible(const double* V, double phi_min, double gamma) {
+  const double rho_eps = V[0] * V[4] - 0.5 * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+  const double slack = 1e-13 * (fabs(rho_eps) + fabs(phi_min * pow(V[0], gamma + 1.0)));
+  return orc_psi(V, phi_min, gamma) >= -slack;
+}
+
 static void axpy_state(const double* U, double t, const double* P, double* out) {
   for (int f = 0; f < NF; ++f) out[f] = U[f] + t * P[f];
 }
@@ -340,7 +351,7 @@ double orc_limiter(const double* U, const double* P, double rho_min, double rho_
   for (int step = 0; step < prm->newton_max; ++step) {
     axpy_state(U, tR, P, V);
     const double PsiR = orc_psi(V, phi_min, gamma);
-    if (PsiR >= 0.0) { /* t_R is admissible: close the interval */
+    if (psi_admissible(V, phi_min, gamma)) { /* t_R is admissible: close the interval */
       tL = tR;
       break;
     }
@@ -353,10 +364,11 @@ double orc_limiter(const double* U, const double* P, double rho_min, double rho_
     double nL = tL, nR = tR;
     quadratic_newton_step(&nL, &nR, PsiL, PsiR, dPsiL, dPsiR, -1.0, prm->newton_eps);
     /* keep t_L admissible and the bracket ordered (Reading A10): the new
-     * left end is checked before it bounds the new right end */
+     * left end is checked before it bounds the new right end (a step that
+     * lands on the root within rounding must not fall back to the old t_L) */
     nL = clamp(nL, tL, tR);
     axpy_state(U, nL, P, V);
-    if (orc_psi(V, phi_min, gamma) < 0.0) nL = tL;
+    if (!psi_admissible(V, phi_min, gamma)) nL = tL;
     nR = clamp(nR, nL, tR);
     tL = nL;
     tR = nR;

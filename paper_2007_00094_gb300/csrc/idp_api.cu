@@ -1,0 +1,415 @@
+// C ABI of libidp (include/idp.h): context, uploads, stepping, read-back.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "idp.h"
+#include "idp_internal.h"
+#include "idp_stage.cuh"
+
+struct idp_ctx {
+  idp_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool has_mesh = false, has_state = false, has_trace = false;
+  idp::HostMatrices M;
+  idp::SellLayout L;
+  idp::DeviceGraph G{};
+  idp::StageBuffers B{};
+  idp::StageConfig C{};
+  std::vector<void*> allocations;
+  double* check = nullptr;  // 5 doubles
+  int64_t launches = 0;
+  idp::Profiler prof;
+};
+
+namespace {
+
+idp_status fail(idp_ctx* ctx, idp_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define IDP_CUDA(ctx, expr)                                                                     \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess) return fail(ctx, IDP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+idp_status dalloc(idp_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, IDP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->allocations.push_back(q);
+  *p = static_cast<T*>(q);
+  return IDP_OK;
+}
+
+template <typename T>
+idp_status upload(idp_ctx* ctx, T** p, const std::vector<T>& v) {
+  idp_status st = dalloc(ctx, p, v.size());
+  if (st != IDP_OK) return st;
+  IDP_CUDA(ctx, cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return IDP_OK;
+}
+
+void free_all(idp_ctx* ctx) {
+  for (void* p : ctx->allocations) cudaFree(p);
+  ctx->allocations.clear();
+}
+
+idp_status device_status(idp_ctx* ctx, bool clear) {
+  int st = 0;
+  IDP_CUDA(ctx, cudaMemcpyAsync(&st, &ctx->B.scal->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (clear && st) IDP_CUDA(ctx, cudaMemsetAsync(&ctx->B.scal->status, 0, sizeof(int), ctx->stream));
+  if (st & idp::kStatusNotAdmissible) return fail(ctx, IDP_ERR_STATE_NOT_ADMISSIBLE, "state not admissible");
+  if (st & idp::kStatusCfl) return fail(ctx, IDP_ERR_CFL, "tau of the first RK stage violates the CFL bound of a later stage");
+  if (st & idp::kStatusNonFinite) return fail(ctx, IDP_ERR_NONFINITE, "non-finite value in the state");
+  if (st & idp::kStatusTimeout) return fail(ctx, IDP_ERR_TIMEOUT, "device wait timed out");
+  return IDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void idp_config_default(idp_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->gamma = 1.4;
+  cfg->cfl = 0.5;
+  cfg->limiter_passes = 2;
+  cfg->newton_max = 2;
+  cfg->newton_tol = 1e-10;
+  cfg->newton_eps = DBL_EPSILON;
+  cfg->precision = IDP_PRECISION_FP64;
+  cfg->schedule = 0;
+  cfg->barrier_spin_limit = 1 << 26;
+}
+
+const char* idp_status_string(idp_status s) {
+  switch (s) {
+    case IDP_OK: return "ok";
+    case IDP_ERR_ARG: return "invalid argument";
+    case IDP_ERR_CUDA: return "CUDA error";
+    case IDP_ERR_OOM: return "out of memory";
+    case IDP_ERR_STATE_NOT_ADMISSIBLE: return "state not admissible";
+    case IDP_ERR_CFL: return "CFL violation";
+    case IDP_ERR_NONFINITE: return "non-finite state";
+    case IDP_ERR_BOUNDS: return "invariant violated";
+    case IDP_ERR_TIMEOUT: return "device wait timed out";
+    case IDP_ERR_STATE: return "call out of order";
+  }
+  return "unknown";
+}
+
+idp_status idp_create(const idp_config* cfg, void* cuda_stream, idp_ctx** out) {
+  if (!out) return IDP_ERR_ARG;
+  *out = nullptr;
+  idp_config c;
+  if (cfg) c = *cfg; else idp_config_default(&c);
+  if (c.gamma != 1.4) return IDP_ERR_ARG;
+  if (!(c.cfl > 0.0 && c.cfl <= 1.0) || c.limiter_passes < 1 || c.newton_max < 0) return IDP_ERR_ARG;
+  if (c.precision != IDP_PRECISION_FP64) return IDP_ERR_ARG;
+  idp_ctx* ctx = new (std::nothrow) idp_ctx;
+  if (!ctx) return IDP_ERR_OOM;
+  ctx->cfg = c;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return IDP_ERR_CUDA;
+  }
+  ctx->C.cfl = c.cfl;
+  ctx->C.limiter_passes = c.limiter_passes;
+  ctx->C.lim.newton_max = c.newton_max;
+  ctx->C.lim.newton_tol = c.newton_tol;
+  ctx->C.lim.newton_eps = c.newton_eps;
+  *out = ctx;
+  return IDP_OK;
+}
+
+void idp_destroy(idp_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->prof.clear();
+  free_all(ctx);
+  delete ctx;
+}
+
+const char* idp_last_error(const idp_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                               const double* cell_xyz, const int32_t* node_bc, const double* inflow_state) {
+  if (!ctx || !cells || !cell_xyz || n_nodes <= 0 || n_cells <= 0) return fail(ctx, IDP_ERR_ARG, "bad mesh arguments");
+  if (ctx->has_mesh) {
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    ctx->has_mesh = ctx->has_state = ctx->has_trace = false;
+  }
+  std::string msg = idp::assemble_q1(n_nodes, n_cells, cells, cell_xyz, ctx->M);
+  if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
+  ctx->M.bc.assign(node_bc ? node_bc : nullptr, node_bc ? node_bc + n_nodes : nullptr);
+  if (!node_bc) ctx->M.bc.assign(n_nodes, 0);
+  msg = idp::build_sell(ctx->M, ctx->L);
+  if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
+  for (int f = 0; f < 5; ++f) ctx->C.inflow[f] = inflow_state ? inflow_state[f] : 0.0;
+
+  const idp::SellLayout& L = ctx->L;
+  idp::DeviceGraph& G = ctx->G;
+  G.n = L.n;
+  G.n_slots = L.n_slots;
+  idp_status st;
+  int32_t *slice_ptr, *row_len, *col, *tpos, *bc;
+  uint8_t* flags;
+  double *cx, *cy, *cz, *mij, *mi, *inv_mi, *lam;
+  if ((st = upload(ctx, &slice_ptr, L.slice_ptr)) || (st = upload(ctx, &row_len, L.row_len)) ||
+      (st = upload(ctx, &col, L.col)) || (st = upload(ctx, &tpos, L.tpos)) || (st = upload(ctx, &flags, L.flags)) ||
+      (st = upload(ctx, &cx, L.cx)) || (st = upload(ctx, &cy, L.cy)) || (st = upload(ctx, &cz, L.cz)) ||
+      (st = upload(ctx, &mij, L.mij)) || (st = upload(ctx, &mi, L.mi)) || (st = upload(ctx, &inv_mi, L.inv_mi)) ||
+      (st = upload(ctx, &lam, L.lam)) || (st = upload(ctx, &bc, L.bc)))
+    return st;
+  G.slice_ptr = slice_ptr;
+  G.row_len = row_len;
+  G.col = col;
+  G.tpos = tpos;
+  G.flags = flags;
+  G.cx = cx;
+  G.cy = cy;
+  G.cz = cz;
+  G.mij = mij;
+  G.mi = mi;
+  G.inv_mi = inv_mi;
+  G.lam = lam;
+  G.bc = bc;
+
+  idp::StageBuffers& B = ctx->B;
+  const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
+  if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) ||
+      (st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) ||
+      (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.UL, 5 * n)) || (st = dalloc(ctx, &B.R, 5 * n)) ||
+      (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) || (st = dalloc(ctx, &B.l[0], ns)) ||
+      (st = dalloc(ctx, &B.l[1], ns)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
+      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)))
+    return st;
+  B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
+  IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
+  IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
+  ctx->has_mesh = true;
+  return IDP_OK;
+}
+
+idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (n_nodes) *n_nodes = ctx->M.n;
+  if (nnz) *nnz = ctx->M.rowptr[ctx->M.n];
+  return IDP_OK;
+}
+
+idp_status idp_get_matrices(idp_ctx* ctx, int64_t* rowptr, int64_t* col, double* mij, double* cij, double* mi) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  const idp::HostMatrices& M = ctx->M;
+  const int64_t nnz = M.rowptr[M.n];
+  if (rowptr) std::memcpy(rowptr, M.rowptr.data(), sizeof(int64_t) * (M.n + 1));
+  if (col) std::memcpy(col, M.col.data(), sizeof(int64_t) * nnz);
+  if (mij) std::memcpy(mij, M.mij.data(), sizeof(double) * nnz);
+  if (cij)
+    for (int d = 0; d < 3; ++d) std::memcpy(cij + d * nnz, M.cij[d].data(), sizeof(double) * nnz);
+  if (mi)
+    for (int64_t i = 0; i < M.n; ++i) mi[i] = ctx->L.mi[ctx->L.perm[i]];
+  return IDP_OK;
+}
+
+idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device) {
+  if (!ctx || !U) return fail(ctx, IDP_ERR_ARG, "null state");
+  if (!ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
+  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->B.U, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                ctx->stream));
+  idp_bounds_report rep;
+  ctx->has_state = true;
+  idp_status st = idp_check_bounds(ctx, &rep);
+  if (st == IDP_ERR_BOUNDS) {
+    ctx->has_state = false;
+    return fail(ctx, IDP_ERR_STATE_NOT_ADMISSIBLE, "initial state has rho <= 0, epsilon <= 0 or non-finite values");
+  }
+  if (st != IDP_OK) ctx->has_state = false;
+  return st;
+}
+
+idp_status idp_get_state(idp_ctx* ctx, double* U, int on_device) {
+  if (!ctx || !U) return fail(ctx, IDP_ERR_ARG, "null state");
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
+  IDP_CUDA(ctx, cudaMemcpyAsync(U, ctx->B.U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return IDP_OK;
+}
+
+idp_status idp_profile(idp_ctx* ctx, int enable) {
+  if (!ctx) return IDP_ERR_ARG;
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->prof.clear();
+  ctx->prof.enabled = enable != 0;
+  return IDP_OK;
+}
+
+idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return IDP_ERR_ARG;
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < IDP_N_KERNELS; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  const idp::Profiler& P = ctx->prof;
+  for (size_t q = 0; q < P.kernel.size(); ++q) {
+    float t = 0.0f;
+    IDP_CUDA(ctx, cudaEventElapsedTime(&t, P.ev[2 * q], P.ev[2 * q + 1]));
+    ms[P.kernel[q]] += t;
+    launches[P.kernel[q]] += 1;
+  }
+  return IDP_OK;
+}
+
+idp_status idp_step(idp_ctx* ctx, int n_steps) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  if (n_steps < 0) return fail(ctx, IDP_ERR_ARG, "negative step count");
+  idp::StageBuffers& B = ctx->B;
+  int64_t launches = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.U, B.Us, B.U, idp::kBlendNone, 0, true, false, false,
+                                       ctx->stream, &ctx->prof);
+    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.Us, B.Us, B.U, idp::kBlendStage2, 1, false, false, false,
+                                       ctx->stream, &ctx->prof);
+    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.Us, B.U, B.U, idp::kBlendStage3, 1, false, true, false,
+                                       ctx->stream, &ctx->prof);
+  }
+  ctx->launches = launches;
+  IDP_CUDA(ctx, cudaGetLastError());
+  return IDP_OK;
+}
+
+idp_status idp_euler_step(idp_ctx* ctx, double tau, int trace, double* tau_out) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  idp::StageBuffers& B = ctx->B;
+  if (trace && !ctx->has_trace) {
+    const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
+    idp_status st;
+    if ((st = dalloc(ctx, &B.tP, 5 * ns)) || (st = dalloc(ctx, &B.tl4, ns)) || (st = dalloc(ctx, &B.tU5, 5 * n)) ||
+        (st = dalloc(ctx, &B.tl5, ns)) || (st = dalloc(ctx, &B.tUlim, 5 * n)))
+      return st;
+    ctx->has_trace = true;
+  }
+  if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(&B.scal->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->launches = idp::launch_euler_step(ctx->G, B, ctx->C, B.U, B.U, B.U, idp::kBlendNone, tau > 0.0 ? 1 : 0, false,
+                                         false, trace != 0, ctx->stream, &ctx->prof);
+  IDP_CUDA(ctx, cudaGetLastError());
+  if (tau_out) {
+    IDP_CUDA(ctx, cudaMemcpyAsync(tau_out, &B.scal->tau, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return device_status(ctx, true);
+}
+
+idp_status idp_synchronize(idp_ctx* ctx) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (!ctx->has_mesh) {
+    IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return IDP_OK;
+  }
+  return device_status(ctx, true);
+}
+
+idp_status idp_get_time(idp_ctx* ctx, double* t, double* last_tau) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  idp::DeviceScalars s;
+  IDP_CUDA(ctx, cudaMemcpyAsync(&s, ctx->B.scal, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (t) *t = s.time;
+  if (last_tau) *last_tau = s.tau;
+  return IDP_OK;
+}
+
+idp_status idp_set_time(idp_ctx* ctx, double t) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  IDP_CUDA(ctx, cudaMemcpyAsync(&ctx->B.scal->time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return IDP_OK;
+}
+
+idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
+  if (!ctx || !out) return IDP_ERR_ARG;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  const idp::SellLayout& L = ctx->L;
+  const idp::StageBuffers& B = ctx->B;
+  const int64_t n = L.n, ns = L.n_slots, nnz = (int64_t)L.slot_of_entry.size();
+  auto node_field = [&](const double* src, int comps) -> idp_status {
+    std::vector<double> h((size_t)comps * n);
+    IDP_CUDA(ctx, cudaMemcpyAsync(h.data(), src, sizeof(double) * comps * n, cudaMemcpyDeviceToHost, ctx->stream));
+    IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < comps; ++c)
+      for (int64_t i = 0; i < n; ++i) out[c * n + i] = h[c * n + L.perm[i]];
+    return IDP_OK;
+  };
+  auto slot_field = [&](const double* src, int comps) -> idp_status {
+    std::vector<double> h((size_t)comps * ns);
+    IDP_CUDA(ctx, cudaMemcpyAsync(h.data(), src, sizeof(double) * comps * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < comps; ++c)
+      for (int64_t e = 0; e < nnz; ++e) out[c * nnz + e] = h[c * ns + L.slot_of_entry[e]];
+    return IDP_OK;
+  };
+  const bool traced = ctx->has_trace;
+  switch (which) {
+    case IDP_FIELD_D: return slot_field(B.d, 1);
+    case IDP_FIELD_ALPHA: return node_field(B.alpha, 1);
+    case IDP_FIELD_UL: return node_field(B.UL, 5);
+    case IDP_FIELD_R: return node_field(B.R, 5);
+    case IDP_FIELD_BOUNDS: return node_field(B.bnd, 3);
+    case IDP_FIELD_P: return traced ? slot_field(B.tP, 5) : fail(ctx, IDP_ERR_STATE, "no traced stage");
+    case IDP_FIELD_L4: return traced ? slot_field(B.tl4, 1) : fail(ctx, IDP_ERR_STATE, "no traced stage");
+    case IDP_FIELD_U5: return traced ? node_field(B.tU5, 5) : fail(ctx, IDP_ERR_STATE, "no traced stage");
+    case IDP_FIELD_L5: return traced ? slot_field(B.tl5, 1) : fail(ctx, IDP_ERR_STATE, "no traced stage");
+    case IDP_FIELD_ULIM: return traced ? node_field(B.tUlim, 5) : fail(ctx, IDP_ERR_STATE, "no traced stage");
+    case IDP_FIELD_TAU_MAX: {
+      IDP_CUDA(ctx, cudaMemcpyAsync(out, &B.scal->tau_max, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      return IDP_OK;
+    }
+  }
+  return fail(ctx, IDP_ERR_ARG, "unknown field");
+}
+
+idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out) {
+  if (!ctx || !out) return IDP_ERR_ARG;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  idp::launch_check_state(ctx->B.U, ctx->G.n, ctx->check, ctx->stream);
+  IDP_CUDA(ctx, cudaGetLastError());
+  double h[5];
+  IDP_CUDA(ctx, cudaMemcpyAsync(h, ctx->check, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  out->n_rho_nonpositive = (int64_t)h[0];
+  out->n_eps_nonpositive = (int64_t)h[1];
+  out->n_nonfinite = (int64_t)h[2];
+  out->rho_min = h[3];
+  out->eps_min = h[4];
+  if (out->n_rho_nonpositive || out->n_eps_nonpositive || out->n_nonfinite)
+    return fail(ctx, IDP_ERR_BOUNDS, "state violates rho > 0, epsilon > 0 or finiteness");
+  return IDP_OK;
+}
+
+int64_t idp_launch_count(const idp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Host set-up of libidp: stencil sparsity, exact Q1 matrices (Sec. 3.1
+// eq. "matrices"), boundary-pair detection and the sliced-ELL device layout
+// (Sec. 4.3, with slice height 32 = one warp instead of the AVX-512 width).
+//
+// Runs once per mesh, off the time loop (Sec. 3.2: "avoid all assembly
+// operations during the time loop").
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "idp_internal.h"
+
+namespace idp {
+
+namespace {
+
+// 3-point Gauss-Legendre rule on [0,1]: exact for polynomials of degree 5,
+// enough for phi_i phi_j det J and phi_i cof(J) grad^ phi_j of a trilinear
+// map (degree <= 4 per direction).
+struct Quadrature {
+  double w[27];
+  double phi[27][8];
+  double dphi[27][8][3];
+  Quadrature() {
+    const double r = std::sqrt(15.0) / 10.0;
+    const double x1[3] = {0.5 - r, 0.5, 0.5 + r};
+    const double w1[3] = {5.0 / 18.0, 4.0 / 9.0, 5.0 / 18.0};
+    for (int q = 0; q < 27; ++q) {
+      const int qi[3] = {q % 3, (q / 3) % 3, q / 9};
+      w[q] = w1[qi[0]] * w1[qi[1]] * w1[qi[2]];
+      for (int v = 0; v < 8; ++v) {
+        double s[3], ds[3];
+        for (int d = 0; d < 3; ++d) {
+          const double x = x1[qi[d]];
+          const bool hi = (v >> d) & 1;
+          s[d] = hi ? x : 1.0 - x;
+          ds[d] = hi ? 1.0 : -1.0;
+        }
+        phi[q][v] = s[0] * s[1] * s[2];
+        dphi[q][v][0] = ds[0] * s[1] * s[2];
+        dphi[q][v][1] = s[0] * ds[1] * s[2];
+        dphi[q][v][2] = s[0] * s[1] * ds[2];
+      }
+    }
+  }
+};
+
+// Local 8x8 matrices of one cell: m_ab, c_ab (3 components) and int phi_a.
+// Uses det(J) grad phi_b = cof(J) grad^ phi_b, with cof(J) the cofactor matrix.
+bool local_matrices(const Quadrature& Q, const double* X, double M[8][8], double Cm[3][8][8], double m[8]) {
+  std::memset(M, 0, sizeof(double) * 64);
+  std::memset(Cm, 0, sizeof(double) * 192);
+  std::memset(m, 0, sizeof(double) * 8);
+  for (int q = 0; q < 27; ++q) {
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int v = 0; v < 8; ++v)
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) J[r][s] += X[3 * v + r] * Q.dphi[q][v][s];
+    double K[3][3];  // cofactors
+    K[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    K[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    K[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    K[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    K[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    K[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    K[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    K[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    K[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * K[0][0] + J[0][1] * K[0][1] + J[0][2] * K[0][2];
+    if (!(det > 0.0)) return false;
+    double G[8][3];
+    for (int b = 0; b < 8; ++b)
+      for (int r = 0; r < 3; ++r)
+        G[b][r] = K[r][0] * Q.dphi[q][b][0] + K[r][1] * Q.dphi[q][b][1] + K[r][2] * Q.dphi[q][b][2];
+    for (int a = 0; a < 8; ++a) {
+      const double wa = Q.w[q] * Q.phi[q][a];
+      m[a] += wa * det;
+      for (int b = 0; b < 8; ++b) {
+        M[a][b] += wa * Q.phi[q][b] * det;
+        Cm[0][a][b] += wa * G[b][0];
+        Cm[1][a][b] += wa * G[b][1];
+        Cm[2][a][b] += wa * G[b][2];
+      }
+    }
+  }
+  return true;
+}
+
+// Local vertices of the six faces of a hexahedron (v = a + 2b + 4c).
+const int kFace[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+
+}  // namespace
+
+std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const double* xyz, HostMatrices& out) {
+  if (n <= 0 || nc <= 0) return "empty mesh";
+  for (int64_t q = 0; q < 8 * nc; ++q)
+    if (cells[q] < 0 || cells[q] >= n) return "cell references a node id out of range";
+  // node -> cell incidence
+  std::vector<int64_t> inc_ptr(n + 1, 0), inc;
+  for (int64_t q = 0; q < 8 * nc; ++q) inc_ptr[cells[q] + 1]++;
+  for (int64_t i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
+  inc.resize(inc_ptr[n]);
+  {
+    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int v = 0; v < 8; ++v) inc[fill[cells[8 * c + v]]++] = c;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (inc_ptr[i + 1] == inc_ptr[i]) return "a node belongs to no cell";
+
+  // stencil I(i): union of the vertices of the cells around node i (sorted)
+  out.n = n;
+  out.rowptr.assign(n + 1, 0);
+  std::vector<std::vector<int64_t>> rows(n);
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<int64_t>& r = rows[i];
+    for (int64_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q)
+      for (int v = 0; v < 8; ++v) r.push_back(cells[8 * inc[q] + v]);
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+  }
+  for (int64_t i = 0; i < n; ++i) out.rowptr[i + 1] = out.rowptr[i] + (int64_t)rows[i].size();
+  const int64_t nnz = out.rowptr[n];
+  out.col.resize(nnz);
+  for (int64_t i = 0; i < n; ++i) std::copy(rows[i].begin(), rows[i].end(), out.col.begin() + out.rowptr[i]);
+  rows.clear();
+  rows.shrink_to_fit();
+
+  out.mij.assign(nnz, 0.0);
+  for (int d = 0; d < 3; ++d) out.cij[d].assign(nnz, 0.0);
+  out.mi.assign(n, 0.0);
+  auto find = [&](int64_t i, int64_t j) -> int64_t {
+    const int64_t* b = out.col.data() + out.rowptr[i];
+    const int64_t* e = out.col.data() + out.rowptr[i + 1];
+    const int64_t* p = std::lower_bound(b, e, j);
+    return (p != e && *p == j) ? (p - out.col.data()) : -1;
+  };
+
+  // cell matrices, computed in parallel chunks and added in cell order so the
+  // sums do not depend on the thread count
+  static const Quadrature Q;
+  const int64_t chunk = 1 << 16;
+  struct Local {
+    double M[8][8], C[3][8][8], m[8];
+  };
+  std::vector<Local> loc(std::min<int64_t>(chunk, nc));
+  for (int64_t c0 = 0; c0 < nc; c0 += chunk) {
+    const int64_t c1 = std::min(nc, c0 + chunk);
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t c = c0; c < c1; ++c) {
+      Local& L = loc[c - c0];
+      if (!local_matrices(Q, xyz + 24 * c, L.M, L.C, L.m)) bad |= 1;
+    }
+    if (bad) return "a cell has a non-positive Jacobian determinant";
+    for (int64_t c = c0; c < c1; ++c) {
+      const Local& L = loc[c - c0];
+      const int64_t* vn = cells + 8 * c;
+      for (int a = 0; a < 8; ++a) {
+        out.mi[vn[a]] += L.m[a];
+        for (int b = 0; b < 8; ++b) {
+          const int64_t k = find(vn[a], vn[b]);
+          out.mij[k] += L.M[a][b];
+          for (int d = 0; d < 3; ++d) out.cij[d][k] += L.C[d][a][b];
+        }
+      }
+    }
+  }
+
+  // boundary faces: faces of exactly one cell.  Entries (i, j) with both
+  // nodes on a common boundary face carry the boundary term
+  // c_ij + c_ji = int_dOmega phi_i phi_j n; all others are skew in exact
+  // arithmetic and are made skew bitwise here.
+  out.boundary_pair.assign(nnz, 0);
+  std::vector<uint8_t> on_boundary(n, 0);
+  std::vector<uint8_t> face_free(6 * nc, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t* vn = cells + 8 * c;
+    for (int f = 0; f < 6; ++f) {
+      const int64_t a = vn[kFace[f][0]], b = vn[kFace[f][1]], e = vn[kFace[f][2]], g = vn[kFace[f][3]];
+      bool shared = false;
+      for (int64_t q = inc_ptr[a]; q < inc_ptr[a + 1] && !shared; ++q) {
+        const int64_t o = inc[q];
+        if (o == c) continue;
+        const int64_t* on = cells + 8 * o;
+        int hit = 0;
+        for (int v = 0; v < 8; ++v) hit += (on[v] == b) + (on[v] == e) + (on[v] == g);
+        shared = hit >= 3;
+      }
+      face_free[6 * c + f] = shared ? 0 : 1;
+    }
+  }
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t* vn = cells + 8 * c;
+    for (int f = 0; f < 6; ++f) {
+      if (!face_free[6 * c + f]) continue;
+      const int64_t fn[4] = {vn[kFace[f][0]], vn[kFace[f][1]], vn[kFace[f][2]], vn[kFace[f][3]]};
+      for (int p = 0; p < 4; ++p) {
+        on_boundary[fn[p]] = 1;
+        for (int r = 0; r < 4; ++r) {
+          const int64_t k = find(fn[p], fn[r]);
+          if (k >= 0) out.boundary_pair[k] = 1;
+        }
+      }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = out.rowptr[i]; k < out.rowptr[i + 1]; ++k) {
+      const int64_t j = out.col[k];
+      if (j == i) {
+        if (!on_boundary[i])
+          for (int d = 0; d < 3; ++d) out.cij[d][k] = 0.0;
+        continue;
+      }
+      if (j < i || out.boundary_pair[k]) continue;
+      const int64_t kt = find(j, i);
+      for (int d = 0; d < 3; ++d) {
+        const double s = 0.5 * (out.cij[d][k] - out.cij[d][kt]);
+        out.cij[d][k] = s;
+        out.cij[d][kt] = -s;
+      }
+    }
+  }
+  return "";
+}
+
+std::string build_sell(const HostMatrices& M, SellLayout& L) {
+  const int64_t n = M.n;
+  L.n = n;
+  L.perm.resize(n);
+  L.iperm.resize(n);
+  for (int64_t i = 0; i < n; ++i) L.perm[i] = L.iperm[i] = i;  // caller order keeps mesh locality
+  L.n_slices = (n + kSlice - 1) / kSlice;
+  L.slice_ptr.assign(L.n_slices + 1, 0);
+  L.row_len.assign(n, 0);
+  int64_t slots = 0;
+  for (int64_t s = 0; s < L.n_slices; ++s) {
+    int64_t w = 0;
+    for (int64_t r = s * kSlice; r < std::min(n, (s + 1) * kSlice); ++r) {
+      const int64_t i = L.iperm[r];
+      w = std::max(w, M.rowptr[i + 1] - M.rowptr[i]);
+    }
+    slots += w * kSlice;
+    if (slots > INT32_MAX) return "too many matrix entries for 32-bit slot indices";
+    L.slice_ptr[s + 1] = (int32_t)slots;
+  }
+  L.n_slots = slots;
+  L.col.assign(slots, 0);
+  L.tpos.assign(slots, 0);
+  L.flags.assign(slots, kEntryPad);
+  L.cx.assign(slots, 0.0);
+  L.cy.assign(slots, 0.0);
+  L.cz.assign(slots, 0.0);
+  L.mij.assign(slots, 0.0);
+  L.mi.resize(n);
+  L.inv_mi.resize(n);
+  L.lam.resize(n);
+  L.bc.assign(n, 0);
+  L.slot_of_entry.assign(M.rowptr[n], -1);
+  auto slot = [&](int64_t r, int64_t k) -> int64_t { return L.slice_ptr[r / kSlice] + k * kSlice + (r % kSlice); };
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t i = L.iperm[r];
+    const int64_t len = M.rowptr[i + 1] - M.rowptr[i];
+    if (len < 2) return "a node has no neighbours";
+    L.row_len[r] = (int32_t)len;
+    // the lumped mass m_i = int phi_i equals the row sum of m_ij (partition of unity)
+    double m = 0.0;
+    for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) m += M.mij[k];
+    L.mi[r] = m;
+    L.inv_mi[r] = 1.0 / m;
+    L.lam[r] = 1.0 / (double)(len - 1);
+    L.bc[r] = M.bc.empty() ? 0 : M.bc[i];
+    const int64_t w = (L.slice_ptr[r / kSlice + 1] - L.slice_ptr[r / kSlice]) / kSlice;
+    for (int64_t k = 0; k < w; ++k) {  // padding slots point at the row itself
+      const int64_t p = slot(r, k);
+      L.col[p] = (int32_t)r;
+      L.tpos[p] = (int32_t)p;
+    }
+    for (int64_t k = 0; k < len; ++k) {
+      const int64_t e = M.rowptr[i] + k;
+      const int64_t p = slot(r, k);
+      const int64_t j = L.perm[M.col[e]];
+      L.slot_of_entry[e] = p;
+      L.col[p] = (int32_t)j;
+      L.cx[p] = M.cij[0][e];
+      L.cy[p] = M.cij[1][e];
+      L.cz[p] = M.cij[2][e];
+      L.mij[p] = M.mij[e];
+      uint8_t f = 0;
+      if (j == r) f |= kEntryDiag;
+      if (j > r) f |= kEntryUpper;
+      L.flags[p] = f;
+    }
+  }
+  // transposed slots and bitwise skew pairs
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t e = M.rowptr[i]; e < M.rowptr[i + 1]; ++e) {
+      const int64_t j = M.col[e];
+      const int64_t* b = M.col.data() + M.rowptr[j];
+      const int64_t* x = M.col.data() + M.rowptr[j + 1];
+      const int64_t* q = std::lower_bound(b, x, i);
+      if (q == x || *q != i) return "sparsity pattern is not structurally symmetric";
+      const int64_t et = q - M.col.data();
+      const int64_t p = L.slot_of_entry[e], pt = L.slot_of_entry[et];
+      L.tpos[p] = (int32_t)pt;
+      if (j != i && M.cij[0][et] == -M.cij[0][e] && M.cij[1][et] == -M.cij[1][e] && M.cij[2][et] == -M.cij[2][e])
+        L.flags[p] |= kEntrySkew;
+    }
+  }
+  return "";
+}
+
+}  // namespace idp

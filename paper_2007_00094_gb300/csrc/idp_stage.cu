@@ -1,0 +1,532 @@
+// FP64 kernels of one euler_step (Alg. 1), thread per row over the
+// sliced-ELL graph.  Kernel boundaries are the global dependencies of the
+// algorithm (Fig. 2): alpha_j and d_ji after Step 1, tau after Step 2, R_j
+// after Step 3, l_ji after Steps 4 and 5.
+#include <cfloat>
+
+#include "idp_internal.h"
+#include "idp_stage.cuh"
+
+namespace idp {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
+  return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
+}
+
+__device__ __forceinline__ void load5(const double* U, int64_t n, int64_t i, double* u) {
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) u[f] = U[f * n + i];
+}
+
+// f(U) . c of eq. (flux): (m.c, v (m.c) + p c, (E+p)/rho (m.c)), with an
+// operation sequence pinned by rounding intrinsics so that equal states give
+// bitwise equal fluxes (differences f_j - f_i then vanish exactly, as in the
+// oracle).
+__device__ __forceinline__ void flux_dot(double m1, double m2, double m3, double inv_rho, double p, double h,
+                                         double cx, double cy, double cz, double* f) {
+  const double mc = __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
+  f[0] = mc;
+  f[1] = __fma_rn(p, cx, __dmul_rn(__dmul_rn(m1, inv_rho), mc));
+  f[2] = __fma_rn(p, cy, __dmul_rn(__dmul_rn(m2, inv_rho), mc));
+  f[3] = __fma_rn(p, cz, __dmul_rn(__dmul_rn(m3, inv_rho), mc));
+  f[4] = __dmul_rn(h, mc);
+}
+
+__device__ __forceinline__ Side load_side(const double* U, const double* Q, int64_t n, int64_t i) {
+  Side s;
+  s.rho = U[i];
+  s.mx = U[n + i];
+  s.my = U[2 * n + i];
+  s.mz = U[3 * n + i];
+  s.inv_rho = Q[kQInvRho * n + i];
+  s.p = Q[kQP * n + i];
+  s.c = Q[kQC * n + i];
+  s.pm = Q[kQPm * n + i];
+  s.inv_p = Q[kQInvP * n + i];
+  return s;
+}
+
+// Step 0: per-node quantities (Sec. 2): 1/rho, p, c, p^(-1/7), 1/p,
+// eta/rho with eta = (rho eps)^(5/12), (E + p)/rho and phi = eps rho^(-7/5).
+__global__ void __launch_bounds__(kBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
+                                                 DeviceScalars* scal) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double u[kFields];
+  load5(U, n, i, u);
+  const double rho = u[0];
+  const double inv_rho = 1.0 / rho;
+  const double eps = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * inv_rho;
+  if (!(rho > 0.0) || !(eps > 0.0)) atomicOr(&scal->status, kStatusNotAdmissible);
+  const double p = 0.4 * eps;
+  const double rho_eps = rho * eps;
+  const double w12 = inv_root<12>(rho_eps);  // (rho eps)^(-1/12)
+  double w7 = w12 * w12 * w12;
+  w7 = w7 * w7 * w12;  // (rho eps)^(-7/12)
+  const double eta = rho_eps * w7;
+  const double w5 = inv_root<5>(rho);
+  double r7 = w5 * w5 * w5;
+  r7 = r7 * r7 * w5;  // rho^(-7/5)
+  Q[kQInvRho * n + i] = inv_rho;
+  Q[kQP * n + i] = p;
+  Q[kQC * n + i] = sqrt(1.4 * p * inv_rho);
+  Q[kQPm * n + i] = inv_root<7>(p);
+  Q[kQInvP * n + i] = 1.0 / p;
+  Q[kQS * n + i] = eta * inv_rho;
+  Q[kQH * n + i] = (u[4] + p) * inv_rho;
+  Q[kQPhi * n + i] = eps * r7;
+}
+
+// Step 1: d^L_ij for the edges this row owns (j > i) and the indicator
+// alpha_i (Sec. 3.7) over all j in I(i).
+__global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
+                                                 const double* __restrict__ Q, double* __restrict__ d,
+                                                 double* __restrict__ alpha, DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) scal->tau_min_bits = 0x7ff0000000000000ull;  // +inf, read by the next kernel
+  if (r >= G.n) return;
+  const int64_t n = G.n;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const Side si = load_side(U, Q, n, r);
+  const double Ei = U[4 * n + r];
+  const double s_i = Q[kQS * n + r], h_i = Q[kQH * n + r];
+  double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0, b4 = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const uint8_t fl = G.flags[p];
+    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
+    const Side sj = load_side(U, Q, n, j);
+    const double s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
+    double fj[kFields], fi[kFields];
+    flux_dot(sj.mx, sj.my, sj.mz, sj.inv_rho, sj.p, h_j, cx, cy, cz, fj);
+    flux_dot(si.mx, si.my, si.mz, si.inv_rho, si.p, h_i, cx, cy, cz, fi);
+    a += (s_j - s_i) * fj[0];
+    b0 += fj[0] - fi[0];
+    b1 += fj[1] - fi[1];
+    b2 += fj[2] - fi[2];
+    b3 += fj[3] - fi[3];
+    b4 += fj[4] - fi[4];
+    if (fl & kEntryUpper) {
+      const double nc = sqrt(cx * cx + cy * cy + cz * cz);
+      double dij = 0.0;
+      if (nc > 0.0) {
+        const double inv = 1.0 / nc;
+        dij = lambda_max(cx * inv, cy * inv, cz * inv, si, sj) * nc;
+      }
+      if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
+        const int64_t pt = G.tpos[p];
+        const double tx = G.cx[pt], ty = G.cy[pt], tz = G.cz[pt];
+        const double nt = sqrt(tx * tx + ty * ty + tz * tz);
+        if (nt > 0.0) {
+          const double inv = 1.0 / nt;
+          dij = fmax(dij, lambda_max(tx * inv, ty * inv, tz * inv, sj, si) * nt);
+        }
+      }
+      d[p] = dij;
+    }
+  }
+  // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
+  const double sc = s_i * si.inv_p * (1.0 / 6.0);
+  const double e0 = sc * Ei, e1 = -sc * si.mx, e2 = -sc * si.my, e3 = -sc * si.mz, e4 = sc * si.rho;
+  const double num = a - (e0 * b0 + e1 * b1 + e2 * b2 + e3 * b3 + e4 * b4) + s_i * b0;
+  const double D = fabs(a) + fabs(e0 - s_i) * fabs(b0) + fabs(e1) * fabs(b1) + fabs(e2) * fabs(b2) +
+                   fabs(e3) * fabs(b3) + fabs(e4) * fabs(b4);
+  alpha[r] = D > 0.0 ? fabs(num) / D : 0.0;
+}
+
+__device__ __forceinline__ double block_min(double v) {
+  __shared__ double red[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
+// CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
+__global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restrict__ d, DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double cand = INFINITY;
+  if (r < G.n) {
+    const int64_t base = slot_base(G, r);
+    const int len = G.row_len[r];
+    double sum = 0.0;
+    int64_t pd = base;
+    for (int k = 0; k < len; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      const int64_t j = G.col[p];
+      if (j == r) {
+        pd = p;
+        continue;
+      }
+      double v;
+      if (j < r) {
+        v = d[G.tpos[p]];
+        d[p] = v;
+      } else {
+        v = d[p];
+      }
+      sum += v;
+    }
+    d[pd] = -sum;
+    cand = G.mi[r] / (2.0 * sum);
+  }
+  cand = block_min(cand);
+  if (threadIdx.x == 0 && cand < INFINITY) atomicMin(&scal->tau_min_bits, (unsigned long long)__double_as_longlong(cand));
+}
+
+__device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_mode, double cfl) {
+  return tau_mode == 0 ? cfl * __longlong_as_double((long long)scal->tau_min_bits) : scal->tau;
+}
+
+// Step 3: low-order update through the bar states (eq. def-ubar), R_i
+// (eq. high-order-final) and the local bounds rho_min, rho_max over
+// rho(Ubar_ij) and phi_min over phi(U_j), j in I(i) (Sec. 3.8).
+__global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                      const double* __restrict__ Q, const double* __restrict__ d,
+                                                      const double* __restrict__ alpha, double* __restrict__ UL,
+                                                      double* __restrict__ R, double* __restrict__ bnd,
+                                                      DeviceScalars* scal, int tau_mode, int accumulate_time) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  if (r == 0) {
+    const double tmax = __longlong_as_double((long long)scal->tau_min_bits);
+    scal->tau_max = tmax;
+    if (tau_mode == 0) {
+      scal->tau = tau;
+      if (accumulate_time) scal->time += tau;
+    } else if (tau > tmax) {
+      atomicOr(&scal->status, kStatusCfl);
+    }
+  }
+  if (r >= G.n) return;
+  const int64_t n = G.n;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double ui[kFields];
+  load5(U, n, r, ui);
+  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
+  const double a_i = alpha[r];
+  const double two_tau_m = 2.0 * tau * G.inv_mi[r];
+  double ul[kFields], rr[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    ul[f] = ui[f];
+    rr[f] = 0.0;
+  }
+  double rho_min = INFINITY, rho_max = -INFINITY, phi_min = INFINITY;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
+    const double dij = d[p];
+    double uj[kFields];
+    load5(U, n, j, uj);
+    const double inv_rho_j = Q[kQInvRho * n + j], p_j = Q[kQP * n + j], h_j = Q[kQH * n + j];
+    double fj[kFields], fi[kFields];
+    flux_dot(uj[1], uj[2], uj[3], inv_rho_j, p_j, h_j, cx, cy, cz, fj);
+    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, cx, cy, cz, fi);
+    const double dH = dij * (a_i + alpha[j]) * 0.5;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) rr[f] += -fj[f] + dH * (uj[f] - ui[f]);
+    if (dij != 0.0) {
+      const double inv2d = 0.5 / dij;
+      const double coef = two_tau_m * dij;
+      double ub[kFields];
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        ub[f] = 0.5 * (ui[f] + uj[f]) - (fj[f] - fi[f]) * inv2d;
+        ul[f] += coef * ub[f];
+      }
+      rho_min = fmin(rho_min, ub[0]);
+      rho_max = fmax(rho_max, ub[0]);
+    }
+    phi_min = fmin(phi_min, Q[kQPhi * n + j]);
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    UL[f * n + r] = ul[f];
+    R[f * n + r] = rr[f];
+  }
+  bnd[r] = rho_min;
+  bnd[n + r] = rho_max;
+  bnd[2 * n + r] = phi_min;
+}
+
+// Step 4: antidiffusive fluxes P_ij (eq. def-p) with b_ij = -m_ij/m_j,
+// b_ji = -m_ij/m_i (j != i) and the first limiter values l_ij.
+__global__ void __launch_bounds__(kBlock) k_flux_limit(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                       const double* __restrict__ d, const double* __restrict__ alpha,
+                                                       const double* __restrict__ UL, const double* __restrict__ R,
+                                                       const double* __restrict__ bnd, double* __restrict__ P,
+                                                       double* __restrict__ l, const DeviceScalars* scal,
+                                                       int tau_mode) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double ui[kFields], ri[kFields], ul[kFields];
+  load5(U, n, r, ui);
+  load5(R, n, r, ri);
+  load5(UL, n, r, ul);
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const double a_i = alpha[r];
+  const double inv_mi = G.inv_mi[r];
+  const double scale = tau * inv_mi * (double)(len - 1);  // tau / (m_i lambda_i)
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) P[f * ns + p] = 0.0;
+      l[p] = 0.0;
+      continue;
+    }
+    double uj[kFields], rj[kFields], pij[kFields];
+    load5(U, n, j, uj);
+    load5(R, n, j, rj);
+    const double m = G.mij[p];
+    const double b_ij = -m * G.inv_mi[j];
+    const double b_ji = -m * inv_mi;
+    const double dij = d[p];
+    const double dd = dij * (a_i + alpha[j]) * 0.5 - dij;  // d^H_ij - d^L_ij
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = scale * (b_ij * rj[f] - b_ji * ri[f] + dd * (uj[f] - ui[f]));
+      P[f * ns + p] = pij[f];
+    }
+    l[p] = limiter(ul, pij, rmin, rmax, pmin, C.lim);
+  }
+}
+
+// Steps 5, 6, ...: U_i += sum_j lambda_i min(l_ij, l_ji) P_ij, then (not in
+// the last pass) P_ij <- (1 - min(l_ij, l_ji)) P_ij and new l_ij.
+__global__ void __launch_bounds__(kBlock) k_limiter_pass(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                         double* __restrict__ Unext, double* __restrict__ P,
+                                                         const double* __restrict__ lold, double* __restrict__ lnew,
+                                                         const double* __restrict__ bnd) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double lam = G.lam[r];
+  double u[kFields];
+  load5(Ucur, n, r, u);
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double lk = fmin(lold[p], lold[G.tpos[p]]);
+    const double w = lam * lk;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) Unext[f * n + r] = u[f];
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) {
+      lnew[p] = 0.0;
+      continue;
+    }
+    const double lk = fmin(lold[p], lold[G.tpos[p]]);
+    double pij[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = (1.0 - lk) * P[f * ns + p];
+      P[f * ns + p] = pij[f];
+    }
+    lnew[p] = limiter(u, pij, rmin, rmax, pmin, C.lim);
+  }
+}
+
+// Last limiter pass, boundary post-processing (slip walls drop the flagged
+// normal momentum components, inflow nodes take the inflow state) and the
+// SSP-RK3 blend (Sec. 3.5): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
+__global__ void __launch_bounds__(kBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                  const double* __restrict__ P, const double* __restrict__ l,
+                                                  const double* __restrict__ Un, double* __restrict__ Uout,
+                                                  double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+                                                  int skip_write_on_error) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double lam = G.lam[r];
+  double u[kFields];
+  load5(Ucur, n, r, u);
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double lk = fmin(l[p], l[G.tpos[p]]);
+    const double w = lam * lk;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
+  }
+  if (Ulim) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) Ulim[f * n + r] = u[f];
+  }
+  const int bc = G.bc[r];
+  if (bc & 8) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) u[f] = C.inflow[f];
+  } else {
+    if (bc & 1) u[1] = 0.0;
+    if (bc & 2) u[2] = 0.0;
+    if (bc & 4) u[3] = 0.0;
+  }
+  double out[kFields];
+  bool finite = true;
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    double v = u[f];
+    if (blend == kBlendStage2) v = 0.75 * Un[f * n + r] + 0.25 * u[f];
+    if (blend == kBlendStage3) v = (1.0 / 3.0) * Un[f * n + r] + (2.0 / 3.0) * u[f];
+    out[f] = v;
+    finite &= isfinite(v);
+  }
+  if (!finite) atomicOr(&scal->status, kStatusNonFinite);
+  if (skip_write_on_error && *(volatile int*)&scal->status != 0) return;
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
+}
+
+__global__ void k_check_state(const double* __restrict__ U, int64_t n, double* out) {
+  __shared__ double smin[2][kBlock / 32];
+  __shared__ unsigned long long cnt[3];
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  double rmin = INFINITY, emin = INFINITY;
+  unsigned long long c0 = 0, c1 = 0, c2 = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double u[kFields];
+    load5(U, n, i, u);
+    bool fin = true;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) fin &= isfinite(u[f]);
+    const double eps = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
+    c0 += !(u[0] > 0.0);
+    c1 += !(eps > 0.0);
+    c2 += !fin;
+    rmin = fmin(rmin, u[0]);
+    emin = fmin(emin, eps);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smin[0][threadIdx.x >> 5] = rmin;
+    smin[1][threadIdx.x >> 5] = emin;
+    atomicAdd(&cnt[0], c0);
+    atomicAdd(&cnt[1], c1);
+    atomicAdd(&cnt[2], c2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kBlock / 32; ++w) {
+      smin[0][0] = fmin(smin[0][0], smin[0][w]);
+      smin[1][0] = fmin(smin[1][0], smin[1][w]);
+    }
+    // single-block launch: plain stores
+    out[0] = (double)cnt[0];
+    out[1] = (double)cnt[1];
+    out[2] = (double)cnt[2];
+    out[3] = smin[0][0];
+    out[4] = smin[1][0];
+  }
+}
+
+}  // namespace
+
+void Profiler::begin(int id, cudaStream_t s) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  ev.push_back(a);
+  ev.push_back(b);
+  kernel.push_back(id);
+  cudaEventRecord(a, s);
+}
+
+void Profiler::end(cudaStream_t s) { cudaEventRecord(ev.back(), s); }
+
+void Profiler::clear() {
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  ev.clear();
+  kernel.clear();
+}
+
+int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
+                      double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
+                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof) {
+  const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
+  const bool p = prof && prof->enabled;
+  int launches = 0;
+  auto run = [&](int id, auto&& launch) {
+    if (p) prof->begin(id, s);
+    launch();
+    if (p) prof->end(s);
+    ++launches;
+  };
+  run(kKNode, [&] { k_node<<<grid, kBlock, 0, s>>>(G.n, Uin, B.node, B.scal); });
+  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.alpha, B.scal); });
+  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, B.d, B.scal); });
+  run(kKLowOrder, [&] {
+    k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.alpha, B.UL, B.R, B.bnd, B.scal, tau_mode,
+                                        accumulate_time ? 1 : 0);
+  });
+  run(kKFluxLimit, [&] {
+    k_flux_limit<<<grid, kBlock, 0, s>>>(G, C, Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], B.scal, tau_mode);
+  });
+  if (trace) {
+    cudaMemcpyAsync(B.tP, B.P, sizeof(double) * kFields * G.n_slots, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(B.tl4, B.l[0], sizeof(double) * G.n_slots, cudaMemcpyDeviceToDevice, s);
+  }
+  const double* cur = B.UL;
+  int lbuf = 0, wbuf = 0;
+  for (int pass = 1; pass < C.limiter_passes; ++pass) {
+    double* next = B.Uw[wbuf];
+    run(kKLimiterPass,
+        [&] { k_limiter_pass<<<grid, kBlock, 0, s>>>(G, C, cur, next, B.P, B.l[lbuf], B.l[lbuf ^ 1], B.bnd); });
+    if (trace && pass == 1) {
+      cudaMemcpyAsync(B.tU5, next, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(B.tl5, B.l[lbuf ^ 1], sizeof(double) * G.n_slots, cudaMemcpyDeviceToDevice, s);
+    }
+    cur = next;
+    wbuf ^= 1;
+    lbuf ^= 1;
+  }
+  run(kKFinal, [&] {
+    k_final<<<grid, kBlock, 0, s>>>(G, C, cur, B.P, B.l[lbuf], Un, Uout, trace ? B.tUlim : nullptr, B.scal, blend,
+                                    skip_write_on_error ? 1 : 0);
+  });
+  return launches;
+}
+
+void launch_check_state(const double* U, int64_t n, double* out, cudaStream_t s) {
+  k_check_state<<<1, kBlock, 0, s>>>(U, n, out);
+}
+
+}  // namespace idp

@@ -1,0 +1,110 @@
+// Device-side data of one context and the stage launcher.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "idp_device.cuh"
+
+namespace idp {
+
+// Read-only graph: sliced-ELL matrices (slot = slice_ptr[r/32] + 32 k + r%32)
+// and per-row data, in the library's row order.
+struct DeviceGraph {
+  int64_t n;
+  int64_t n_slots;
+  const int32_t* slice_ptr;
+  const int32_t* row_len;
+  const int32_t* col;
+  const int32_t* tpos;
+  const uint8_t* flags;
+  const double* cx;
+  const double* cy;
+  const double* cz;
+  const double* mij;
+  const double* mi;
+  const double* inv_mi;
+  const double* lam;
+  const int32_t* bc;
+};
+
+// Device status bits latched by the kernels.
+enum : int {
+  kStatusNotAdmissible = 1,
+  kStatusCfl = 2,
+  kStatusNonFinite = 4,
+  kStatusTimeout = 8
+};
+
+// Device scalars of a context.
+struct DeviceScalars {
+  double tau;                     // tau_n of the current RK step
+  double time;                    // accumulated simulated time
+  double tau_max;                 // min_i m_i / (-2 d_ii) of the last stage
+  unsigned long long tau_min_bits;  // atomicMin accumulator of positive doubles
+  int status;
+};
+
+// Work buffers of the stage (all device memory owned by the context).
+struct StageBuffers {
+  double* U;     // U^n, 5n
+  double* Us;    // RK stage state, 5n
+  double* node;  // kNodeQ * n
+  double* d;     // n_slots
+  double* alpha; // n
+  double* UL;    // 5n
+  double* R;     // 5n
+  double* bnd;   // 3n
+  double* P;     // 5 * n_slots
+  double* l[2];  // n_slots each
+  double* Uw[2]; // 5n each
+  DeviceScalars* scal;
+  // trace copies (allocated on first traced stage)
+  double* tP;
+  double* tl4;
+  double* tU5;
+  double* tl5;
+  double* tUlim;
+};
+
+struct StageConfig {
+  double cfl;
+  int limiter_passes;
+  LimiterParams lim;
+  double inflow[5];
+};
+
+enum Blend : int { kBlendNone = 0, kBlendStage2 = 1, kBlendStage3 = 2 };
+
+// Kernel ids of one euler_step (also the order of idp_profile_read).
+enum KernelId : int { kKNode = 0, kKEdge, kKDiag, kKLowOrder, kKFluxLimit, kKLimiterPass, kKFinal, kNumKernels };
+
+// Optional per-kernel timing: CUDA events recorded on the launch stream
+// around each kernel; read back (and synchronised) by the owner.
+struct Profiler {
+  bool enabled = false;
+  std::vector<cudaEvent_t> ev;     // begin/end pairs
+  std::vector<int> kernel;         // kernel id per pair
+  cudaEvent_t take();
+  void begin(int id, cudaStream_t s);
+  void end(cudaStream_t s);
+  void clear();
+};
+
+// Enqueues one euler_step (Alg. 1) on stream s:
+//   Uin -> Uout with boundary post-processing and the RK blend with Un.
+// tau_mode 0: tau = c_cfl min m_i/(-2 d_ii) is computed and stored (stage 1);
+// tau_mode 1: the stored tau is used and checked (stages 2, 3, fixed tau).
+// accumulate_time adds tau to the simulated time (once per RK step).
+// Returns the number of kernel launches.
+int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
+                      double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
+                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof = nullptr);
+
+// Counts nodes with rho <= 0, epsilon <= 0, non-finite values; writes
+// {count_rho, count_eps, count_nonfinite} as doubles plus rho_min, eps_min
+// into out[0..4] (device memory).
+void launch_check_state(const double* U, int64_t n, double* out, cudaStream_t s);
+
+}  // namespace idp

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libidp (include/idp.h).
+
+Argument marshalling only: every step of the stage runs in the CUDA kernels
+of libidp.so.  Functions keep the C names (``idp_create``, ``idp_step``, ...);
+:class:`Solver` bundles them for convenience.  Device buffers may be torch
+CUDA tensors (their ``data_ptr()`` is passed with ``on_device=1``), streams
+may be ``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers.
+
+If libidp.so has not been built (``python -m paper_2007_00094_gb300.build``)
+loading fails with an ImportError: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libidp.so")
+
+IDP_OK = 0
+STATUS_NAMES = {0: "IDP_OK", 1: "IDP_ERR_ARG", 2: "IDP_ERR_CUDA", 3: "IDP_ERR_OOM", 4: "IDP_ERR_STATE_NOT_ADMISSIBLE",
+                5: "IDP_ERR_CFL", 6: "IDP_ERR_NONFINITE", 7: "IDP_ERR_BOUNDS", 8: "IDP_ERR_TIMEOUT",
+                9: "IDP_ERR_STATE"}
+FIELDS = {"d": 0, "alpha": 1, "UL": 2, "R": 3, "bounds": 4, "P": 5, "l4": 6, "U5": 7, "l5": 8, "Ulim": 9,
+          "tau_max": 10}
+
+# Every symbol include/idp.h declares.
+EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error", "idp_status_string",
+            "idp_upload_mesh_hex", "idp_mesh_info", "idp_get_matrices", "idp_init_state", "idp_get_state",
+            "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
+            "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read"]
+KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final"]
+
+
+class IdpConfig(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter_passes", C.c_int), ("newton_max", C.c_int),
+                ("newton_tol", C.c_double), ("newton_eps", C.c_double), ("precision", C.c_int),
+                ("schedule", C.c_int), ("barrier_spin_limit", C.c_int64)]
+
+
+class BoundsReport(C.Structure):
+    _fields_ = [("n_rho_nonpositive", C.c_int64), ("n_eps_nonpositive", C.c_int64), ("n_nonfinite", C.c_int64),
+                ("rho_min", C.c_double), ("eps_min", C.c_double)]
+
+
+class IdpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+
+
+def load(path: str = LIB_PATH):
+    """Loads libidp.so (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libidp.so not built at {path}; run paper_2007_00094_gb300.build.build()")
+    L = C.CDLL(path)
+    L.idp_config_default.argtypes = [C.POINTER(IdpConfig)]
+    L.idp_config_default.restype = None
+    L.idp_create.argtypes = [C.POINTER(IdpConfig), _vp, C.POINTER(_vp)]
+    L.idp_destroy.argtypes = [_vp]
+    L.idp_destroy.restype = None
+    L.idp_last_error.argtypes = [_vp]
+    L.idp_last_error.restype = C.c_char_p
+    L.idp_status_string.argtypes = [C.c_int]
+    L.idp_status_string.restype = C.c_char_p
+    L.idp_upload_mesh_hex.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
+    L.idp_mesh_info.argtypes = [_vp, _i64p, _i64p]
+    L.idp_get_matrices.argtypes = [_vp, _i64p, _i64p, _dp, _dp, _dp]
+    L.idp_init_state.argtypes = [_vp, _vp, C.c_int]
+    L.idp_get_state.argtypes = [_vp, _vp, C.c_int]
+    L.idp_step.argtypes = [_vp, C.c_int]
+    L.idp_euler_step.argtypes = [_vp, C.c_double, C.c_int, _dp]
+    L.idp_synchronize.argtypes = [_vp]
+    L.idp_get_time.argtypes = [_vp, _dp, _dp]
+    L.idp_set_time.argtypes = [_vp, C.c_double]
+    L.idp_get_field.argtypes = [_vp, C.c_int, _dp]
+    L.idp_check_bounds.argtypes = [_vp, C.POINTER(BoundsReport)]
+    L.idp_launch_count.argtypes = [_vp]
+    L.idp_launch_count.restype = C.c_int64
+    L.idp_profile.argtypes = [_vp, C.c_int]
+    L.idp_profile_read.argtypes = [_vp, _dp, _i64p]
+    _lib = L
+    return L
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def idp_config_default() -> IdpConfig:
+    cfg = IdpConfig()
+    load().idp_config_default(C.byref(cfg))
+    return cfg
+
+
+def _check(ctx, st):
+    if st != IDP_OK:
+        msg = load().idp_last_error(ctx).decode() if ctx else ""
+        raise IdpError(st, msg)
+
+
+class Solver:
+    """One libidp context: a mesh, its matrices and the stage buffers."""
+
+    def __init__(self, mesh, config: IdpConfig | None = None, stream=None, **overrides):
+        L = load()
+        cfg = config or idp_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        self._ctx = _vp()
+        st = L.idp_create(C.byref(cfg), _stream_handle(stream), C.byref(self._ctx))
+        if st != IDP_OK:
+            raise IdpError(st, "idp_create failed")
+        self.n = mesh.n_nodes
+        cells = np.ascontiguousarray(mesh.cells, dtype=np.int64)
+        xyz = np.ascontiguousarray(mesh.cell_xyz, dtype=np.float64)
+        bc = np.ascontiguousarray(mesh.bc, dtype=np.int32)
+        inflow = None if mesh.inflow is None else np.ascontiguousarray(mesh.inflow, dtype=np.float64)
+        _check(self._ctx, L.idp_upload_mesh_hex(self._ctx, mesh.n_nodes, cells.shape[0], _ptr(cells, _i64p),
+                                                _ptr(xyz), _ptr(bc, _i32p),
+                                                None if inflow is None else _ptr(inflow)))
+        n, nnz = C.c_int64(), C.c_int64()
+        _check(self._ctx, L.idp_mesh_info(self._ctx, C.byref(n), C.byref(nnz)))
+        self.nnz = nnz.value
+
+    def close(self):
+        if self._ctx:
+            load().idp_destroy(self._ctx)
+            self._ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_state(self, U):
+        """U: (5, n) float64 numpy array or CUDA torch tensor (caller order)."""
+        if hasattr(U, "data_ptr"):
+            assert U.is_cuda and U.dtype.itemsize == 8 and U.is_contiguous() and U.numel() == 5 * self.n
+            _check(self._ctx, load().idp_init_state(self._ctx, U.data_ptr(), 1))
+        else:
+            a = np.ascontiguousarray(U, dtype=np.float64)
+            assert a.size == 5 * self.n
+            _check(self._ctx, load().idp_init_state(self._ctx, a.ctypes.data, 0))
+
+    def get_state(self, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            _check(self._ctx, load().idp_get_state(self._ctx, out.data_ptr(), 1))
+            return out
+        a = np.empty((5, self.n)) if out is None else out
+        _check(self._ctx, load().idp_get_state(self._ctx, a.ctypes.data, 0))
+        return a
+
+    def step(self, n_steps=1):
+        """Enqueues n_steps SSP-RK3 steps (no host synchronisation)."""
+        _check(self._ctx, load().idp_step(self._ctx, int(n_steps)))
+
+    def synchronize(self):
+        _check(self._ctx, load().idp_synchronize(self._ctx))
+
+    def euler_step(self, tau=None, trace=False):
+        """One euler_step in place; returns tau."""
+        t = C.c_double(0.0)
+        _check(self._ctx, load().idp_euler_step(self._ctx, 0.0 if tau is None else float(tau), int(trace),
+                                                C.byref(t)))
+        return t.value
+
+    def field(self, name):
+        which = FIELDS[name]
+        size = {"d": self.nnz, "alpha": self.n, "UL": 5 * self.n, "R": 5 * self.n, "bounds": 3 * self.n,
+                "P": 5 * self.nnz, "l4": self.nnz, "U5": 5 * self.n, "l5": self.nnz, "Ulim": 5 * self.n,
+                "tau_max": 1}[name]
+        out = np.empty(size)
+        _check(self._ctx, load().idp_get_field(self._ctx, which, _ptr(out)))
+        shapes = {"UL": (5, self.n), "R": (5, self.n), "bounds": (3, self.n), "P": (5, self.nnz),
+                  "U5": (5, self.n), "Ulim": (5, self.n)}
+        if name == "tau_max":
+            return float(out[0])
+        return out.reshape(shapes[name]) if name in shapes else out
+
+    def matrices(self):
+        n, nnz = self.n, self.nnz
+        rowptr = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(nnz, dtype=np.int64)
+        mij = np.empty(nnz)
+        cij = np.empty((3, nnz))
+        mi = np.empty(n)
+        _check(self._ctx, load().idp_get_matrices(self._ctx, _ptr(rowptr, _i64p), _ptr(col, _i64p), _ptr(mij),
+                                                  _ptr(cij), _ptr(mi)))
+        return rowptr, col, mij, cij, mi
+
+    def time(self):
+        t, tau = C.c_double(), C.c_double()
+        _check(self._ctx, load().idp_get_time(self._ctx, C.byref(t), C.byref(tau)))
+        return t.value, tau.value
+
+    def set_time(self, t):
+        _check(self._ctx, load().idp_set_time(self._ctx, float(t)))
+
+    def check_bounds(self):
+        rep = BoundsReport()
+        st = load().idp_check_bounds(self._ctx, C.byref(rep))
+        return st, rep
+
+    def launch_count(self):
+        return load().idp_launch_count(self._ctx)
+
+    def profile(self, enable=True):
+        """Starts (clearing earlier records) or stops per-kernel event timing."""
+        _check(self._ctx, load().idp_profile(self._ctx, int(enable)))
+
+    def profile_read(self):
+        """{kernel: (milliseconds, launches)} since profiling started."""
+        ms = np.zeros(len(KERNELS))
+        cnt = np.zeros(len(KERNELS), dtype=np.int64)
+        _check(self._ctx, load().idp_profile_read(self._ctx, _ptr(ms), _ptr(cnt, _i64p)))
+        return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(KERNELS)}
