@@ -105,7 +105,7 @@ idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device);
 /* Copies the current state out (5*n values); synchronises the stream. */
 idp_status idp_get_state(idp_ctx* ctx, double* U, int on_device);
 
-/* Enqueues n_steps SSP-RK3 steps (Sec. 3.5 eq. ssprk3), each three
+/* Enqueues n_steps SSP-RK3 steps (Sec. 3.6 eq. ssprk3), each three
  * euler_steps (Alg. 1) with tau_n fixed by the first one.  Returns without
  * waiting for the GPU; device-side errors (CFL, non-finite) are latched and
  * returned by idp_synchronize.  A step that meets a CFL violation leaves the
@@ -143,7 +143,7 @@ enum {
 };
 idp_status idp_get_field(idp_ctx* ctx, int which, double* out);
 
-/* Invariant check of the current state (Sec. 3.3, Sec. 3.8): counts nodes
+/* Invariant check of the current state (Sec. 3.3, Sec. 3.9): counts nodes
  * with rho <= 0, epsilon <= 0 or a non-finite value.  Synchronises.  Returns
  * IDP_ERR_BOUNDS when any count is non-zero. */
 typedef struct {

@@ -179,7 +179,7 @@ def euler_step(om: OracleMesh, U, tau=None, params=None, trace=False):
 
 
 def ssprk3_step(om: OracleMesh, U, params=None):
-    """One SSP-RK3 step (Sec. 3.5 eq. ssprk3); returns ``(U_new, tau, status)``."""
+    """One SSP-RK3 step (Sec. 3.6 eq. ssprk3); returns ``(U_new, tau, status)``."""
     prm = params or default_params()
     U = np.array(U, dtype=np.float64, order="C", copy=True)
     t = C.c_double(0.0)
@@ -201,7 +201,7 @@ def run(om: OracleMesh, U, n_steps, params=None):
 
 
 def lambda_max(n, Ui, Uj, gamma=1.4) -> float:
-    """lambda~_max(n, U_i, U_j) of Sec. 3.6."""
+    """lambda~_max(n, U_i, U_j) of Sec. 3.7."""
     n = np.ascontiguousarray(n, dtype=np.float64)
     Ui = np.ascontiguousarray(Ui, dtype=np.float64)
     Uj = np.ascontiguousarray(Uj, dtype=np.float64)
@@ -222,7 +222,7 @@ def psi(U, phi_min, gamma=1.4) -> float:
 
 
 def node_quantities(U, gamma=1.4):
-    """(p, c, phi, eta, eta'(5)) of a single state (Sec. 2, Sec. 3.7)."""
+    """(p, c, phi, eta, eta'(5)) of a single state (Sec. 2, Sec. 3.8)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     out = np.zeros(9)
     lib().orc_node_quantities(_p(U), gamma, _p(out))

@@ -190,7 +190,7 @@ static double harten_entropy(const double* U, double gamma) {
 }
 
 /* eta'(U) = (rho epsilon)^(-gamma/(gamma+1)) / (gamma+1) * (E, -m, rho),
- * derivative with respect to (rho, m, E) (Sec. 3.7; Reading A7). */
+ * derivative with respect to (rho, m, E) (Sec. 3.8; Reading A7). */
 static void harten_entropy_derivative(const double* U, double gamma, double* out) {
   const double s = pow(U[0] * internal_energy(U), -gamma / (gamma + 1.0)) / (gamma + 1.0);
   out[0] = s * U[4];
@@ -226,7 +226,7 @@ void orc_node_quantities(const double* U, double gamma, double* out) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Two-rarefaction maximum wavespeed bound, Sec. 3.6                         */
+/* Two-rarefaction maximum wavespeed bound, Sec. 3.7                         */
 /* ------------------------------------------------------------------------ */
 
 static double positive_part(double x) { return 0.5 * (fabs(x) + x); }
@@ -249,13 +249,13 @@ static state1d project(const double* n, const double* U, double gamma) {
   return s;
 }
 
-/* f(U, p) of the pressure function psi (Sec. 3.6). */
+/* f(U, p) of the pressure function psi (Sec. 3.7). */
 static double riemann_f(const state1d* s, double p, double gamma) {
   if (p >= s->p) return sqrt(2.0) * (p - s->p) / sqrt(s->rho * ((gamma + 1.0) * p + (gamma - 1.0) * s->p));
   return (pow(p / s->p, (gamma - 1.0) / (2.0 * gamma)) - 1.0) * 2.0 * s->c / (gamma - 1.0);
 }
 
-/* lambda~_max(n, U_i, U_j) of Sec. 3.6 with U_i as the left and U_j as the
+/* lambda~_max(n, U_i, U_j) of Sec. 3.7 with U_i as the left and U_j as the
  * right state. */
 double orc_lambda_max(const double* n, const double* Ui, const double* Uj, double gamma) {
   const state1d L = project(n, Ui, gamma), R = project(n, Uj, gamma);
@@ -277,7 +277,7 @@ double orc_lambda_max(const double* n, const double* Ui, const double* Uj, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Convex limiter, Sec. 3.8, Alg. 2 and Alg. 3                               */
+/* Convex limiter, Sec. 3.9, Alg. 2 and Alg. 3                               */
 /* ------------------------------------------------------------------------ */
 
 /* Psi(U) = rho^(gamma+1) (phi(U) - phi_min).  Since rho^(gamma+1) phi(U) =
@@ -444,7 +444,7 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
   double* Unext = (double*)malloc(sizeof(double) * NF * (size_t)n);
 
   /* Step 1: off-diagonal d_ij for j > i (Sec. 3.3) and the indicator alpha_i
-   * (Sec. 3.7); the indicator runs over all j in I(i) (Reading A2). */
+   * (Sec. 3.8); the indicator runs over all j in I(i) (Reading A2). */
 #pragma omp parallel for num_threads(nt) schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double ui[NF], uj[NF], Fi[NF][3], Fj[NF][3], c[3], cT[3], fi[NF], fj[NF], etap[NF];
@@ -515,7 +515,7 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
   const double dt = *tau;
 
   /* Step 3: low-order update via bar states (Sec. 3.3 eq. def-ubar, Reading
-   * A1), R_i (eq. high-order-final) and the local bounds (Sec. 3.8). */
+   * A1), R_i (eq. high-order-final) and the local bounds (Sec. 3.9). */
 #pragma omp parallel for num_threads(nt) schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double ui[NF], uj[NF], Fi[NF][3], Fj[NF][3], c[3], fi[NF], fj[NF], r[NF], ul[NF];
@@ -652,7 +652,7 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
 }
 
 /* ------------------------------------------------------------------------ */
-/* SSP-RK3, Sec. 3.5 eq. (ssprk3): tau fixed by the first stage               */
+/* SSP-RK3, Sec. 3.6 eq. (ssprk3): tau fixed by the first stage               */
 /* ------------------------------------------------------------------------ */
 int orc_ssprk3_step(const orc_mesh* M, const orc_params* prm, double* U, double* tau_out) {
   const int64_t n = M->n;

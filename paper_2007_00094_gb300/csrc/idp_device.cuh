@@ -1,6 +1,6 @@
 // Device building blocks of the stage for gamma = 7/5 (Sec. 2): powers with
-// fixed rational exponents, the two-rarefaction wavespeed bound (Sec. 3.6)
-// and the convex limiter (Sec. 3.8, Alg. 2 and Alg. 3), in FP64.
+// fixed rational exponents, the two-rarefaction wavespeed bound (Sec. 3.7)
+// and the convex limiter (Sec. 3.9, Alg. 2 and Alg. 3), in FP64.
 #pragma once
 #include <cstdint>
 
@@ -46,7 +46,7 @@ struct Side {
   double rho, inv_rho, mx, my, mz, p, c, pm, inv_p;
 };
 
-// lambda~_max(n, U_L, U_R) of Sec. 3.6.  For gamma = 7/5 the two-rarefaction
+// lambda~_max(n, U_L, U_R) of Sec. 3.7.  For gamma = 7/5 the two-rarefaction
 // pressure is p~* = ((c_L + c_R - (u_R - u_L)/5) / (c_L p_L^(-1/7) +
 // c_R p_R^(-1/7)))^7 (the printed form divided through by p_R^(1/7)); the
 // projection leaves the pressure unchanged (E~ - m~^2/(2 rho) = epsilon).

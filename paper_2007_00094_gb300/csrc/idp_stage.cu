@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) k_node(int64_t n, const double* __rest
 }
 
 // Step 1: d^L_ij for the edges this row owns (j > i) and the indicator
-// alpha_i (Sec. 3.7) over all j in I(i).
+// alpha_i (Sec. 3.8) over all j in I(i).
 __global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
                                                  const double* __restrict__ Q, double* __restrict__ d,
                                                  double* __restrict__ alpha, DeviceScalars* scal) {
@@ -193,7 +193,7 @@ __device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_m
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
 // (eq. high-order-final) and the local bounds rho_min, rho_max over
-// rho(Ubar_ij) and phi_min over phi(U_j), j in I(i) (Sec. 3.8).
+// rho(Ubar_ij) and phi_min over phi(U_j), j in I(i) (Sec. 3.9).
 __global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
                                                       const double* __restrict__ Q, const double* __restrict__ d,
                                                       const double* __restrict__ alpha, double* __restrict__ UL,
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kBlock) k_limiter_pass(DeviceGraph G, StageCon
 
 // Last limiter pass, boundary post-processing (slip walls drop the flagged
 // normal momentum components, inflow nodes take the inflow state) and the
-// SSP-RK3 blend (Sec. 3.5): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
+// SSP-RK3 blend (Sec. 3.6): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
 __global__ void __launch_bounds__(kBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                   const double* __restrict__ P, const double* __restrict__ l,
                                                   const double* __restrict__ Un, double* __restrict__ Uout,

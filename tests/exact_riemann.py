@@ -2,7 +2,7 @@
 
 Test-only pin for the oracle, independent of it: the star pressure is found
 by bisection on the monotone pressure function (not by the two-rarefaction
-bound of Sec. 3.6), and the self-similar solution is sampled from the wave
+bound of Sec. 3.7), and the self-similar solution is sampled from the wave
 structure (rarefaction fans, shocks, contact) in the usual way.
 """
 from __future__ import annotations

@@ -1,10 +1,10 @@
 """Pins for the oracle's pointwise building blocks.
 
-* lambda~_max (Sec. 3.6): equal-state closed form |u| + c, the orientation
+* lambda~_max (Sec. 3.7): equal-state closed form |u| + c, the orientation
   symmetry, and brute force against an exact Riemann solver (bisection for
   p*): the bound never falls below the exact maximum wavespeed and is exact
   when both waves are rarefactions.
-* Harten entropy derivative (Sec. 3.7, Reading A7) by central differences.
+* Harten entropy derivative (Sec. 3.8, Reading A7) by central differences.
 * Limiter (Alg. 2/3): the returned t keeps U + tP inside the local bounds,
   t = 1 whenever U + P is admissible, and t never exceeds the largest
   admissible t found by bisection.

@@ -1,10 +1,10 @@
-"""Pins for the oracle's euler_step (Alg. 1) and SSP-RK3 (Sec. 3.5).
+"""Pins for the oracle's euler_step (Alg. 1) and SSP-RK3 (Sec. 3.6).
 
 Each check compares the oracle with something other than itself: an identity
 of the method (conservation, symmetry of d_ij, skew P_ij, the low-order
 update written as eq. (low-order) instead of the bar-state form the oracle
 uses, the Neumann-series high-order update), an invariant (positivity and the
-local bounds of Sec. 3.8), consistency with -div f on smooth data, the exact
+local bounds of Sec. 3.9), consistency with -div f on smooth data, the exact
 Sod solution and the exact translated vortex.
 """
 import numpy as np
@@ -227,7 +227,7 @@ def _vortex_l1(n, n_threads, t_end=0.05):
 def test_vortex_converges(n_threads):
     """L1 density error against the exact translated vortex decreases at (at
     least) first order.  The vortex is isentropic, so phi_min equals phi
-    almost everywhere and the entropy bound of Sec. 3.8 clips the high-order
+    almost everywhere and the entropy bound of Sec. 3.9 clips the high-order
     update at every node; without the bound relaxation that the paper leaves
     to its reference [gnpt, Sec. 4.7] (Reading A14) the observed order stays
     near 1 (measured: 1.23 and 1.01 on 20 -> 40 -> 80 nodes across)."""
