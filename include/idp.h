@@ -177,6 +177,34 @@ enum {
 idp_status idp_profile(idp_ctx* ctx, int enable);
 idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches);
 
+/* Time-step bound without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory, such as a host framework that owns all device memory
+ * through its own pool, or code that is recording work into a CUDA graph,
+ * where cudaMalloc is not allowed.  Those callers cannot create an idp_ctx,
+ * which allocates, so they pass their own device arrays instead.
+ *
+ * Computes tau_max = min_i m_i / (-2 d_ii), the bound that idp_euler_step
+ * scales by c_cfl and reports as IDP_FIELD_TAU_MAX, for the state U:
+ *   n_nodes, nnz : sizes; 1 <= n_nodes <= IDP_NOALLOC_MAX_NODES, else IDP_ERR_ARG
+ *   rowptr, col  : device, CSR pattern (n_nodes+1, nnz), columns sorted per row
+ *   cij          : device, 3*nnz, c_ij component-major (as idp_get_matrices)
+ *   mi           : device, n_nodes lumped masses
+ *   U            : device, 5*n_nodes conserved state, admissible
+ *   tau_max      : device, 1 double written by the kernel
+ *   cuda_stream  : cudaStream_t (may be NULL); the call does not synchronise.
+ * It calls no cudaMalloc or cudaFree.  Its scratch is a fixed device array in
+ * the library (one partial minimum per 128 nodes, 128 KiB), which every GPU
+ * that loads the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  All calls share the array, so calls that overlap on
+ * the GPU (e.g. on two streams at once) race and give wrong results; the
+ * call clears what must start at zero itself. */
+#define IDP_NOALLOC_MAX_NODES 2097152
+idp_status idp_tau_max_noalloc(int64_t n_nodes, int64_t nnz, const int64_t* rowptr, const int64_t* col,
+                               const double* cij, const double* mi, const double* U, double* tau_max,
+                               void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

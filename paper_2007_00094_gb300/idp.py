@@ -30,7 +30,8 @@ FIELDS = {"d": 0, "alpha": 1, "UL": 2, "R": 3, "bounds": 4, "P": 5, "l4": 6, "U5
 EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error", "idp_status_string",
             "idp_upload_mesh_hex", "idp_mesh_info", "idp_get_matrices", "idp_init_state", "idp_get_state",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
-            "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read"]
+            "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc"]
+NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final"]
 
 
@@ -91,8 +92,17 @@ def load(path: str = LIB_PATH):
     L.idp_launch_count.restype = C.c_int64
     L.idp_profile.argtypes = [_vp, C.c_int]
     L.idp_profile_read.argtypes = [_vp, _dp, _i64p]
+    L.idp_tau_max_noalloc.argtypes = [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     _lib = L
     return L
+
+
+def idp_tau_max_noalloc(n_nodes, nnz, rowptr, col, cij, mi, U, tau_max, stream=None):
+    """tau_max = min_i m_i/(-2 d_ii) from caller-owned device arrays, without
+    any device allocation (see include/idp.h).  Array arguments are device
+    pointers (ints) or CUDA tensors; returns the idp_status code."""
+    ptrs = [a.data_ptr() if hasattr(a, "data_ptr") else int(a) for a in (rowptr, col, cij, mi, U, tau_max)]
+    return load().idp_tau_max_noalloc(int(n_nodes), int(nnz), *ptrs, _stream_handle(stream))
 
 
 def _ptr(a, t=_dp):
