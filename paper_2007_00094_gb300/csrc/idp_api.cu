@@ -24,6 +24,7 @@ struct idp_ctx {
   idp::StageConfig C{};
   std::vector<void*> allocations;
   double* check = nullptr;  // 5 doubles
+  unsigned long long* check_acc = nullptr;  // 5 words
   int64_t launches = 0;
   idp::Profiler prof;
 };
@@ -200,7 +201,7 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
       (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.UL, 5 * n)) || (st = dalloc(ctx, &B.R, 5 * n)) ||
       (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) || (st = dalloc(ctx, &B.l[0], ns)) ||
       (st = dalloc(ctx, &B.l[1], ns)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
-      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)))
+      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)) || (st = dalloc(ctx, &ctx->check_acc, 5)))
     return st;
   B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
@@ -395,7 +396,7 @@ idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
 idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out) {
   if (!ctx || !out) return IDP_ERR_ARG;
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
-  idp::launch_check_state(ctx->B.U, ctx->G.n, ctx->check, ctx->stream);
+  idp::launch_check_state(ctx->B.U, ctx->G.n, ctx->check, ctx->check_acc, ctx->stream);
   IDP_CUDA(ctx, cudaGetLastError());
   double h[5];
   IDP_CUDA(ctx, cudaMemcpyAsync(h, ctx->check, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));

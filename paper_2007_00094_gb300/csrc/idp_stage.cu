@@ -408,11 +408,23 @@ __global__ void __launch_bounds__(kBlock) k_final(DeviceGraph G, StageConfig C, 
   for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
 }
 
-__global__ void k_check_state(const double* __restrict__ U, int64_t n, double* out) {
-  __shared__ double smin[2][kBlock / 32];
-  __shared__ unsigned long long cnt[3];
-  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
-  __syncthreads();
+// Order-preserving map of doubles to unsigned 64-bit keys (negative values
+// reverse their bit order), so that atomicMin on keys is a min on values.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double from_order_key(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Invariant check of a state: counts of rho <= 0, eps <= 0 and non-finite
+// nodes, and the minima of rho and eps, accumulated with atomics into
+// acc = {count_rho, count_eps, count_nonfinite, key(rho_min), key(eps_min)}.
+__global__ void __launch_bounds__(kBlock) k_check_state(const double* __restrict__ U, int64_t n,
+                                                        unsigned long long* acc) {
   double rmin = INFINITY, emin = INFINITY;
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -437,25 +449,20 @@ __global__ void k_check_state(const double* __restrict__ U, int64_t n, double* o
     c2 += __shfl_xor_sync(0xffffffffu, c2, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    smin[0][threadIdx.x >> 5] = rmin;
-    smin[1][threadIdx.x >> 5] = emin;
-    atomicAdd(&cnt[0], c0);
-    atomicAdd(&cnt[1], c1);
-    atomicAdd(&cnt[2], c2);
+    if (c0) atomicAdd(&acc[0], c0);
+    if (c1) atomicAdd(&acc[1], c1);
+    if (c2) atomicAdd(&acc[2], c2);
+    atomicMin(&acc[3], order_key(rmin));
+    atomicMin(&acc[4], order_key(emin));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < kBlock / 32; ++w) {
-      smin[0][0] = fmin(smin[0][0], smin[0][w]);
-      smin[1][0] = fmin(smin[1][0], smin[1][w]);
-    }
-    // single-block launch: plain stores
-    out[0] = (double)cnt[0];
-    out[1] = (double)cnt[1];
-    out[2] = (double)cnt[2];
-    out[3] = smin[0][0];
-    out[4] = smin[1][0];
-  }
+}
+
+__global__ void k_check_finish(const unsigned long long* acc, double* out) {
+  out[0] = (double)acc[0];
+  out[1] = (double)acc[1];
+  out[2] = (double)acc[2];
+  out[3] = from_order_key(acc[3]);
+  out[4] = from_order_key(acc[4]);
 }
 
 }  // namespace
@@ -525,8 +532,14 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
   return launches;
 }
 
-void launch_check_state(const double* U, int64_t n, double* out, cudaStream_t s) {
-  k_check_state<<<1, kBlock, 0, s>>>(U, n, out);
+void launch_check_state(const double* U, int64_t n, double* out, unsigned long long* acc, cudaStream_t s) {
+  // counts start at 0, minimum keys at the largest key
+  cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(acc + 3, 0xff, 2 * sizeof(unsigned long long), s);
+  const int64_t blocks = (n + kBlock - 1) / kBlock;
+  const unsigned grid = (unsigned)(blocks < 152 * 8 ? blocks : 152 * 8);
+  k_check_state<<<grid, kBlock, 0, s>>>(U, n, acc);
+  k_check_finish<<<1, 1, 0, s>>>(acc, out);
 }
 
 }  // namespace idp

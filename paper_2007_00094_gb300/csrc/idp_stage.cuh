@@ -104,7 +104,7 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
 
 // Counts nodes with rho <= 0, epsilon <= 0, non-finite values; writes
 // {count_rho, count_eps, count_nonfinite} as doubles plus rho_min, eps_min
-// into out[0..4] (device memory).
-void launch_check_state(const double* U, int64_t n, double* out, cudaStream_t s);
+// into out[0..4] (device memory); acc is 5 words of device scratch.
+void launch_check_state(const double* U, int64_t n, double* out, unsigned long long* acc, cudaStream_t s);
 
 }  // namespace idp
