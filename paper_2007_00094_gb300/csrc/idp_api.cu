@@ -173,12 +173,14 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   idp_status st;
   int32_t *slice_ptr, *row_len, *col, *tpos, *bc;
   uint8_t* flags;
-  double *cx, *cy, *cz, *mij, *mi, *inv_mi, *lam;
+  double *cx, *cy, *cz, *mij, *mi, *inv_mi, *lam, *cn, *inv_cn, *csx, *csy, *csz;
   if ((st = upload(ctx, &slice_ptr, L.slice_ptr)) || (st = upload(ctx, &row_len, L.row_len)) ||
       (st = upload(ctx, &col, L.col)) || (st = upload(ctx, &tpos, L.tpos)) || (st = upload(ctx, &flags, L.flags)) ||
       (st = upload(ctx, &cx, L.cx)) || (st = upload(ctx, &cy, L.cy)) || (st = upload(ctx, &cz, L.cz)) ||
       (st = upload(ctx, &mij, L.mij)) || (st = upload(ctx, &mi, L.mi)) || (st = upload(ctx, &inv_mi, L.inv_mi)) ||
-      (st = upload(ctx, &lam, L.lam)) || (st = upload(ctx, &bc, L.bc)))
+      (st = upload(ctx, &lam, L.lam)) || (st = upload(ctx, &bc, L.bc)) || (st = upload(ctx, &cn, L.cn)) ||
+      (st = upload(ctx, &inv_cn, L.inv_cn)) || (st = upload(ctx, &csx, L.csx)) || (st = upload(ctx, &csy, L.csy)) ||
+      (st = upload(ctx, &csz, L.csz)))
     return st;
   G.slice_ptr = slice_ptr;
   G.row_len = row_len;
@@ -189,6 +191,11 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   G.cy = cy;
   G.cz = cz;
   G.mij = mij;
+  G.cn = cn;
+  G.inv_cn = inv_cn;
+  G.csx = csx;
+  G.csy = csy;
+  G.csz = csz;
   G.mi = mi;
   G.inv_mi = inv_mi;
   G.lam = lam;
@@ -197,7 +204,7 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   idp::StageBuffers& B = ctx->B;
   const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
   if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) ||
-      (st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) ||
+      (st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) || (st = dalloc(ctx, &B.dinv, ns)) ||
       (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.UL, 5 * n)) || (st = dalloc(ctx, &B.R, 5 * n)) ||
       (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) || (st = dalloc(ctx, &B.l[0], ns)) ||
       (st = dalloc(ctx, &B.l[1], ns)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||

@@ -6,21 +6,29 @@
 
 namespace idp {
 
-// x^(-1/k) for x > 0 by Newton's method on g(w) = x w^k - 1, from a
-// single-precision seed w0 = x^(-1/k) (the __powf intrinsic).  Each step
-// w <- w (k + 1 - x w^k) / k squares the relative error (times (k+1)/2), so
-// two steps take the ~1e-6 seed to full double precision.
+// w^K by repeated squaring (K = 5, 7, 12 in this file).
+template <int K>
+__device__ __forceinline__ double ipow(double w) {
+  if constexpr (K == 1) {
+    return w;
+  } else if constexpr (K % 2 == 0) {
+    const double h = ipow<K / 2>(w);
+    return h * h;
+  } else {
+    return ipow<K - 1>(w) * w;
+  }
+}
+
+// x^(-1/K) for x > 0.  A single-precision seed w0 = powf(x, -1/K) (relative
+// error below 3e-7) is corrected with the second-order series of
+// (1 - delta)^(-1/K) = 1 + delta/K + (K+1) delta^2/(2K^2) + O(delta^3), where
+// delta = 1 - x w0^K; the neglected term is ~delta^3 < 1e-17 for K <= 12.
 template <int K>
 __device__ __forceinline__ double inv_root(double x) {
-  double w = (double)__powf((float)x, -1.0f / (float)K);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    double wk = w;
-#pragma unroll
-    for (int q = 1; q < K; ++q) wk *= w;
-    w = w * ((double)(K + 1) - x * wk) * (1.0 / (double)K);
-  }
-  return w;
+  const double w0 = (double)powf((float)x, -1.0f / (float)K);
+  const double delta = 1.0 - x * ipow<K>(w0);
+  const double c1 = 1.0 / (double)K, c2 = (double)(K + 1) / (2.0 * (double)K * (double)K);
+  return fma(w0, fma(c2, delta, c1) * delta, w0);
 }
 
 // rho^(gamma+1) = rho^(12/5) = rho^3 * (rho^(-1/5))^3
@@ -50,7 +58,7 @@ struct Side {
 // pressure is p~* = ((c_L + c_R - (u_R - u_L)/5) / (c_L p_L^(-1/7) +
 // c_R p_R^(-1/7)))^7 (the printed form divided through by p_R^(1/7)); the
 // projection leaves the pressure unchanged (E~ - m~^2/(2 rho) = epsilon).
-// psi is evaluated at p_max, where only the side with the smaller pressure
+// psi is needed at p_max, where only the side with the smaller pressure
 // contributes (its shock branch); the other side's f vanishes.
 __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, const Side& L, const Side& R) {
   const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
@@ -64,8 +72,14 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   const double p_max = left_high ? L.p : R.p;
   const double p_low = left_high ? R.p : L.p;
   const double rho_low = left_high ? R.rho : L.rho;
-  const double psi = 1.4142135623730951 * (p_max - p_low) / sqrt(rho_low * (2.4 * p_max + 0.4 * p_low)) + (uR - uL);
-  const double p_star = psi < 0.0 ? p_tr : fmin(p_max, p_tr);
+  // psi(p_max) = A/B + du with A = sqrt(2)(p_max - p_low) >= 0 and
+  // B = sqrt(rho_low (2.4 p_max + 0.4 p_low)) > 0, so psi < 0 exactly when
+  // du < 0 and A^2 < du^2 B^2: the same decision without a square root or a
+  // division
+  const double du = uR - uL;
+  const double dp = p_max - p_low;
+  const bool psi_negative = du < 0.0 && 2.0 * dp * dp < du * du * (rho_low * (2.4 * p_max + 0.4 * p_low));
+  const double p_star = psi_negative ? p_tr : fmin(p_max, p_tr);
   const double k = 6.0 / 7.0;  // (gamma+1)/(2 gamma)
   const double lam1 = uL - L.c * sqrt(1.0 + k * fmax((p_star - L.p) * L.inv_p, 0.0));
   const double lam3 = uR + R.c * sqrt(1.0 + k * fmax((p_star - R.p) * R.inv_p, 0.0));

@@ -43,7 +43,9 @@ struct SellLayout {
   std::vector<int32_t> col, tpos; // n_slots (library ids / slot of the transposed entry)
   std::vector<uint8_t> flags;     // n_slots
   std::vector<double> cx, cy, cz, mij;  // n_slots
+  std::vector<double> cn, inv_cn;       // n_slots: |c_ij| and 1/|c_ij| (0 for c_ij = 0)
   std::vector<double> mi, inv_mi, lam;  // n (lam = 1 / (card I(i) - 1))
+  std::vector<double> csx, csy, csz;    // n: row sums sum_j c_ij (zero up to rounding)
   std::vector<int32_t> bc;              // n
   std::vector<int64_t> slot_of_entry;   // caller CSR entry -> slot
 };

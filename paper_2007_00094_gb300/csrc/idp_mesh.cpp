@@ -254,6 +254,11 @@ std::string build_sell(const HostMatrices& M, SellLayout& L) {
   L.cy.assign(slots, 0.0);
   L.cz.assign(slots, 0.0);
   L.mij.assign(slots, 0.0);
+  L.cn.assign(slots, 0.0);
+  L.inv_cn.assign(slots, 0.0);
+  L.csx.assign(n, 0.0);
+  L.csy.assign(n, 0.0);
+  L.csz.assign(n, 0.0);
   L.mi.resize(n);
   L.inv_mi.resize(n);
   L.lam.resize(n);
@@ -288,6 +293,14 @@ std::string build_sell(const HostMatrices& M, SellLayout& L) {
       L.cy[p] = M.cij[1][e];
       L.cz[p] = M.cij[2][e];
       L.mij[p] = M.mij[e];
+      // |c_ij| and 1/|c_ij| once here (n_ij = c_ij/|c_ij|, Sec. 3.2): on GB300
+      // a square root and a division cost more FP64 issue than loading them
+      const double nc = std::sqrt(L.cx[p] * L.cx[p] + L.cy[p] * L.cy[p] + L.cz[p] * L.cz[p]);
+      L.cn[p] = nc;
+      L.inv_cn[p] = nc > 0.0 ? 1.0 / nc : 0.0;
+      L.csx[r] += L.cx[p];
+      L.csy[r] += L.cy[p];
+      L.csz[r] += L.cz[p];
       uint8_t f = 0;
       if (j == r) f |= kEntryDiag;
       if (j > r) f |= kEntryUpper;

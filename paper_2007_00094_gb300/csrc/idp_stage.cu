@@ -81,15 +81,18 @@ __global__ void __launch_bounds__(kBlock) k_node(int64_t n, const double* __rest
   Q[kQPhi * n + i] = eps * r7;
 }
 
-// Step 1: d^L_ij for the edges this row owns (j > i) and the indicator
-// alpha_i (Sec. 3.8) over all j in I(i).
+// Step 1: d^L_ij for the edges this row owns (j > i), stored with 1/(2 d_ij),
+// and the indicator alpha_i (Sec. 3.8) over all j in I(i).  The flux
+// differences (f_j - f_i).c_ij computed for the indicator are stored (in the
+// P buffer, free until Step 4) for the bar states and R_i of Step 3.
 __global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
                                                  const double* __restrict__ Q, double* __restrict__ d,
+                                                 double* __restrict__ dinv, double* __restrict__ dF,
                                                  double* __restrict__ alpha, DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r == 0) scal->tau_min_bits = 0x7ff0000000000000ull;  // +inf, read by the next kernel
   if (r >= G.n) return;
-  const int64_t n = G.n;
+  const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
   const Side si = load_side(U, Q, n, r);
@@ -107,28 +110,34 @@ __global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __
     flux_dot(sj.mx, sj.my, sj.mz, sj.inv_rho, sj.p, h_j, cx, cy, cz, fj);
     flux_dot(si.mx, si.my, si.mz, si.inv_rho, si.p, h_i, cx, cy, cz, fi);
     a += (s_j - s_i) * fj[0];
-    b0 += fj[0] - fi[0];
-    b1 += fj[1] - fi[1];
-    b2 += fj[2] - fi[2];
-    b3 += fj[3] - fi[3];
-    b4 += fj[4] - fi[4];
+    double df[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      df[f] = fj[f] - fi[f];
+      dF[f * ns + p] = df[f];
+    }
+    b0 += df[0];
+    b1 += df[1];
+    b2 += df[2];
+    b3 += df[3];
+    b4 += df[4];
     if (fl & kEntryUpper) {
-      const double nc = sqrt(cx * cx + cy * cy + cz * cz);
+      const double nc = G.cn[p];
       double dij = 0.0;
       if (nc > 0.0) {
-        const double inv = 1.0 / nc;
+        const double inv = G.inv_cn[p];
         dij = lambda_max(cx * inv, cy * inv, cz * inv, si, sj) * nc;
       }
       if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
         const int64_t pt = G.tpos[p];
-        const double tx = G.cx[pt], ty = G.cy[pt], tz = G.cz[pt];
-        const double nt = sqrt(tx * tx + ty * ty + tz * tz);
+        const double nt = G.cn[pt];
         if (nt > 0.0) {
-          const double inv = 1.0 / nt;
-          dij = fmax(dij, lambda_max(tx * inv, ty * inv, tz * inv, sj, si) * nt);
+          const double inv = G.inv_cn[pt];
+          dij = fmax(dij, lambda_max(G.cx[pt] * inv, G.cy[pt] * inv, G.cz[pt] * inv, sj, si) * nt);
         }
       }
       d[p] = dij;
+      dinv[p] = dij != 0.0 ? 0.5 / dij : 0.0;
     }
   }
   // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
@@ -156,7 +165,8 @@ __device__ __forceinline__ double block_min(double v) {
 
 // Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
 // CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
-__global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restrict__ d, DeviceScalars* scal) {
+__global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restrict__ d, double* __restrict__ dinv,
+                                                 DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double cand = INFINITY;
   if (r < G.n) {
@@ -173,8 +183,10 @@ __global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restri
       }
       double v;
       if (j < r) {
-        v = d[G.tpos[p]];
+        const int64_t pt = G.tpos[p];
+        v = d[pt];
         d[p] = v;
+        dinv[p] = dinv[pt];
       } else {
         v = d[p];
       }
@@ -193,9 +205,13 @@ __device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_m
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
 // (eq. high-order-final) and the local bounds rho_min, rho_max over
-// rho(Ubar_ij) and phi_min over phi(U_j), j in I(i) (Sec. 3.9).
+// rho(Ubar_ij) and phi_min over phi(U_j), j in I(i) (Sec. 3.9).  With the
+// flux differences df_ij = (f_j - f_i).c_ij of Step 1,
+// Ubar_ij = (U_i + U_j)/2 - df_ij/(2 d_ij) and, since sum_j c_ij = s_i,
+// sum_j -f_j.c_ij = -sum_j df_ij - f_i.s_i (s_i is zero up to rounding).
 __global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
                                                       const double* __restrict__ Q, const double* __restrict__ d,
+                                                      const double* __restrict__ dinv, const double* __restrict__ dF,
                                                       const double* __restrict__ alpha, double* __restrict__ UL,
                                                       double* __restrict__ R, double* __restrict__ bnd,
                                                       DeviceScalars* scal, int tau_mode, int accumulate_time) {
@@ -212,42 +228,43 @@ __global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig
     }
   }
   if (r >= G.n) return;
-  const int64_t n = G.n;
+  const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
   double ui[kFields];
   load5(U, n, r, ui);
-  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
   const double a_i = alpha[r];
   const double two_tau_m = 2.0 * tau * G.inv_mi[r];
   double ul[kFields], rr[kFields];
+  {
+    double fs[kFields];  // f_i . s_i
+    flux_dot(ui[1], ui[2], ui[3], Q[kQInvRho * n + r], Q[kQP * n + r], Q[kQH * n + r], G.csx[r], G.csy[r],
+             G.csz[r], fs);
 #pragma unroll
-  for (int f = 0; f < kFields; ++f) {
-    ul[f] = ui[f];
-    rr[f] = 0.0;
+    for (int f = 0; f < kFields; ++f) {
+      ul[f] = ui[f];
+      rr[f] = -fs[f];
+    }
   }
   double rho_min = INFINITY, rho_max = -INFINITY, phi_min = INFINITY;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
-    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
     const double dij = d[p];
-    double uj[kFields];
+    double uj[kFields], df[kFields];
     load5(U, n, j, uj);
-    const double inv_rho_j = Q[kQInvRho * n + j], p_j = Q[kQP * n + j], h_j = Q[kQH * n + j];
-    double fj[kFields], fi[kFields];
-    flux_dot(uj[1], uj[2], uj[3], inv_rho_j, p_j, h_j, cx, cy, cz, fj);
-    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, cx, cy, cz, fi);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) df[f] = dF[f * ns + p];
     const double dH = dij * (a_i + alpha[j]) * 0.5;
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) rr[f] += -fj[f] + dH * (uj[f] - ui[f]);
+    for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * (uj[f] - ui[f]);
     if (dij != 0.0) {
-      const double inv2d = 0.5 / dij;
+      const double inv2d = dinv[p];
       const double coef = two_tau_m * dij;
       double ub[kFields];
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        ub[f] = 0.5 * (ui[f] + uj[f]) - (fj[f] - fi[f]) * inv2d;
+        ub[f] = 0.5 * (ui[f] + uj[f]) - df[f] * inv2d;
         ul[f] += coef * ub[f];
       }
       rho_min = fmin(rho_min, ub[0]);
@@ -498,11 +515,11 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
     ++launches;
   };
   run(kKNode, [&] { k_node<<<grid, kBlock, 0, s>>>(G.n, Uin, B.node, B.scal); });
-  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.alpha, B.scal); });
-  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, B.d, B.scal); });
+  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.scal); });
+  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, B.d, B.dinv, B.scal); });
   run(kKLowOrder, [&] {
-    k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.alpha, B.UL, B.R, B.bnd, B.scal, tau_mode,
-                                        accumulate_time ? 1 : 0);
+    k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
+                                        tau_mode, accumulate_time ? 1 : 0);
   });
   run(kKFluxLimit, [&] {
     k_flux_limit<<<grid, kBlock, 0, s>>>(G, C, Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], B.scal, tau_mode);

@@ -23,6 +23,11 @@ struct DeviceGraph {
   const double* cy;
   const double* cz;
   const double* mij;
+  const double* cn;      // |c_ij|
+  const double* inv_cn;  // 1/|c_ij|
+  const double* csx;     // row sums of c_ij
+  const double* csy;
+  const double* csz;
   const double* mi;
   const double* inv_mi;
   const double* lam;
@@ -52,11 +57,12 @@ struct StageBuffers {
   double* Us;    // RK stage state, 5n
   double* node;  // kNodeQ * n
   double* d;     // n_slots
+  double* dinv;  // n_slots: 1/(2 d_ij)
   double* alpha; // n
   double* UL;    // 5n
   double* R;     // 5n
   double* bnd;   // 3n
-  double* P;     // 5 * n_slots
+  double* P;     // 5 * n_slots (holds (f_j - f_i).c_ij from Step 1 to Step 3)
   double* l[2];  // n_slots each
   double* Uw[2]; // 5n each
   DeviceScalars* scal;
