@@ -131,8 +131,6 @@ __device__ __forceinline__ double limiter(const double* U, const double* P, doub
   if (rhoU + tR * rhoP > rho_max && rhoP != 0.0) tR = fabs(rho_max - rhoU) / fabs(rhoP);
   if (rhoU + tR * rhoP < rho_min && rhoP != 0.0) tR = fabs(rho_min - rhoU) / fabs(rhoP);
   tR = fmin(fmax(tR, 0.0), 1.0);
-  double r;
-  const double tol = prm.newton_tol * rho_eps_at(U, P, 0.0, &r);
   // Psi and rho^(gamma+1) at the current t_L (t_L = 0 at the start)
   double psiL = 0.0, powL = 0.0;
   bool haveL = false;
@@ -152,6 +150,8 @@ __device__ __forceinline__ double limiter(const double* U, const double* P, doub
       psiL = reL - phi_min * powL;
       haveL = true;
     }
+    // tolerance relative to rho eps(U) (Reading A11), only needed on this path
+    const double tol = prm.newton_tol * (U[0] * U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]));
     if (psiL <= tol) break;
     const double rhoL = U[0] + tL * P[0];
     const double dpsiL = drho_eps_at(U, P, tL) - phi_min * 2.4 * (powL / rhoL) * P[0];

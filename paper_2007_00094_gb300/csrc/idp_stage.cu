@@ -363,12 +363,16 @@ __global__ void __launch_bounds__(kBlock) k_limiter_pass(DeviceGraph G, StageCon
     }
     const double lk = fmin(lold[p], lold[G.tpos[p]]);
     double pij[kFields];
+    bool zero = true;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
       pij[f] = (1.0 - lk) * P[f * ns + p];
       P[f * ns + p] = pij[f];
+      zero &= pij[f] == 0.0;
     }
-    lnew[p] = limiter(u, pij, rmin, rmax, pmin, C.lim);
+    // A zero P_ij (the previous pass accepted it in full, so P_ji is zero
+    // too) is moved by no value of l_ij: skip the limiter.
+    lnew[p] = zero ? 1.0 : limiter(u, pij, rmin, rmax, pmin, C.lim);
   }
 }
 
