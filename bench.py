@@ -45,6 +45,82 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 NCU_TRAFFIC_BYTES = {}
 
 
+# Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
+# or write once; neighbour gathers counted once per node): bytes per stored
+# entry (slot) and per node.
+MIXED_BYTES = {"node": (0, 92), "edge": (45, 56), "diag": (18, 8), "low_order": (32, 164),
+               "flux_limit": (36, 116), "limiter_pass": (60, 112), "final": (36, 124)}
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of this machine (GB/s), else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _time_steps(solver, stream, steps, warmup):
+    """Warm-up, then steps SSP-RK3 steps timed with CUDA events; returns
+    (ms per step, per-kernel profile)."""
+    import torch
+
+    solver.step(warmup)
+    solver.synchronize()
+    solver.profile(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    solver.synchronize()
+    prof = solver.profile_read()
+    solver.profile(False)
+    return e0.elapsed_time(e1) / steps, prof
+
+
+def pattern_mixed(stream, args):
+    """FP32-mixed vs FP64 on the 3D Sod tube, 128^3 nodes, slip walls."""
+    import numpy as np
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+
+    mesh = W.sod_cube_mesh(args.sod_n)
+    U0 = W.sod_state(mesh)
+    out = {"config": {"workload": f"sod_tube_{args.sod_n}^3_slip_walls", "nodes": mesh.n_nodes,
+                      "steps_timed": args.pattern_steps, "warmup": args.warmup}}
+    states = {}
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+        s = Solver(mesh, stream=stream, precision=prec)
+        s.init_state(U0)
+        ms, prof = _time_steps(s, stream, args.pattern_steps, args.warmup)
+        states[name] = s.get_state()
+        entry = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                 "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
+        if prec == 1:
+            dom = max(prof, key=lambda k: prof[k][0])
+            dom_ms, dom_n = prof[dom]
+            per_slot, per_node = MIXED_BYTES[dom]
+            bytes_per_launch = per_slot * s.nnz + per_node * mesh.n_nodes
+            peak, src = _hbm_peak()
+            achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+            entry["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": achieved / peak, "traffic": None, "peak_source": src,
+                                 "work": f"{per_slot} B/entry x {s.nnz} + {per_node} B/node x {mesh.n_nodes}"}
+        out[name] = entry
+        s.close()
+    ref = states["fp64"]
+    scale = np.abs(ref).max(axis=1)
+    scale = np.where(scale > 1e-12 * scale.max(), scale, scale.max())
+    err = np.abs(states["fp32_mixed"] - ref).mean(axis=1) / scale
+    out["fp32_mixed"]["l1_error_vs_fp64"] = {f: float(e) for f, e in zip(["rho", "m_x", "m_y", "m_z", "E"], err)}
+    out["fp32_mixed"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_mixed"]["ms_per_step"]
+    return out
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,6 +269,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-m", type=int, default=60, help="mesh of the CPU oracle sample (h = 1/cpu_m)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the FP32-mixed / batched / adjoint lines")
+    ap.add_argument("--pattern-steps", type=int, default=5)
+    ap.add_argument("--sod-n", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -309,6 +388,8 @@ def main():
             "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items()},
             "clocks": clocks,
         }
+        if not args.no_patterns:
+            line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)

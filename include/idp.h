@@ -54,7 +54,9 @@ typedef struct {
   int newton_max;           /* Newton steps of Alg. 2 */
   double newton_tol;        /* Alg. 2 stops when Psi(t_L) <= newton_tol * rho*eps(U) */
   double newton_eps;        /* eps of Alg. 3 */
-  int precision;            /* IDP_PRECISION_FP64 */
+  int precision;            /* IDP_PRECISION_FP64, or IDP_PRECISION_MIXED: per-entry flux, wavespeed,
+                               antidiffusive-flux and limiter arithmetic in FP32; state, its
+                               accumulation, mass division, tau and the final limiter check in FP64 */
   int schedule;             /* kernel schedule id; 0 = default */
   int64_t barrier_spin_limit; /* iteration limit of any device-side wait */
 } idp_config;

@@ -9,6 +9,7 @@
 
 #include "idp.h"
 #include "idp_internal.h"
+#include "idp_mixed.cuh"
 #include "idp_stage.cuh"
 
 struct idp_ctx {
@@ -22,6 +23,9 @@ struct idp_ctx {
   idp::DeviceGraph G{};
   idp::StageBuffers B{};
   idp::StageConfig C{};
+  idp::MixedGraph MG{};
+  idp::MixedBuffers MB{};
+  bool mixed = false;
   std::vector<void*> allocations;
   double* check = nullptr;  // 5 doubles
   unsigned long long* check_acc = nullptr;  // 5 words
@@ -80,6 +84,16 @@ idp_status device_status(idp_ctx* ctx, bool clear) {
   return IDP_OK;
 }
 
+// One euler_step in the context's precision.
+int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int blend, int tau_mode, bool acc_time,
+           bool skip_write_on_error, bool trace) {
+  if (ctx->mixed)
+    return idp::launch_euler_step_mixed(ctx->G, ctx->MG, ctx->B, ctx->MB, ctx->C, Uin, Uout, Un, blend, tau_mode,
+                                        acc_time, skip_write_on_error, trace, ctx->stream, &ctx->prof);
+  return idp::launch_euler_step(ctx->G, ctx->B, ctx->C, Uin, Uout, Un, blend, tau_mode, acc_time, skip_write_on_error,
+                                trace, ctx->stream, &ctx->prof);
+}
+
 }  // namespace
 
 extern "C" {
@@ -121,7 +135,7 @@ idp_status idp_create(const idp_config* cfg, void* cuda_stream, idp_ctx** out) {
   if (cfg) c = *cfg; else idp_config_default(&c);
   if (c.gamma != 1.4) return IDP_ERR_ARG;
   if (!(c.cfl > 0.0 && c.cfl <= 1.0) || c.limiter_passes < 1 || c.newton_max < 0) return IDP_ERR_ARG;
-  if (c.precision != IDP_PRECISION_FP64) return IDP_ERR_ARG;
+  if (c.precision != IDP_PRECISION_FP64 && c.precision != IDP_PRECISION_MIXED) return IDP_ERR_ARG;
   idp_ctx* ctx = new (std::nothrow) idp_ctx;
   if (!ctx) return IDP_ERR_OOM;
   ctx->cfg = c;
@@ -131,6 +145,7 @@ idp_status idp_create(const idp_config* cfg, void* cuda_stream, idp_ctx** out) {
     delete ctx;
     return IDP_ERR_CUDA;
   }
+  ctx->mixed = c.precision == IDP_PRECISION_MIXED;
   ctx->C.cfl = c.cfl;
   ctx->C.limiter_passes = c.limiter_passes;
   ctx->C.lim.newton_max = c.newton_max;
@@ -203,16 +218,35 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
 
   idp::StageBuffers& B = ctx->B;
   const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
-  if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) ||
-      (st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) || (st = dalloc(ctx, &B.dinv, ns)) ||
-      (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.UL, 5 * n)) || (st = dalloc(ctx, &B.R, 5 * n)) ||
-      (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) || (st = dalloc(ctx, &B.l[0], ns)) ||
-      (st = dalloc(ctx, &B.l[1], ns)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
+  B = idp::StageBuffers{};
+  if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) || (st = dalloc(ctx, &B.UL, 5 * n)) ||
+      (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
       (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)) || (st = dalloc(ctx, &ctx->check_acc, 5)))
     return st;
+  if (!ctx->mixed) {
+    if ((st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) || (st = dalloc(ctx, &B.dinv, ns)) ||
+        (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.R, 5 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) ||
+        (st = dalloc(ctx, &B.l[0], ns)) || (st = dalloc(ctx, &B.l[1], ns)))
+      return st;
+    IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
+  } else {
+    auto to_float = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    float *fcx, *fcy, *fcz, *fm, *fcn, *finv, *fimi;
+    if ((st = upload(ctx, &fcx, to_float(L.cx))) || (st = upload(ctx, &fcy, to_float(L.cy))) ||
+        (st = upload(ctx, &fcz, to_float(L.cz))) || (st = upload(ctx, &fm, to_float(L.mij))) ||
+        (st = upload(ctx, &fcn, to_float(L.cn))) || (st = upload(ctx, &finv, to_float(L.inv_cn))) ||
+        (st = upload(ctx, &fimi, to_float(L.inv_mi))))
+      return st;
+    ctx->MG = idp::MixedGraph{fcx, fcy, fcz, fm, fcn, finv, fimi};
+    idp::MixedBuffers& X = ctx->MB;
+    if ((st = dalloc(ctx, &X.Uf, 5 * n)) || (st = dalloc(ctx, &X.Q, idp::kNodeQ * n)) || (st = dalloc(ctx, &X.d, ns)) ||
+        (st = dalloc(ctx, &X.dinv, ns)) || (st = dalloc(ctx, &X.P, 5 * ns)) || (st = dalloc(ctx, &X.l[0], ns)) ||
+        (st = dalloc(ctx, &X.l[1], ns)) || (st = dalloc(ctx, &X.alpha, n)) || (st = dalloc(ctx, &X.R, 5 * n)))
+      return st;
+    IDP_CUDA(ctx, cudaMemset(X.d, 0, sizeof(float) * ns));
+  }
   B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
-  IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
   ctx->has_mesh = true;
   return IDP_OK;
 }
@@ -297,12 +331,9 @@ idp_status idp_step(idp_ctx* ctx, int n_steps) {
   idp::StageBuffers& B = ctx->B;
   int64_t launches = 0;
   for (int s = 0; s < n_steps; ++s) {
-    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.U, B.Us, B.U, idp::kBlendNone, 0, true, false, false,
-                                       ctx->stream, &ctx->prof);
-    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.Us, B.Us, B.U, idp::kBlendStage2, 1, false, false, false,
-                                       ctx->stream, &ctx->prof);
-    launches += idp::launch_euler_step(ctx->G, B, ctx->C, B.Us, B.U, B.U, idp::kBlendStage3, 1, false, true, false,
-                                       ctx->stream, &ctx->prof);
+    launches += launch(ctx, B.U, B.Us, B.U, idp::kBlendNone, 0, true, false, false);
+    launches += launch(ctx, B.Us, B.Us, B.U, idp::kBlendStage2, 1, false, false, false);
+    launches += launch(ctx, B.Us, B.U, B.U, idp::kBlendStage3, 1, false, true, false);
   }
   ctx->launches = launches;
   IDP_CUDA(ctx, cudaGetLastError());
@@ -322,8 +353,7 @@ idp_status idp_euler_step(idp_ctx* ctx, double tau, int trace, double* tau_out) 
     ctx->has_trace = true;
   }
   if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(&B.scal->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  ctx->launches = idp::launch_euler_step(ctx->G, B, ctx->C, B.U, B.U, B.U, idp::kBlendNone, tau > 0.0 ? 1 : 0, false,
-                                         false, trace != 0, ctx->stream, &ctx->prof);
+  ctx->launches = launch(ctx, B.U, B.U, B.U, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false, trace != 0);
   IDP_CUDA(ctx, cudaGetLastError());
   if (tau_out) {
     IDP_CUDA(ctx, cudaMemcpyAsync(tau_out, &B.scal->tau, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -379,7 +409,34 @@ idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
       for (int64_t e = 0; e < nnz; ++e) out[c * nnz + e] = h[c * ns + L.slot_of_entry[e]];
     return IDP_OK;
   };
+  auto node_field_f = [&](const float* src, int comps) -> idp_status {
+    std::vector<float> h((size_t)comps * n);
+    IDP_CUDA(ctx, cudaMemcpyAsync(h.data(), src, sizeof(float) * comps * n, cudaMemcpyDeviceToHost, ctx->stream));
+    IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < comps; ++c)
+      for (int64_t i = 0; i < n; ++i) out[c * n + i] = h[c * n + L.perm[i]];
+    return IDP_OK;
+  };
+  auto slot_field_f = [&](const float* src, int comps) -> idp_status {
+    std::vector<float> h((size_t)comps * ns);
+    IDP_CUDA(ctx, cudaMemcpyAsync(h.data(), src, sizeof(float) * comps * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < comps; ++c)
+      for (int64_t e = 0; e < nnz; ++e) out[c * nnz + e] = h[c * ns + L.slot_of_entry[e]];
+    return IDP_OK;
+  };
   const bool traced = ctx->has_trace;
+  if (ctx->mixed) {
+    switch (which) {
+      case IDP_FIELD_D: return slot_field_f(ctx->MB.d, 1);
+      case IDP_FIELD_ALPHA: return node_field_f(ctx->MB.alpha, 1);
+      case IDP_FIELD_R: return node_field_f(ctx->MB.R, 5);
+      case IDP_FIELD_P:
+      case IDP_FIELD_L4:
+      case IDP_FIELD_L5: return fail(ctx, IDP_ERR_STATE, "field not kept in the mixed precision mode");
+      default: break;
+    }
+  }
   switch (which) {
     case IDP_FIELD_D: return slot_field(B.d, 1);
     case IDP_FIELD_ALPHA: return node_field(B.alpha, 1);

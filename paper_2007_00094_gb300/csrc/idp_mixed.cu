@@ -1,0 +1,631 @@
+// FP32-mixed euler_step (Alg. 1): per-edge flux, wavespeed, antidiffusive
+// flux and limiter-candidate arithmetic in FP32; the state, its accumulation,
+// the lumped-mass division, tau and the density interval in FP64.
+//
+// On GB300 an FP64 operation issues at 1/64 of the FP32 rate, so every
+// per-edge quantity is FP32 and FP64 touches each row a handful of times:
+//   * U^L_i = U_i + sum_j (2 tau d_ij/m_i)(Ubar_ij - U_i): the increments are
+//     summed in FP32 and added to the FP64 state once per row; likewise the
+//     limiter passes sum lambda_i l_ij P_ij in FP32.
+//   * lambda_max is evaluated in FP32 and multiplied by (1 + 1e-5) so that it
+//     stays above the FP64 bound (Sec. 3.7) despite FP32 rounding.
+//   * the limiter's line search (Alg. 2/3) runs in FP32 on the deviation of
+//     Psi from its FP64 value at t = 0 (computed once per row), shifted by a
+//     margin m = 1e-6 (|rho eps| + phi_min rho^(gamma+1)), several times the
+//     FP32 error of that deviation, so an accepted t keeps Psi >= 0 in FP64;
+//     the density interval cuts against FP64 gaps rho_max - rho(U), rho_min -
+//     rho(U) computed once per row, and a returned t whose FP32
+//     Psi is within a few margins of the bound is re-checked in FP64 (t = 0
+//     if it fails).
+#include <cfloat>
+
+#include "idp_internal.h"
+#include "idp_mixed.cuh"
+
+namespace idp {
+
+namespace {
+
+constexpr int kBlock = 128;
+constexpr float kLambdaSafety = 1.0f + 1e-5f;
+constexpr float kPsiMargin = 1e-6f;
+
+__device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
+  return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
+}
+
+template <typename T>
+__device__ __forceinline__ void load5(const T* U, int64_t n, int64_t i, T* u) {
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) u[f] = U[f * n + i];
+}
+
+struct SideF {
+  float rho, inv_rho, mx, my, mz, p, c, pm, inv_p;
+};
+
+__device__ __forceinline__ SideF load_side_f(const float* U, const float* Q, int64_t n, int64_t i) {
+  SideF s;
+  s.rho = U[i];
+  s.mx = U[n + i];
+  s.my = U[2 * n + i];
+  s.mz = U[3 * n + i];
+  s.inv_rho = Q[kQInvRho * n + i];
+  s.p = Q[kQP * n + i];
+  s.c = Q[kQC * n + i];
+  s.pm = Q[kQPm * n + i];
+  s.inv_p = Q[kQInvP * n + i];
+  return s;
+}
+
+// f(U) . c in FP32 with a pinned operation sequence (equal states give equal
+// fluxes bitwise, so flux differences of equal states vanish).
+__device__ __forceinline__ void flux_dot_f(float m1, float m2, float m3, float inv_rho, float p, float h, float cx,
+                                           float cy, float cz, float* f) {
+  const float mc = __fmaf_rn(m3, cz, __fmaf_rn(m2, cy, __fmul_rn(m1, cx)));
+  f[0] = mc;
+  f[1] = __fmaf_rn(p, cx, __fmul_rn(__fmul_rn(m1, inv_rho), mc));
+  f[2] = __fmaf_rn(p, cy, __fmul_rn(__fmul_rn(m2, inv_rho), mc));
+  f[3] = __fmaf_rn(p, cz, __fmul_rn(__fmul_rn(m3, inv_rho), mc));
+  f[4] = __fmul_rn(h, mc);
+}
+
+// Two-rarefaction wavespeed bound of Sec. 3.7 in FP32 (same algebra as the
+// FP64 version in idp_device.cuh), times the safety factor.
+__device__ __forceinline__ float lambda_max_f(float nx, float ny, float nz, const SideF& L, const SideF& R) {
+  const float uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
+  const float uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
+  float num = L.c + R.c - 0.2f * (uR - uL);
+  num = num > 0.0f ? num : 0.0f;
+  const float x = num / (L.c * L.pm + R.c * R.pm);
+  const float x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
+  const float p_tr = x6 * x;
+  const bool left_high = L.p >= R.p;
+  const float p_max = left_high ? L.p : R.p;
+  const float p_low = left_high ? R.p : L.p;
+  const float rho_low = left_high ? R.rho : L.rho;
+  const float du = uR - uL;
+  const float dp = p_max - p_low;
+  const bool psi_negative = du < 0.0f && 2.0f * dp * dp < du * du * (rho_low * (2.4f * p_max + 0.4f * p_low));
+  const float p_star = psi_negative ? p_tr : fminf(p_max, p_tr);
+  const float k = 6.0f / 7.0f;
+  const float lam1 = uL - L.c * sqrtf(1.0f + k * fmaxf((p_star - L.p) * L.inv_p, 0.0f));
+  const float lam3 = uR + R.c * sqrtf(1.0f + k * fmaxf((p_star - R.p) * R.inv_p, 0.0f));
+  return fmaxf(fmaxf(-lam1, 0.0f), fmaxf(lam3, 0.0f)) * kLambdaSafety;
+}
+
+// Per-row FP64 anchor of the limiter's Psi along U + tP: for the row state U
+// and the row's phi_min, Psi(0) = rho eps(U) - phi_min rho^(12/5) is exact in
+// FP64, and per entry only the deviation Psi(t) - Psi(0) is evaluated in FP32.
+// That removes the cancellation between rho E and |m|^2/2 and between rho eps
+// and phi_min rho^(12/5) from the FP32 arithmetic.
+struct PsiAnchor {
+  float u[kFields];  // FP32 copy of U
+  float psi0;        // Psi(0)
+  float rho0, inv_rho0;
+  float phi_pow0;    // phi_min rho^(12/5)
+  float margin;      // admissibility margin of the FP32 line search
+  float gap_max;     // rho_max - rho(U), rounded toward zero
+  float gap_min;     // rho_min - rho(U), rounded toward zero
+};
+
+__device__ __forceinline__ PsiAnchor make_anchor(const double* U, double rho_min, double rho_max, double phi_min) {
+  PsiAnchor a;
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) a.u[f] = (float)U[f];
+  const double re = U[0] * U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+  const double pp = U[0] > 0.0 ? phi_min * pow_12_5(U[0]) : 0.0;
+  a.psi0 = (float)(re - pp);
+  a.rho0 = (float)U[0];
+  a.inv_rho0 = (float)(1.0 / U[0]);
+  a.phi_pow0 = (float)pp;
+  // FP32 evaluation error of Psi(t) is a few 1e-7 of this scale
+  a.margin = kPsiMargin * (float)(fabs(re) + pp);
+  // density gaps in FP64, rounded toward zero so that FP32 cuts stay inside
+  a.gap_max = __double2float_rz(rho_max - U[0]);
+  a.gap_min = __double2float_rz(rho_min - U[0]);
+  return a;
+}
+
+// Psi(t) - margin and dPsi/dt along U + tP with the anchor:
+//   rho eps(U + tP) = rho eps(U) + t g + t^2 h,
+//   g = P_rho E + rho P_E - m.P_m,  h = P_rho P_E - |P_m|^2/2,
+//   rho(U + tP)^(12/5) = rho^(12/5) (1 + q),  q = (1 + t P_rho/rho)^(12/5) - 1.
+struct PsiLine {
+  float g, h, sr;  // sr = P_rho / rho
+};
+
+__device__ __forceinline__ PsiLine make_line(const PsiAnchor& a, const float* P) {
+  PsiLine L;
+  L.g = P[0] * a.u[4] + a.u[0] * P[4] - (a.u[1] * P[1] + a.u[2] * P[2] + a.u[3] * P[3]);
+  L.h = P[0] * P[4] - 0.5f * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
+  L.sr = P[0] * a.inv_rho0;
+  return L;
+}
+
+__device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, float t, float* dpsi) {
+  const float s = t * L.sr;  // > -1 inside the density interval
+  const float lg = log1pf(s);
+  const float q = expm1f(2.4f * lg);
+  if (dpsi) *dpsi = L.g + 2.0f * t * L.h - a.phi_pow0 * 2.4f * ((1.0f + q) / (1.0f + s)) * L.sr;
+  return a.psi0 + t * (L.g + t * L.h) - a.phi_pow0 * q - a.margin;
+}
+
+// limiter.compute of Alg. 2 for the mixed path.  U (FP64) is the row state,
+// P (FP32) the direction.  Returns t in [0, 1].
+__device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor& A, const float* P, double phi_min,
+                                               const LimiterParams& prm) {
+  // density interval (Reading A12) against the row's FP64 gaps: the cut
+  // t = |gap|/|rho(P)| is shrunk by 2^-22 to absorb the FP32 division, so
+  // rho(U) + t rho(P) stays inside [rho_min, rho_max]
+  const float rhoP = P[0];
+  float tR = 1.0f;
+  if (rhoP > A.gap_max && rhoP != 0.0f) tR = fabsf(A.gap_max) / fabsf(rhoP) * (1.0f - 2.384185791015625e-7f);
+  if (tR * rhoP < A.gap_min && rhoP != 0.0f) tR = fabsf(A.gap_min) / fabsf(rhoP) * (1.0f - 2.384185791015625e-7f);
+  tR = fminf(fmaxf(tR, 0.0f), 1.0f);
+  float tL = 0.0f;
+  const PsiLine L = make_line(A, P);
+  float psiL = 0.0f, dpsiL = 0.0f, psiAtL;
+  bool haveL = false, accepted = false;
+  for (int step = 0; step < prm.newton_max; ++step) {
+    float dpsiR;
+    const float psiR = psi_at(A, L, tR, &dpsiR);
+    if (psiR >= 0.0f) {
+      tL = tR;
+      psiAtL = psiR;
+      accepted = true;
+      break;
+    }
+    if (!haveL) {
+      psiL = psi_at(A, L, tL, &dpsiL);
+      haveL = true;
+    }
+    const float tol = (float)prm.newton_tol * (A.psi0 + A.phi_pow0);
+    if (psiL <= tol) break;
+    const float scaling = 1.0f / (tR - tL + FLT_EPSILON);
+    const float d12 = (psiR - psiL) * scaling;
+    const float d112 = (d12 - dpsiL) * scaling;
+    const float d122 = (dpsiR - d12) * scaling;
+    const float lamL = fmaxf(dpsiL * dpsiL - 4.0f * psiL * d112, 0.0f);
+    const float lamR = fmaxf(dpsiR * dpsiR - 4.0f * psiR * d122, 0.0f);
+    float nL = tL - 2.0f * psiL / (dpsiL - sqrtf(lamL));
+    float nR = tR - 2.0f * psiR / (dpsiR - sqrtf(lamR));
+    if (!(nL >= tL)) nL = tL;
+    if (!(nL <= tR)) nL = tR;
+    float dpsiN;
+    const float psiN = psi_at(A, L, nL, &dpsiN);
+    if (psiN >= 0.0f) {
+      psiL = psiN;
+      dpsiL = dpsiN;
+    } else {
+      nL = tL;
+    }
+    if (!(nR >= nL)) nR = nL;
+    if (!(nR <= tR)) nR = tR;
+    tL = nL;
+    tR = nR;
+  }
+  if (!accepted) psiAtL = haveL ? psiL : psi_at(A, L, tL, nullptr);
+  // final FP64 check of the entropy bound where the FP32 value is close to it
+  if (tL > 0.0f && psiAtL < 3.0f * A.margin) {
+    double V[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) V[f] = U[f] + (double)tL * (double)P[f];
+    const double re = V[0] * V[4] - 0.5 * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
+    const double pw = phi_min * pow_12_5(V[0]);
+    if (!(V[0] > 0.0) || re - pw < -1e-13 * (fabs(re) + fabs(pw))) tL = 0.0f;
+  }
+  return tL;
+}
+
+// Step 0: per-node quantities (FP32 copies) and an FP32 copy of the state.
+__global__ void __launch_bounds__(kBlock) k_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
+                                                   float* __restrict__ Uf, DeviceScalars* scal) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double u[kFields];
+  load5(U, n, i, u);
+  const double rho = u[0];
+  const double inv_rho = 1.0 / rho;
+  const double eps = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * inv_rho;
+  if (!(rho > 0.0) || !(eps > 0.0)) atomicOr(&scal->status, kStatusNotAdmissible);
+  const double p = 0.4 * eps;
+  const float pf = (float)p, rf = (float)rho, ef = (float)eps;
+  Q[kQInvRho * n + i] = (float)inv_rho;
+  Q[kQP * n + i] = pf;
+  Q[kQC * n + i] = sqrtf((float)(1.4 * p * inv_rho));
+  Q[kQPm * n + i] = powf(pf, -1.0f / 7.0f);
+  Q[kQInvP * n + i] = (float)(1.0 / p);
+  Q[kQS * n + i] = powf((float)(rho * eps), 5.0f / 12.0f) * (float)inv_rho;
+  Q[kQH * n + i] = (float)((u[4] + p) * inv_rho);
+  Q[kQPhi * n + i] = ef * powf(rf, -1.4f);
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) Uf[f * n + i] = (float)u[f];
+}
+
+// Step 1 in FP32: d_ij (upper edges) with 1/(2 d_ij), flux differences and alpha_i.
+__global__ void __launch_bounds__(kBlock) k_edge_m(DeviceGraph G, MixedGraph M, const float* __restrict__ U,
+                                                   const float* __restrict__ Q, float* __restrict__ d,
+                                                   float* __restrict__ dinv, float* __restrict__ dF,
+                                                   float* __restrict__ alpha, DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) scal->tau_min_bits = 0x7ff0000000000000ull;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const SideF si = load_side_f(U, Q, n, r);
+  const float Ei = U[4 * n + r];
+  const float s_i = Q[kQS * n + r], h_i = Q[kQH * n + r];
+  float a = 0.0f, b0 = 0.0f, b1 = 0.0f, b2 = 0.0f, b3 = 0.0f, b4 = 0.0f;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const uint8_t fl = G.flags[p];
+    const float cx = M.cx[p], cy = M.cy[p], cz = M.cz[p];
+    const SideF sj = load_side_f(U, Q, n, j);
+    const float s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
+    float fj[kFields], fi[kFields];
+    flux_dot_f(sj.mx, sj.my, sj.mz, sj.inv_rho, sj.p, h_j, cx, cy, cz, fj);
+    flux_dot_f(si.mx, si.my, si.mz, si.inv_rho, si.p, h_i, cx, cy, cz, fi);
+    a += (s_j - s_i) * fj[0];
+    float df[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      df[f] = fj[f] - fi[f];
+      dF[f * ns + p] = df[f];
+    }
+    b0 += df[0];
+    b1 += df[1];
+    b2 += df[2];
+    b3 += df[3];
+    b4 += df[4];
+    if (fl & kEntryUpper) {
+      const float nc = M.cn[p];
+      float dij = 0.0f;
+      if (nc > 0.0f) {
+        const float inv = M.inv_cn[p];
+        dij = lambda_max_f(cx * inv, cy * inv, cz * inv, si, sj) * nc;
+      }
+      if (!(fl & kEntrySkew)) {
+        const int64_t pt = G.tpos[p];
+        const float nt = M.cn[pt];
+        if (nt > 0.0f) {
+          const float inv = M.inv_cn[pt];
+          dij = fmaxf(dij, lambda_max_f(M.cx[pt] * inv, M.cy[pt] * inv, M.cz[pt] * inv, sj, si) * nt);
+        }
+      }
+      d[p] = dij;
+      dinv[p] = dij != 0.0f ? 0.5f / dij : 0.0f;
+    }
+  }
+  const float sc = s_i * si.inv_p * (1.0f / 6.0f);
+  const float e0 = sc * Ei, e1 = -sc * si.mx, e2 = -sc * si.my, e3 = -sc * si.mz, e4 = sc * si.rho;
+  const float num = a - (e0 * b0 + e1 * b1 + e2 * b2 + e3 * b3 + e4 * b4) + s_i * b0;
+  const float D = fabsf(a) + fabsf(e0 - s_i) * fabsf(b0) + fabsf(e1) * fabsf(b1) + fabsf(e2) * fabsf(b2) +
+                  fabsf(e3) * fabsf(b3) + fabsf(e4) * fabsf(b4);
+  alpha[r] = D > 0.0f ? fabsf(num) / D : 0.0f;
+}
+
+__device__ __forceinline__ double block_min(double v) {
+  __shared__ double red[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Step 2: lower half of d and 1/(2d), and the CFL bound min_i m_i/(-2 d_ii)
+// with d_ii summed in FP64.
+__global__ void __launch_bounds__(kBlock) k_diag_m(DeviceGraph G, float* __restrict__ d, float* __restrict__ dinv,
+                                                   DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double cand = INFINITY;
+  if (r < G.n) {
+    const int64_t base = slot_base(G, r);
+    const int len = G.row_len[r];
+    double sum = 0.0;
+    for (int k = 0; k < len; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      const int64_t j = G.col[p];
+      if (j == r) continue;
+      float v;
+      if (j < r) {
+        const int64_t pt = G.tpos[p];
+        v = d[pt];
+        d[p] = v;
+        dinv[p] = dinv[pt];
+      } else {
+        v = d[p];
+      }
+      sum += (double)v;
+    }
+    cand = G.mi[r] / (2.0 * sum);
+  }
+  cand = block_min(cand);
+  if (threadIdx.x == 0 && cand < INFINITY)
+    atomicMin(&scal->tau_min_bits, (unsigned long long)__double_as_longlong(cand));
+}
+
+__device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_mode, double cfl) {
+  return tau_mode == 0 ? cfl * __longlong_as_double((long long)scal->tau_min_bits) : scal->tau;
+}
+
+// Step 3: U^L_i = U_i + sum_j (2 tau d_ij/m_i)(Ubar_ij - U_i) with
+// Ubar_ij - U_i = (U_j - U_i)/2 - df_ij/(2 d_ij) summed in FP32 and added to
+// the FP64 state; bounds rho_i + min/max_j (Ubar_ij - U_i)_rho and phi_min;
+// R_i = -sum_j df_ij - f_i.s_i + sum_j d^H_ij (U_j - U_i) in FP32.
+__global__ void __launch_bounds__(kBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                        const float* __restrict__ Uf, const float* __restrict__ Q,
+                                                        const float* __restrict__ d, const float* __restrict__ dinv,
+                                                        const float* __restrict__ dF, const float* __restrict__ alpha,
+                                                        double* __restrict__ UL, float* __restrict__ R,
+                                                        double* __restrict__ bnd, DeviceScalars* scal, int tau_mode,
+                                                        int accumulate_time) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  if (r == 0) {
+    const double tmax = __longlong_as_double((long long)scal->tau_min_bits);
+    scal->tau_max = tmax;
+    if (tau_mode == 0) {
+      scal->tau = tau;
+      if (accumulate_time) scal->time += tau;
+    } else if (tau > tmax) {
+      atomicOr(&scal->status, kStatusCfl);
+    }
+  }
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  float ui[kFields];
+  load5(Uf, n, r, ui);
+  const float a_i = alpha[r];
+  const float two_tau_m = (float)(2.0 * tau * G.inv_mi[r]);
+  float inc[kFields], rr[kFields];
+  {
+    float fs[kFields];
+    flux_dot_f(ui[1], ui[2], ui[3], Q[kQInvRho * n + r], Q[kQP * n + r], Q[kQH * n + r], (float)G.csx[r],
+               (float)G.csy[r], (float)G.csz[r], fs);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      inc[f] = 0.0f;
+      rr[f] = -fs[f];
+    }
+  }
+  float dmin = 0.0f, dmax = 0.0f, phi_min = INFINITY;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const float dij = d[p];
+    float diff[kFields], df[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      diff[f] = Uf[f * n + j] - ui[f];
+      df[f] = dF[f * ns + p];
+    }
+    const float dH = dij * (a_i + alpha[j]) * 0.5f;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * diff[f];
+    if (dij != 0.0f && j != r) {
+      const float inv2d = dinv[p];
+      const float coef = two_tau_m * dij;
+      float db[kFields];
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        db[f] = 0.5f * diff[f] - df[f] * inv2d;
+        inc[f] += coef * db[f];
+      }
+      dmin = fminf(dmin, db[0]);
+      dmax = fmaxf(dmax, db[0]);
+    }
+    phi_min = fminf(phi_min, Q[kQPhi * n + j]);
+  }
+  const double rho_i = U[r];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    UL[f * n + r] = U[f * n + r] + (double)inc[f];
+    R[f * n + r] = rr[f];
+  }
+  bnd[r] = rho_i + (double)dmin;
+  bnd[n + r] = rho_i + (double)dmax;
+  bnd[2 * n + r] = (double)phi_min;
+}
+
+// Step 4 in FP32: P_ij and the first limiter values.
+__global__ void __launch_bounds__(kBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
+                                                         const float* __restrict__ Uf, const float* __restrict__ d,
+                                                         const float* __restrict__ alpha, const double* __restrict__ UL,
+                                                         const float* __restrict__ R, const double* __restrict__ bnd,
+                                                         float* __restrict__ P, float* __restrict__ l,
+                                                         const DeviceScalars* scal, int tau_mode) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  float ui[kFields], ri[kFields];
+  double ul[kFields];
+  load5(Uf, n, r, ui);
+  load5(R, n, r, ri);
+  load5(UL, n, r, ul);
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const PsiAnchor anchor = make_anchor(ul, rmin, rmax, pmin);
+  const float a_i = alpha[r];
+  const float inv_mi = (float)G.inv_mi[r];
+  const float scale = (float)(tau * G.inv_mi[r] * (double)(len - 1));
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) P[f * ns + p] = 0.0f;
+      l[p] = 0.0f;
+      continue;
+    }
+    float pij[kFields];
+    const float m = M.mij[p];
+    const float b_ij = -m * M.inv_mi[j];
+    const float b_ji = -m * inv_mi;
+    const float dij = d[p];
+    const float dd = dij * (a_i + alpha[j]) * 0.5f - dij;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = scale * (b_ij * R[f * n + j] - b_ji * ri[f] + dd * (Uf[f * n + j] - ui[f]));
+      P[f * ns + p] = pij[f];
+    }
+    l[p] = limiter_mixed(ul, anchor, pij, pmin, C.lim);
+  }
+}
+
+// Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
+// FP32, added to FP64), P_ij <- (1 - min) P_ij and new l_ij.
+__global__ void __launch_bounds__(kBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                           double* __restrict__ Unext, float* __restrict__ P,
+                                                           const float* __restrict__ lold, float* __restrict__ lnew,
+                                                           const double* __restrict__ bnd) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const float lam = (float)G.lam[r];
+  float inc[kFields] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const float w = lam * fminf(lold[p], lold[G.tpos[p]]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) inc[f] += w * P[f * ns + p];
+  }
+  double u[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    u[f] = Ucur[f * n + r] + (double)inc[f];
+    Unext[f * n + r] = u[f];
+  }
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const PsiAnchor anchor = make_anchor(u, rmin, rmax, pmin);
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) {
+      lnew[p] = 0.0f;
+      continue;
+    }
+    const float lk = fminf(lold[p], lold[G.tpos[p]]);
+    float pij[kFields];
+    bool zero = true;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = (1.0f - lk) * P[f * ns + p];
+      P[f * ns + p] = pij[f];
+      zero &= pij[f] == 0.0f;
+    }
+    lnew[p] = zero ? 1.0f : limiter_mixed(u, anchor, pij, pmin, C.lim);
+  }
+}
+
+// Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
+__global__ void __launch_bounds__(kBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                    const float* __restrict__ P, const float* __restrict__ l,
+                                                    const double* __restrict__ Un, double* __restrict__ Uout,
+                                                    double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+                                                    int skip_write_on_error) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const float lam = (float)G.lam[r];
+  float inc[kFields] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const float w = lam * fminf(l[p], l[G.tpos[p]]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) inc[f] += w * P[f * ns + p];
+  }
+  double u[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) u[f] = Ucur[f * n + r] + (double)inc[f];
+  if (Ulim) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) Ulim[f * n + r] = u[f];
+  }
+  const int bc = G.bc[r];
+  if (bc & 8) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) u[f] = C.inflow[f];
+  } else {
+    if (bc & 1) u[1] = 0.0;
+    if (bc & 2) u[2] = 0.0;
+    if (bc & 4) u[3] = 0.0;
+  }
+  double out[kFields];
+  bool finite = true;
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    double v = u[f];
+    if (blend == kBlendStage2) v = 0.75 * Un[f * n + r] + 0.25 * u[f];
+    if (blend == kBlendStage3) v = (1.0 / 3.0) * Un[f * n + r] + (2.0 / 3.0) * u[f];
+    out[f] = v;
+    finite &= isfinite(v);
+  }
+  if (!finite) atomicOr(&scal->status, kStatusNonFinite);
+  if (skip_write_on_error && *(volatile int*)&scal->status != 0) return;
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
+}
+
+}  // namespace
+
+int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B, const MixedBuffers& X,
+                            const StageConfig& C, const double* Uin, double* Uout, const double* Un, int blend,
+                            int tau_mode, bool accumulate_time, bool skip_write_on_error, bool trace, cudaStream_t s,
+                            Profiler* prof) {
+  const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
+  const bool p = prof && prof->enabled;
+  int launches = 0;
+  auto run = [&](int id, auto&& launch) {
+    if (p) prof->begin(id, s);
+    launch();
+    if (p) prof->end(s);
+    ++launches;
+  };
+  run(kKNode, [&] { k_node_m<<<grid, kBlock, 0, s>>>(G.n, Uin, X.Q, X.Uf, B.scal); });
+  run(kKEdge, [&] { k_edge_m<<<grid, kBlock, 0, s>>>(G, M, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.scal); });
+  run(kKDiag, [&] { k_diag_m<<<grid, kBlock, 0, s>>>(G, X.d, X.dinv, B.scal); });
+  run(kKLowOrder, [&] {
+    k_low_order_m<<<grid, kBlock, 0, s>>>(G, C, Uin, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.UL, X.R, B.bnd, B.scal,
+                                          tau_mode, accumulate_time ? 1 : 0);
+  });
+  run(kKFluxLimit, [&] {
+    k_flux_limit_m<<<grid, kBlock, 0, s>>>(G, M, C, X.Uf, X.d, X.alpha, B.UL, X.R, B.bnd, X.P, X.l[0], B.scal,
+                                           tau_mode);
+  });
+  const double* cur = B.UL;
+  int lbuf = 0, wbuf = 0;
+  for (int pass = 1; pass < C.limiter_passes; ++pass) {
+    double* next = B.Uw[wbuf];
+    run(kKLimiterPass,
+        [&] { k_limiter_pass_m<<<grid, kBlock, 0, s>>>(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd); });
+    if (trace && pass == 1) cudaMemcpyAsync(B.tU5, next, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
+    cur = next;
+    wbuf ^= 1;
+    lbuf ^= 1;
+  }
+  run(kKFinal, [&] {
+    k_final_m<<<grid, kBlock, 0, s>>>(G, C, cur, X.P, X.l[lbuf], Un, Uout, trace ? B.tUlim : nullptr, B.scal, blend,
+                                      skip_write_on_error ? 1 : 0);
+  });
+  return launches;
+}
+
+}  // namespace idp
