@@ -61,14 +61,15 @@ def _hbm_peak():
         return 6800.0, "fallback"
 
 
-def _time_steps(solver, stream, steps, warmup):
+def _time_steps(solver, stream, steps, warmup, profile=True):
     """Warm-up, then steps SSP-RK3 steps timed with CUDA events; returns
-    (ms per step, per-kernel profile)."""
+    (ms per step, per-kernel profile or None)."""
     import torch
 
     solver.step(warmup)
     solver.synchronize()
-    solver.profile(True)
+    if profile:
+        solver.profile(True)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -76,9 +77,35 @@ def _time_steps(solver, stream, steps, warmup):
     solver.step(steps)
     e1.record(stream)
     solver.synchronize()
-    prof = solver.profile_read()
-    solver.profile(False)
+    prof = None
+    if profile:
+        prof = solver.profile_read()
+        solver.profile(False)
     return e0.elapsed_time(e1) / steps, prof
+
+
+def pattern_batched(stream, args):
+    """256 independent Riemann problems on slip-walled cubes of random size,
+    advanced together (per-instance tau_n); schedule chosen by the autotuner."""
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+
+    parts = W.random_riemann_batch(n_instances=args.batch_instances, side_range=(8, 48), seed=4)
+    mesh, off, U0 = W.concat_meshes([m for m, _ in parts], [u for _, u in parts])
+    del parts
+    out = {"config": {"workload": f"{args.batch_instances}_riemann_cubes_sides_8-48_seed4", "nodes": mesh.n_nodes,
+                      "instances": args.batch_instances, "steps_timed": args.pattern_steps, "warmup": args.warmup}}
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+        s = Solver(mesh, stream=stream, precision=prec)
+        s.set_instances(off)
+        s.init_state(U0)
+        block, graph, ms_tuned = s.autotune(steps=1)
+        ms, _ = _time_steps(s, stream, args.pattern_steps, args.warmup, profile=False)
+        out[name] = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "schedule": {"block": block, "cuda_graph": graph, "autotune_ms_per_step": ms_tuned},
+                     "gpu_launches_per_step": 21}
+        s.close()
+    return out
 
 
 def pattern_mixed(stream, args):
@@ -272,6 +299,7 @@ def main():
     ap.add_argument("--no-patterns", action="store_true", help="skip the FP32-mixed / batched / adjoint lines")
     ap.add_argument("--pattern-steps", type=int, default=5)
     ap.add_argument("--sod-n", type=int, default=128)
+    ap.add_argument("--batch-instances", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -389,7 +417,7 @@ def main():
             "clocks": clocks,
         }
         if not args.no_patterns:
-            line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args)}
+            line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)

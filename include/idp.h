@@ -179,6 +179,29 @@ enum {
 idp_status idp_profile(idp_ctx* ctx, int enable);
 idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches);
 
+/* Many independent instances in one context (SURVEY batching pattern): the
+ * uploaded mesh is the union of instance meshes whose nodes occupy the
+ * contiguous ranges [node_offsets[k], node_offsets[k+1]) (n_instances + 1
+ * host values, 0 first, n_nodes last) and share no matrix entry (else
+ * IDP_ERR_ARG).  Every instance then takes its own tau_n = c_cfl min over its
+ * nodes of m_i/(-2 d_ii) (Sec. 3.3) and keeps its own time; all instances
+ * advance in the same kernel launches.  Call after idp_upload_mesh_hex;
+ * synchronises. */
+idp_status idp_set_instances(idp_ctx* ctx, int64_t n_instances, const int64_t* node_offsets);
+/* Per-instance time and last tau_n (host arrays of n_instances, either may be
+ * NULL); synchronises. */
+idp_status idp_get_instance_times(idp_ctx* ctx, double* t, double* last_tau);
+
+/* Launch schedule of the stage kernels: block_size 64, 128 or 256 threads
+ * (one row per thread), and use_graph != 0 to capture one SSP-RK3 step in a
+ * CUDA graph on first use and replay it in idp_step (per-kernel profiling
+ * then runs without the graph).  Results do not depend on the schedule. */
+idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph);
+/* Times every schedule for `steps` SSP-RK3 steps on the current state, keeps
+ * the fastest and restores the state and clocks; writes the choice and its
+ * milliseconds per step (any output pointer may be NULL); synchronises. */
+idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, double* ms_per_step);
+
 /* Time-step bound without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory, such as a host framework that owns all device memory

@@ -31,6 +31,14 @@ struct idp_ctx {
   unsigned long long* check_acc = nullptr;  // 5 words
   int64_t launches = 0;
   idp::Profiler prof;
+  // per-instance device state (one instance unless idp_set_instances)
+  std::vector<void*> inst_allocs;
+  // schedule: block size of the stage kernels and CUDA-graph replay of idp_step
+  int block = 128;
+  bool use_graph = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;
 };
 
 namespace {
@@ -67,9 +75,58 @@ idp_status upload(idp_ctx* ctx, T** p, const std::vector<T>& v) {
   return IDP_OK;
 }
 
+void drop_graph(idp_ctx* ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  ctx->graph_exec = nullptr;
+}
+
+void free_instances(idp_ctx* ctx) {
+  for (void* p : ctx->inst_allocs) cudaFree(p);
+  ctx->inst_allocs.clear();
+}
+
 void free_all(idp_ctx* ctx) {
+  drop_graph(ctx);
+  free_instances(ctx);
   for (void* p : ctx->allocations) cudaFree(p);
   ctx->allocations.clear();
+}
+
+// Per-instance tau, time, bound and reduction word for n_inst instances;
+// inst (host, per library row) may be empty for a single instance.
+idp_status alloc_instances(idp_ctx* ctx, int64_t n_inst, const std::vector<int32_t>& inst) {
+  drop_graph(ctx);
+  free_instances(ctx);
+  auto get = [&](void** p, size_t bytes) -> idp_status {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, IDP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->inst_allocs.push_back(*p);
+    return IDP_OK;
+  };
+  void *tau, *time, *tmax, *tmin, *ins = nullptr;
+  idp_status st;
+  if ((st = get(&tau, sizeof(double) * n_inst)) || (st = get(&time, sizeof(double) * n_inst)) ||
+      (st = get(&tmax, sizeof(double) * n_inst)) || (st = get(&tmin, sizeof(unsigned long long) * n_inst)))
+    return st;
+  if (!inst.empty()) {
+    if ((st = get(&ins, sizeof(int32_t) * inst.size()))) return st;
+    IDP_CUDA(ctx, cudaMemcpy(ins, inst.data(), sizeof(int32_t) * inst.size(), cudaMemcpyHostToDevice));
+  }
+  IDP_CUDA(ctx, cudaMemset(tau, 0, sizeof(double) * n_inst));
+  IDP_CUDA(ctx, cudaMemset(time, 0, sizeof(double) * n_inst));
+  IDP_CUDA(ctx, cudaMemset(tmax, 0, sizeof(double) * n_inst));
+  IDP_CUDA(ctx, cudaMemset(tmin, 0, sizeof(unsigned long long) * n_inst));
+  idp::DeviceGraph& G = ctx->G;
+  G.n_inst = n_inst;
+  G.inst = static_cast<const int32_t*>(ins);
+  G.tau = static_cast<double*>(tau);
+  G.time = static_cast<double*>(time);
+  G.tau_max = static_cast<double*>(tmax);
+  G.tau_min = static_cast<unsigned long long*>(tmin);
+  return IDP_OK;
 }
 
 idp_status device_status(idp_ctx* ctx, bool clear) {
@@ -86,12 +143,45 @@ idp_status device_status(idp_ctx* ctx, bool clear) {
 
 // One euler_step in the context's precision.
 int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int blend, int tau_mode, bool acc_time,
-           bool skip_write_on_error, bool trace) {
+           bool skip_write_on_error, bool trace, cudaStream_t s, idp::Profiler* prof) {
   if (ctx->mixed)
     return idp::launch_euler_step_mixed(ctx->G, ctx->MG, ctx->B, ctx->MB, ctx->C, Uin, Uout, Un, blend, tau_mode,
-                                        acc_time, skip_write_on_error, trace, ctx->stream, &ctx->prof);
+                                        acc_time, skip_write_on_error, trace, s, prof, ctx->block);
   return idp::launch_euler_step(ctx->G, ctx->B, ctx->C, Uin, Uout, Un, blend, tau_mode, acc_time, skip_write_on_error,
-                                trace, ctx->stream, &ctx->prof);
+                                trace, s, prof, ctx->block);
+}
+
+// The three euler_steps of one SSP-RK3 step (eq. ssprk3) on stream s.
+int64_t launch_rk3(idp_ctx* ctx, cudaStream_t s, idp::Profiler* prof) {
+  idp::StageBuffers& B = ctx->B;
+  int64_t n = 0;
+  n += launch(ctx, B.U, B.Us, B.U, idp::kBlendNone, 0, true, false, false, s, prof);
+  n += launch(ctx, B.Us, B.Us, B.U, idp::kBlendStage2, 1, false, false, false, s, prof);
+  n += launch(ctx, B.Us, B.U, B.U, idp::kBlendStage3, 1, false, true, false, s, prof);
+  return n;
+}
+
+// Captures one SSP-RK3 step into a CUDA graph (on a private stream; the
+// legacy default stream cannot be captured) and instantiates it.
+idp_status build_graph(idp_ctx* ctx) {
+  drop_graph(ctx);
+  if (!ctx->cap_stream) IDP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  IDP_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  ctx->graph_launches = launch_rk3(ctx, ctx->cap_stream, nullptr);
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, IDP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graph_exec = nullptr;
+    return fail(ctx, IDP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return IDP_OK;
 }
 
 }  // namespace
@@ -160,6 +250,7 @@ void idp_destroy(idp_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->prof.clear();
   free_all(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 
@@ -247,6 +338,7 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   }
   B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
+  if ((st = alloc_instances(ctx, 1, std::vector<int32_t>()))) return st;
   ctx->has_mesh = true;
   return IDP_OK;
 }
@@ -328,12 +420,16 @@ idp_status idp_step(idp_ctx* ctx, int n_steps) {
   if (!ctx) return IDP_ERR_ARG;
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
   if (n_steps < 0) return fail(ctx, IDP_ERR_ARG, "negative step count");
-  idp::StageBuffers& B = ctx->B;
   int64_t launches = 0;
-  for (int s = 0; s < n_steps; ++s) {
-    launches += launch(ctx, B.U, B.Us, B.U, idp::kBlendNone, 0, true, false, false);
-    launches += launch(ctx, B.Us, B.Us, B.U, idp::kBlendStage2, 1, false, false, false);
-    launches += launch(ctx, B.Us, B.U, B.U, idp::kBlendStage3, 1, false, true, false);
+  if (ctx->use_graph && !ctx->prof.enabled) {
+    if (!ctx->graph_exec) {
+      idp_status st = build_graph(ctx);
+      if (st != IDP_OK) return st;
+    }
+    for (int s = 0; s < n_steps; ++s) IDP_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    launches = ctx->graph_launches * n_steps;
+  } else {
+    for (int s = 0; s < n_steps; ++s) launches += launch_rk3(ctx, ctx->stream, &ctx->prof);
   }
   ctx->launches = launches;
   IDP_CUDA(ctx, cudaGetLastError());
@@ -352,11 +448,15 @@ idp_status idp_euler_step(idp_ctx* ctx, double tau, int trace, double* tau_out) 
       return st;
     ctx->has_trace = true;
   }
-  if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(&B.scal->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-  ctx->launches = launch(ctx, B.U, B.U, B.U, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false, trace != 0);
+  if (tau > 0.0) {
+    std::vector<double> t(ctx->G.n_inst, tau);
+    IDP_CUDA(ctx, cudaMemcpy(ctx->G.tau, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+  }
+  ctx->launches = launch(ctx, B.U, B.U, B.U, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false, trace != 0,
+                         ctx->stream, &ctx->prof);
   IDP_CUDA(ctx, cudaGetLastError());
   if (tau_out) {
-    IDP_CUDA(ctx, cudaMemcpyAsync(tau_out, &B.scal->tau, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    IDP_CUDA(ctx, cudaMemcpyAsync(tau_out, ctx->G.tau, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   }
   return device_status(ctx, true);
 }
@@ -372,19 +472,101 @@ idp_status idp_synchronize(idp_ctx* ctx) {
 
 idp_status idp_get_time(idp_ctx* ctx, double* t, double* last_tau) {
   if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
-  idp::DeviceScalars s;
-  IDP_CUDA(ctx, cudaMemcpyAsync(&s, ctx->B.scal, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
+  if (t) IDP_CUDA(ctx, cudaMemcpyAsync(t, ctx->G.time, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (last_tau) IDP_CUDA(ctx, cudaMemcpyAsync(last_tau, ctx->G.tau, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (t) *t = s.time;
-  if (last_tau) *last_tau = s.tau;
   return IDP_OK;
 }
 
 idp_status idp_set_time(idp_ctx* ctx, double t) {
   if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
-  IDP_CUDA(ctx, cudaMemcpyAsync(&ctx->B.scal->time, &t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<double> v(ctx->G.n_inst, t);
+  IDP_CUDA(ctx, cudaMemcpy(ctx->G.time, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+  return IDP_OK;
+}
+
+idp_status idp_set_instances(idp_ctx* ctx, int64_t n_instances, const int64_t* node_offsets) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (n_instances < 1 || !node_offsets) return fail(ctx, IDP_ERR_ARG, "bad instance list");
+  const int64_t n = ctx->M.n;
+  if (node_offsets[0] != 0 || node_offsets[n_instances] != n)
+    return fail(ctx, IDP_ERR_ARG, "instance offsets must start at 0 and end at n_nodes");
+  std::vector<int32_t> of_node(n);
+  for (int64_t k = 0; k < n_instances; ++k) {
+    if (node_offsets[k + 1] <= node_offsets[k]) return fail(ctx, IDP_ERR_ARG, "empty or decreasing instance range");
+    for (int64_t i = node_offsets[k]; i < node_offsets[k + 1]; ++i) of_node[i] = (int32_t)k;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = ctx->M.rowptr[i]; e < ctx->M.rowptr[i + 1]; ++e)
+      if (of_node[ctx->M.col[e]] != of_node[i]) return fail(ctx, IDP_ERR_ARG, "a matrix entry couples two instances");
+  std::vector<int32_t> of_row(n);
+  for (int64_t i = 0; i < n; ++i) of_row[ctx->L.perm[i]] = of_node[i];
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return alloc_instances(ctx, n_instances, of_row);
+}
+
+idp_status idp_get_instance_times(idp_ctx* ctx, double* t, double* last_tau) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  const size_t bytes = sizeof(double) * ctx->G.n_inst;
+  if (t) IDP_CUDA(ctx, cudaMemcpyAsync(t, ctx->G.time, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  if (last_tau) IDP_CUDA(ctx, cudaMemcpyAsync(last_tau, ctx->G.tau, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return IDP_OK;
+}
+
+idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (block_size != 64 && block_size != 128 && block_size != 256) return fail(ctx, IDP_ERR_ARG, "block size");
+  if (block_size != ctx->block) drop_graph(ctx);
+  ctx->block = block_size;
+  ctx->use_graph = use_graph != 0;
+  return IDP_OK;
+}
+
+idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, double* ms_per_step) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  if (steps < 1) return fail(ctx, IDP_ERR_ARG, "steps");
+  const size_t n = (size_t)ctx->G.n, ni = (size_t)ctx->G.n_inst;
+  // the trial steps advance the state: keep U and the instance clocks
+  std::vector<double> U0(5 * n), t0(ni), tau0(ni);
+  IDP_CUDA(ctx, cudaMemcpyAsync(U0.data(), ctx->B.U, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, ctx->stream));
+  idp_status st = idp_get_instance_times(ctx, t0.data(), tau0.data());
+  if (st != IDP_OK) return st;
+  const int blocks[3] = {64, 128, 256};
+  double best = 1e300;
+  int best_b = ctx->block, best_g = ctx->use_graph ? 1 : 0;
+  cudaEvent_t a, b;
+  IDP_CUDA(ctx, cudaEventCreate(&a));
+  IDP_CUDA(ctx, cudaEventCreate(&b));
+  for (int g = 0; g < 2; ++g)
+    for (int q = 0; q < 3; ++q) {
+      if ((st = idp_set_schedule(ctx, blocks[q], g))) break;
+      if ((st = idp_step(ctx, 1))) break;  // warm-up (and graph capture)
+      IDP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
+      if ((st = idp_step(ctx, steps))) break;
+      IDP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
+      IDP_CUDA(ctx, cudaEventSynchronize(b));
+      float ms = 0.0f;
+      IDP_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
+      if (ms / steps < best) {
+        best = ms / steps;
+        best_b = blocks[q];
+        best_g = g;
+      }
+      IDP_CUDA(ctx, cudaMemcpyAsync(ctx->B.U, U0.data(), sizeof(double) * 5 * n, cudaMemcpyHostToDevice, ctx->stream));
+      IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.time, t0.data(), sizeof(double) * ni, cudaMemcpyHostToDevice, ctx->stream));
+      IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != IDP_OK) return st;
+  if ((st = idp_set_schedule(ctx, best_b, best_g))) return st;
+  if (block_size) *block_size = best_b;
+  if (use_graph) *use_graph = best_g;
+  if (ms_per_step) *ms_per_step = best;
+  return device_status(ctx, true);
 }
 
 idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
@@ -449,7 +631,7 @@ idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
     case IDP_FIELD_L5: return traced ? slot_field(B.tl5, 1) : fail(ctx, IDP_ERR_STATE, "no traced stage");
     case IDP_FIELD_ULIM: return traced ? node_field(B.tUlim, 5) : fail(ctx, IDP_ERR_STATE, "no traced stage");
     case IDP_FIELD_TAU_MAX: {
-      IDP_CUDA(ctx, cudaMemcpyAsync(out, &B.scal->tau_max, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      IDP_CUDA(ctx, cudaMemcpyAsync(out, ctx->G.tau_max, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       return IDP_OK;
     }

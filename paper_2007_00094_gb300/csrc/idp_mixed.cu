@@ -26,7 +26,6 @@ namespace idp {
 
 namespace {
 
-constexpr int kBlock = 128;
 constexpr float kLambdaSafety = 1.0f + 1e-5f;
 constexpr float kPsiMargin = 1e-6f;
 
@@ -219,7 +218,7 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
 }
 
 // Step 0: per-node quantities (FP32 copies) and an FP32 copy of the state.
-__global__ void __launch_bounds__(kBlock) k_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
+__global__ void __launch_bounds__(kMaxBlock) k_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
                                                    float* __restrict__ Uf, DeviceScalars* scal) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -244,12 +243,12 @@ __global__ void __launch_bounds__(kBlock) k_node_m(int64_t n, const double* __re
 }
 
 // Step 1 in FP32: d_ij (upper edges) with 1/(2 d_ij), flux differences and alpha_i.
-__global__ void __launch_bounds__(kBlock) k_edge_m(DeviceGraph G, MixedGraph M, const float* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph M, const float* __restrict__ U,
                                                    const float* __restrict__ Q, float* __restrict__ d,
                                                    float* __restrict__ dinv, float* __restrict__ dF,
                                                    float* __restrict__ alpha, DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r == 0) scal->tau_min_bits = 0x7ff0000000000000ull;
+  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -307,23 +306,9 @@ __global__ void __launch_bounds__(kBlock) k_edge_m(DeviceGraph G, MixedGraph M, 
   alpha[r] = D > 0.0f ? fabsf(num) / D : 0.0f;
 }
 
-__device__ __forceinline__ double block_min(double v) {
-  __shared__ double red[kBlock / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    v = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  }
-  return v;
-}
-
 // Step 2: lower half of d and 1/(2d), and the CFL bound min_i m_i/(-2 d_ii)
 // with d_ii summed in FP64.
-__global__ void __launch_bounds__(kBlock) k_diag_m(DeviceGraph G, float* __restrict__ d, float* __restrict__ dinv,
+__global__ void __launch_bounds__(kMaxBlock) k_diag_m(DeviceGraph G, float* __restrict__ d, float* __restrict__ dinv,
                                                    DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double cand = INFINITY;
@@ -348,20 +333,14 @@ __global__ void __launch_bounds__(kBlock) k_diag_m(DeviceGraph G, float* __restr
     }
     cand = G.mi[r] / (2.0 * sum);
   }
-  cand = block_min(cand);
-  if (threadIdx.x == 0 && cand < INFINITY)
-    atomicMin(&scal->tau_min_bits, (unsigned long long)__double_as_longlong(cand));
-}
-
-__device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_mode, double cfl) {
-  return tau_mode == 0 ? cfl * __longlong_as_double((long long)scal->tau_min_bits) : scal->tau;
+  reduce_tau_candidate(G, r, cand);
 }
 
 // Step 3: U^L_i = U_i + sum_j (2 tau d_ij/m_i)(Ubar_ij - U_i) with
 // Ubar_ij - U_i = (U_j - U_i)/2 - df_ij/(2 d_ij) summed in FP32 and added to
 // the FP64 state; bounds rho_i + min/max_j (Ubar_ij - U_i)_rho and phi_min;
 // R_i = -sum_j df_ij - f_i.s_i + sum_j d^H_ij (U_j - U_i) in FP32.
-__global__ void __launch_bounds__(kBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,
                                                         const float* __restrict__ Uf, const float* __restrict__ Q,
                                                         const float* __restrict__ d, const float* __restrict__ dinv,
                                                         const float* __restrict__ dF, const float* __restrict__ alpha,
@@ -369,18 +348,9 @@ __global__ void __launch_bounds__(kBlock) k_low_order_m(DeviceGraph G, StageConf
                                                         double* __restrict__ bnd, DeviceScalars* scal, int tau_mode,
                                                         int accumulate_time) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double tau = stage_tau(scal, tau_mode, C.cfl);
-  if (r == 0) {
-    const double tmax = __longlong_as_double((long long)scal->tau_min_bits);
-    scal->tau_max = tmax;
-    if (tau_mode == 0) {
-      scal->tau = tau;
-      if (accumulate_time) scal->time += tau;
-    } else if (tau > tmax) {
-      atomicOr(&scal->status, kStatusCfl);
-    }
-  }
+  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
   if (r >= G.n) return;
+  const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -439,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_low_order_m(DeviceGraph G, StageConf
 }
 
 // Step 4 in FP32: P_ij and the first limiter values.
-__global__ void __launch_bounds__(kBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
+__global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
                                                          const float* __restrict__ Uf, const float* __restrict__ d,
                                                          const float* __restrict__ alpha, const double* __restrict__ UL,
                                                          const float* __restrict__ R, const double* __restrict__ bnd,
@@ -447,7 +417,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_limit_m(DeviceGraph G, MixedGra
                                                          const DeviceScalars* scal, int tau_mode) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
-  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -487,7 +457,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_limit_m(DeviceGraph G, MixedGra
 
 // Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
 // FP32, added to FP64), P_ij <- (1 - min) P_ij and new l_ij.
-__global__ void __launch_bounds__(kBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                            double* __restrict__ Unext, float* __restrict__ P,
                                                            const float* __restrict__ lold, float* __restrict__ lnew,
                                                            const double* __restrict__ bnd) {
@@ -533,7 +503,7 @@ __global__ void __launch_bounds__(kBlock) k_limiter_pass_m(DeviceGraph G, StageC
 }
 
 // Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
-__global__ void __launch_bounds__(kBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                     const float* __restrict__ P, const float* __restrict__ l,
                                                     const double* __restrict__ Un, double* __restrict__ Uout,
                                                     double* __restrict__ Ulim, DeviceScalars* scal, int blend,
@@ -589,7 +559,8 @@ __global__ void __launch_bounds__(kBlock) k_final_m(DeviceGraph G, StageConfig C
 int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B, const MixedBuffers& X,
                             const StageConfig& C, const double* Uin, double* Uout, const double* Un, int blend,
                             int tau_mode, bool accumulate_time, bool skip_write_on_error, bool trace, cudaStream_t s,
-                            Profiler* prof) {
+                            Profiler* prof, int block) {
+  const int kBlock = block;
   const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
   const bool p = prof && prof->enabled;
   int launches = 0;

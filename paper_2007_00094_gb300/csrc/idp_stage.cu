@@ -11,7 +11,7 @@ namespace idp {
 
 namespace {
 
-constexpr int kBlock = 128;
+constexpr int kBlock = 128;  // state-check kernels
 
 __device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
   return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
@@ -52,7 +52,7 @@ __device__ __forceinline__ Side load_side(const double* U, const double* Q, int6
 
 // Step 0: per-node quantities (Sec. 2): 1/rho, p, c, p^(-1/7), 1/p,
 // eta/rho with eta = (rho eps)^(5/12), (E + p)/rho and phi = eps rho^(-7/5).
-__global__ void __launch_bounds__(kBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
+__global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
                                                  DeviceScalars* scal) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(kBlock) k_node(int64_t n, const double* __rest
 // and the indicator alpha_i (Sec. 3.8) over all j in I(i).  The flux
 // differences (f_j - f_i).c_ij computed for the indicator are stored (in the
 // P buffer, free until Step 4) for the bar states and R_i of Step 3.
-__global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
                                                  const double* __restrict__ Q, double* __restrict__ d,
                                                  double* __restrict__ dinv, double* __restrict__ dF,
                                                  double* __restrict__ alpha, DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r == 0) scal->tau_min_bits = 0x7ff0000000000000ull;  // +inf, read by the next kernel
+  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;  // +inf, read by the next kernel
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -149,23 +149,9 @@ __global__ void __launch_bounds__(kBlock) k_edge(DeviceGraph G, const double* __
   alpha[r] = D > 0.0 ? fabs(num) / D : 0.0;
 }
 
-__device__ __forceinline__ double block_min(double v) {
-  __shared__ double red[kBlock / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    v = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  }
-  return v;
-}
-
 // Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
 // CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
-__global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restrict__ d, double* __restrict__ dinv,
+__global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, double* __restrict__ d, double* __restrict__ dinv,
                                                  DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double cand = INFINITY;
@@ -195,12 +181,7 @@ __global__ void __launch_bounds__(kBlock) k_diag(DeviceGraph G, double* __restri
     d[pd] = -sum;
     cand = G.mi[r] / (2.0 * sum);
   }
-  cand = block_min(cand);
-  if (threadIdx.x == 0 && cand < INFINITY) atomicMin(&scal->tau_min_bits, (unsigned long long)__double_as_longlong(cand));
-}
-
-__device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_mode, double cfl) {
-  return tau_mode == 0 ? cfl * __longlong_as_double((long long)scal->tau_min_bits) : scal->tau;
+  reduce_tau_candidate(G, r, cand);
 }
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
@@ -209,25 +190,16 @@ __device__ __forceinline__ double stage_tau(const DeviceScalars* scal, int tau_m
 // flux differences df_ij = (f_j - f_i).c_ij of Step 1,
 // Ubar_ij = (U_i + U_j)/2 - df_ij/(2 d_ij) and, since sum_j c_ij = s_i,
 // sum_j -f_j.c_ij = -sum_j df_ij - f_i.s_i (s_i is zero up to rounding).
-__global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
                                                       const double* __restrict__ Q, const double* __restrict__ d,
                                                       const double* __restrict__ dinv, const double* __restrict__ dF,
                                                       const double* __restrict__ alpha, double* __restrict__ UL,
                                                       double* __restrict__ R, double* __restrict__ bnd,
                                                       DeviceScalars* scal, int tau_mode, int accumulate_time) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double tau = stage_tau(scal, tau_mode, C.cfl);
-  if (r == 0) {
-    const double tmax = __longlong_as_double((long long)scal->tau_min_bits);
-    scal->tau_max = tmax;
-    if (tau_mode == 0) {
-      scal->tau = tau;
-      if (accumulate_time) scal->time += tau;
-    } else if (tau > tmax) {
-      atomicOr(&scal->status, kStatusCfl);
-    }
-  }
+  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
   if (r >= G.n) return;
+  const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -284,7 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_low_order(DeviceGraph G, StageConfig
 
 // Step 4: antidiffusive fluxes P_ij (eq. def-p) with b_ij = -m_ij/m_j,
 // b_ji = -m_ij/m_i (j != i) and the first limiter values l_ij.
-__global__ void __launch_bounds__(kBlock) k_flux_limit(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+__global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageConfig C, const double* __restrict__ U,
                                                        const double* __restrict__ d, const double* __restrict__ alpha,
                                                        const double* __restrict__ UL, const double* __restrict__ R,
                                                        const double* __restrict__ bnd, double* __restrict__ P,
@@ -292,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_limit(DeviceGraph G, StageConfi
                                                        int tau_mode) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
-  const double tau = stage_tau(scal, tau_mode, C.cfl);
+  const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -332,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_flux_limit(DeviceGraph G, StageConfi
 
 // Steps 5, 6, ...: U_i += sum_j lambda_i min(l_ij, l_ji) P_ij, then (not in
 // the last pass) P_ij <- (1 - min(l_ij, l_ji)) P_ij and new l_ij.
-__global__ void __launch_bounds__(kBlock) k_limiter_pass(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                          double* __restrict__ Unext, double* __restrict__ P,
                                                          const double* __restrict__ lold, double* __restrict__ lnew,
                                                          const double* __restrict__ bnd) {
@@ -379,7 +351,7 @@ __global__ void __launch_bounds__(kBlock) k_limiter_pass(DeviceGraph G, StageCon
 // Last limiter pass, boundary post-processing (slip walls drop the flagged
 // normal momentum components, inflow nodes take the inflow state) and the
 // SSP-RK3 blend (Sec. 3.6): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
-__global__ void __launch_bounds__(kBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                   const double* __restrict__ P, const double* __restrict__ l,
                                                   const double* __restrict__ Un, double* __restrict__ Uout,
                                                   double* __restrict__ Ulim, DeviceScalars* scal, int blend,
@@ -508,7 +480,8 @@ void Profiler::clear() {
 
 int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
-                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof) {
+                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof, int block) {
+  const int kBlock = block;  // block size of this schedule (<= kMaxBlock)
   const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
   const bool p = prof && prof->enabled;
   int launches = 0;

@@ -32,7 +32,19 @@ struct DeviceGraph {
   const double* inv_mi;
   const double* lam;
   const int32_t* bc;
+  // Independent instances (node ranges without entries between them): each
+  // has its own tau_n and time.  inst[r] is the instance of row r (nullptr:
+  // one instance).  The per-instance arrays below are device state written
+  // by the kernels, not part of the read-only graph.
+  int64_t n_inst;
+  const int32_t* inst;
+  double* tau;                   // tau_n of the current RK step
+  double* time;                  // accumulated simulated time
+  double* tau_max;               // min_i m_i / (-2 d_ii) of the last stage
+  unsigned long long* tau_min;   // atomicMin accumulator (bits of positive doubles)
 };
+
+__device__ __forceinline__ int instance_of(const DeviceGraph& G, int64_t r) { return G.inst ? G.inst[r] : 0; }
 
 // Device status bits latched by the kernels.
 enum : int {
@@ -44,10 +56,6 @@ enum : int {
 
 // Device scalars of a context.
 struct DeviceScalars {
-  double tau;                     // tau_n of the current RK step
-  double time;                    // accumulated simulated time
-  double tau_max;                 // min_i m_i / (-2 d_ii) of the last stage
-  unsigned long long tau_min_bits;  // atomicMin accumulator of positive doubles
   int status;
 };
 
@@ -83,6 +91,48 @@ struct StageConfig {
 
 enum Blend : int { kBlendNone = 0, kBlendStage2 = 1, kBlendStage3 = 2 };
 
+// Largest block size the stage kernels are compiled for.
+constexpr int kMaxBlock = 256;
+
+// tau of row r's instance: c_cfl times the CFL bound in the first RK stage,
+// the stored tau_n in the later ones.
+__device__ __forceinline__ double stage_tau(const DeviceGraph& G, int ins, int tau_mode, double cfl) {
+  return tau_mode == 0 ? cfl * __longlong_as_double((long long)G.tau_min[ins]) : G.tau[ins];
+}
+
+// Thread r < n_inst keeps instance r's books after the CFL reduction: the
+// bound, tau_n and the time in the first stage, the CFL check in the others.
+__device__ __forceinline__ void instance_books(const DeviceGraph& G, int64_t r, int tau_mode, double cfl,
+                                               int accumulate_time, DeviceScalars* scal) {
+  if (r >= G.n_inst) return;
+  const double tmax = __longlong_as_double((long long)G.tau_min[r]);
+  G.tau_max[r] = tmax;
+  if (tau_mode == 0) {
+    const double tau = cfl * tmax;
+    G.tau[r] = tau;
+    if (accumulate_time) G.time[r] += tau;
+  } else if (G.tau[r] > tmax) {
+    atomicOr(&scal->status, kStatusCfl);
+  }
+}
+
+// min-reduction of the CFL candidates into their instances' accumulators:
+// one atomic per warp when the warp's rows share an instance.
+__device__ __forceinline__ void reduce_tau_candidate(const DeviceGraph& G, int64_t r, double cand) {
+  const bool valid = r < G.n;
+  const int ins = valid ? instance_of(G, r) : -1;
+  const int ins0 = __shfl_sync(0xffffffffu, ins, 0);
+  const bool uniform = __all_sync(0xffffffffu, !valid || ins == ins0);
+  if (uniform) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cand = fmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+    if ((threadIdx.x & 31) == 0 && ins0 >= 0 && cand < INFINITY)
+      atomicMin(&G.tau_min[ins0], (unsigned long long)__double_as_longlong(cand));
+  } else if (valid && cand < INFINITY) {
+    atomicMin(&G.tau_min[ins], (unsigned long long)__double_as_longlong(cand));
+  }
+}
+
 // Kernel ids of one euler_step (also the order of idp_profile_read).
 enum KernelId : int { kKNode = 0, kKEdge, kKDiag, kKLowOrder, kKFluxLimit, kKLimiterPass, kKFinal, kNumKernels };
 
@@ -106,7 +156,8 @@ struct Profiler {
 // Returns the number of kernel launches.
 int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
-                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof = nullptr);
+                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof = nullptr,
+                      int block = 128);
 
 // Counts nodes with rho <= 0, epsilon <= 0, non-finite values; writes
 // {count_rho, count_eps, count_nonfinite} as doubles plus rho_min, eps_min

@@ -30,7 +30,8 @@ FIELDS = {"d": 0, "alpha": 1, "UL": 2, "R": 3, "bounds": 4, "P": 5, "l4": 6, "U5
 EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error", "idp_status_string",
             "idp_upload_mesh_hex", "idp_mesh_info", "idp_get_matrices", "idp_init_state", "idp_get_state",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
-            "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc"]
+            "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
+            "idp_get_instance_times", "idp_set_schedule", "idp_autotune"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final"]
 
@@ -93,6 +94,10 @@ def load(path: str = LIB_PATH):
     L.idp_profile.argtypes = [_vp, C.c_int]
     L.idp_profile_read.argtypes = [_vp, _dp, _i64p]
     L.idp_tau_max_noalloc.argtypes = [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.idp_set_instances.argtypes = [_vp, C.c_int64, _i64p]
+    L.idp_get_instance_times.argtypes = [_vp, _dp, _dp]
+    L.idp_set_schedule.argtypes = [_vp, C.c_int, C.c_int]
+    L.idp_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]
     _lib = L
     return L
 
@@ -253,3 +258,24 @@ class Solver:
         cnt = np.zeros(len(KERNELS), dtype=np.int64)
         _check(self._ctx, load().idp_profile_read(self._ctx, _ptr(ms), _ptr(cnt, _i64p)))
         return {k: (float(ms[q]), int(cnt[q])) for q, k in enumerate(KERNELS)}
+
+    def set_instances(self, node_offsets):
+        """Declares independent instances by contiguous node ranges."""
+        off = np.ascontiguousarray(node_offsets, dtype=np.int64)
+        _check(self._ctx, load().idp_set_instances(self._ctx, len(off) - 1, _ptr(off, _i64p)))
+        self.n_instances = len(off) - 1
+
+    def instance_times(self):
+        k = getattr(self, "n_instances", 1)
+        t, tau = np.zeros(k), np.zeros(k)
+        _check(self._ctx, load().idp_get_instance_times(self._ctx, _ptr(t), _ptr(tau)))
+        return t, tau
+
+    def set_schedule(self, block_size=128, use_graph=False):
+        _check(self._ctx, load().idp_set_schedule(self._ctx, int(block_size), int(bool(use_graph))))
+
+    def autotune(self, steps=2):
+        """Times every schedule and keeps the fastest; returns (block, graph, ms/step)."""
+        b, g, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(self._ctx, load().idp_autotune(self._ctx, int(steps), C.byref(b), C.byref(g), C.byref(ms)))
+        return b.value, bool(g.value), ms.value

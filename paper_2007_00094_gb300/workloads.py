@@ -333,3 +333,24 @@ def sod_mesh(nx, ny=4, nz=4):
 def sod_cube_mesh(n=128):
     """128^3-node slip-walled unit cube for the 3D Sod precision workload."""
     return box_mesh((n, n, n), periodic=(False, False, False), walls="slip", name=f"sodcube{n}")
+
+
+def concat_meshes(meshes, states=None):
+    """Union of independent meshes in one HexMesh.
+
+    Node ids of mesh k are shifted by the node count of meshes 0..k-1, so the
+    instances occupy contiguous node ranges and share no cell.  Returns
+    ``(mesh, node_offsets, U)`` with ``node_offsets`` of length len(meshes)+1
+    and ``U`` the concatenated states (None if ``states`` is None).
+    """
+    offsets = [0]
+    for m in meshes:
+        offsets.append(offsets[-1] + m.n_nodes)
+    cells = np.concatenate([m.cells + off for m, off in zip(meshes, offsets[:-1])])
+    x = np.concatenate([m.x for m in meshes])
+    cell_xyz = np.concatenate([m.cell_xyz for m in meshes])
+    bc = np.concatenate([m.bc for m in meshes]).astype(np.int32)
+    U = None if states is None else np.concatenate([np.asarray(u) for u in states], axis=1)
+    mesh = HexMesh(x=x, cells=cells, cell_xyz=cell_xyz, bc=bc, volume=float(sum(m.volume for m in meshes)),
+                   name=f"batch{len(meshes)}", meta={"instances": len(meshes)})
+    return mesh, np.asarray(offsets, dtype=np.int64), U
