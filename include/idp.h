@@ -202,6 +202,41 @@ idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph);
  * milliseconds per step (any output pointer may be NULL); synchronises. */
 idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, double* ms_per_step);
 
+/* Reverse mode (discrete adjoint) of the FP64 scheme, for gradients of a
+ * functional J(U^N) with respect to the state U^0 it evolved from.  The
+ * adjoint differentiates the stage as computed (Alg. 1 with the limiter of
+ * Alg. 2/3 and the bound of Sec. 3.7, Newton steps included); at
+ * non-smooth points it takes the branch the forward pass took:
+ * min(l_ij, l_ji) and every min/max bound go to the first extremal entry,
+ * tau_n = c_cfl min_i m_i/(-2 d_ii) (Sec. 3.3) to the first row attaining
+ * the minimum.  Supported for precision IDP_PRECISION_FP64,
+ * limiter_passes = 2 and a single instance, else IDP_ERR_ARG.  The
+ * adjoint buffers (about 32 doubles per stencil entry) are allocated on
+ * first use.  Arrays are (5, n_nodes) field-major doubles in caller order;
+ * on_device != 0: device pointers, else host pointers.
+ *
+ * idp_adjoint_euler_step: the adjoint gU of the input U of one euler_step
+ * (Alg. 1, boundary post-processing included) given the adjoint gE of its
+ * output.  tau > 0: fixed tau_n, and *g_tau (host, may be NULL) receives
+ * dJ/dtau_n; tau <= 0: tau_n is computed from U (first RK stage) and gU
+ * includes its dependence on U (*g_tau then holds the partial derivative
+ * at fixed tau_n).  Leaves the context's state untouched; synchronises. */
+idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, const double* gE, double* gU,
+                                  double* g_tau, int on_device);
+/* idp_adjoint_record: advances the context's state by n_steps SSP-RK3 steps
+ * (eq. ssprk3, as idp_step) and keeps what the backward sweep needs: a
+ * checkpoint of the state every checkpoint_every steps (clamped to n_steps)
+ * and tau_n of every step, replacing any earlier record.  Device memory:
+ * ceil(n_steps/checkpoint_every) + 3 checkpoint_every states.  Synchronises.
+ * idp_adjoint_backward: given the adjoint gU_final of the state after the
+ * recorded steps, writes the adjoint gU_initial of the state before them.
+ * Each checkpoint segment is recomputed forward once, then every stage is
+ * re-evaluated with its trace and reversed (eq. ssprk3 blends included).
+ * The context's state, time and record stay as they were; synchronises.
+ * IDP_ERR_STATE without a record. */
+idp_status idp_adjoint_record(idp_ctx* ctx, int n_steps, int checkpoint_every);
+idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU_initial, int on_device);
+
 /* Time-step bound without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory, such as a host framework that owns all device memory

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libidp.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["idp_stage.cu", "idp_mixed.cu", "idp_api.cu", "idp_noalloc.cu"]
+CUDA_SOURCES = ["idp_stage.cu", "idp_mixed.cu", "idp_api.cu", "idp_noalloc.cu", "idp_adjoint.cu"]
 CXX_SOURCES = ["idp_mesh.cpp"]
 
 

@@ -1,0 +1,679 @@
+// Discrete adjoint (reverse mode) of one FP64 euler_step (Alg. 1): given the
+// adjoint of the stage output, the adjoint of the stage input.
+//
+// The reverse kernels run the forward sweeps backwards (Step 6 -> Step 0)
+// over the intermediates of a traced forward evaluation of the stage.
+// Non-smooth points take the branch the forward pass took: min(l_ij, l_ji)
+// routes to the smaller value (own entry on ties), each bound to the first
+// entry attaining it, tau_n to the first row attaining the CFL minimum, the
+// limiter and the wavespeed bound to their evaluated branches, |x| has the
+// derivative sign(x) with sign(0) = 0.  Per-entry local derivatives (fluxes,
+// entropies, the wavespeed bound and the limiter with its Newton steps) come
+// from forward-mode dual numbers.  A row never writes another row's adjoint:
+// a contribution to neighbour j of entry (i, j) is stored at that entry and
+// row j gathers it through the transposed entry, so results do not depend
+// on thread scheduling.
+#include <cfloat>
+
+#include "idp_adjoint.cuh"
+#include "idp_dual.cuh"
+#include "idp_internal.h"
+
+namespace idp {
+
+namespace {
+
+constexpr int kB = 128;
+
+__device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
+  return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
+}
+
+__device__ __forceinline__ void load5(const double* U, int64_t n, int64_t i, double* u) {
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) u[f] = U[f * n + i];
+}
+
+__device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// gl times the derivative of limiter(U, P, rho_min, rho_max, phi_min),
+// added to gU, gP and gb = (g rho_min, g rho_max, g phi_min).
+__device__ void limiter_vjp(const double* U, const double* P, double rmin, double rmax, double pmin, double gl,
+                            const LimiterParams& prm, double* gU, double* gP, double* gb) {
+  {
+    Dual<5> Ud[kFields], Pd[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      Ud[f] = dseed<5>(U[f], f);
+      Pd[f] = dconst<5>(P[f]);
+    }
+    const Dual<5> t = limiter_t(Ud, Pd, dconst<5>(rmin), dconst<5>(rmax), dconst<5>(pmin), prm);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) gU[f] += gl * t.d[f];
+  }
+  {
+    Dual<5> Ud[kFields], Pd[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      Ud[f] = dconst<5>(U[f]);
+      Pd[f] = dseed<5>(P[f], f);
+    }
+    const Dual<5> t = limiter_t(Ud, Pd, dconst<5>(rmin), dconst<5>(rmax), dconst<5>(pmin), prm);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) gP[f] += gl * t.d[f];
+  }
+  {
+    Dual<3> Ud[kFields], Pd[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      Ud[f] = dconst<3>(U[f]);
+      Pd[f] = dconst<3>(P[f]);
+    }
+    const Dual<3> t = limiter_t(Ud, Pd, dseed<3>(rmin, 0), dseed<3>(rmax, 1), dseed<3>(pmin, 2), prm);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gb[q] += gl * t.d[q];
+  }
+}
+
+// out += sign * J^T g, J the Jacobian of U -> f(U).c at state u
+__device__ void flux_vjp(const double* u, double cx, double cy, double cz, const double* g, double sign, double* out) {
+  Dual<5> ud[kFields], F[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) ud[f] = dseed<5>(u[f], f);
+  flux_dot_t(ud, cx, cy, cz, F);
+#pragma unroll
+  for (int q = 0; q < kFields; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) acc += F[f].d[q] * g[f];
+    out[q] += sign * acc;
+  }
+}
+
+// out += g * grad s(u), s = eta/rho
+__device__ void entropy_s_vjp(const double* u, double g, double* out) {
+  Dual<5> ud[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) ud[f] = dseed<5>(u[f], f);
+  const Dual<5> s = entropy_s(ud);
+#pragma unroll
+  for (int q = 0; q < kFields; ++q) out[q] += g * s.d[q];
+}
+
+// d_ij of the edge {i, j} (Step 1) as a function of the two states
+template <typename T>
+__device__ __forceinline__ T edge_d(const T* ui, const T* uj, double cx, double cy, double cz, double nc, double inv,
+                                    bool skew, double tx, double ty, double tz, double nt, double invt) {
+  const SideT<T> si = side_of_state(ui), sj = side_of_state(uj);
+  T dij = ui[0] * 0.0;
+  if (nc > 0.0) dij = lambda_max_t(cx * inv, cy * inv, cz * inv, si, sj) * nc;
+  if (!skew && nt > 0.0) dij = fmax(dij, lambda_max_t(tx * invt, ty * invt, tz * invt, sj, si) * nt);
+  return dij;
+}
+
+// Step 6 reverse: boundary post-processing and the last limiter pass
+// U6 = U5 + sum_j lambda_i min(l_ij, l_ji) P'_ij.
+__global__ void __launch_bounds__(kB) ka_final(DeviceGraph G, const double* __restrict__ gE, const double* __restrict__ Pp,
+                                               const double* __restrict__ l5, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  double g[kFields];
+  load5(gE, n, r, g);
+  const int bc = G.bc[r];
+  if (bc & 8) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) g[f] = 0.0;
+  } else {
+    if (bc & 1) g[1] = 0.0;
+    if (bc & 2) g[2] = 0.0;
+    if (bc & 4) g[3] = 0.0;
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) A.gU5[f * n + r] = g[f];
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double lam = G.lam[r];
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double lij = l5[p], lji = l5[G.tpos[p]];
+    const double m = fmin(lij, lji);
+    double gm = 0.0;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      A.gPp[f * ns + p] = lam * m * g[f];
+      gm += lam * Pp[f * ns + p] * g[f];
+    }
+    A.gl5_own[p] = lij <= lji ? gm : 0.0;
+    A.gl5_tr[p] = lij <= lji ? 0.0 : gm;
+  }
+}
+
+// Step 5 reverse: l5_ij = limiter(U5, P'_ij, bounds), P'_ij = (1 - m_ij) P_ij
+// and U5 = U^L + sum_j lambda_i m_ij P_ij with m_ij = min(l4_ij, l4_ji).
+__global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, StageConfig C, const double* __restrict__ U5,
+                                              const double* __restrict__ P, const double* __restrict__ Pp,
+                                              const double* __restrict__ l4, const double* __restrict__ l5,
+                                              const double* __restrict__ bnd, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double lam = G.lam[r];
+  double u5[kFields], gU5[kFields], gb[3] = {0.0, 0.0, 0.0};
+  load5(U5, n, r, u5);
+  load5(A.gU5, n, r, gU5);
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double gl = A.gl5_own[p] + A.gl5_tr[G.tpos[p]];
+    const double l = l5[p];
+    // l = 0 and l = 1 are clamped (or skipped) values: locally constant
+    if (gl == 0.0 || !(l > 0.0 && l < 1.0)) continue;
+    double pij[kFields], gP[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = Pp[f * ns + p];
+      gP[f] = 0.0;
+    }
+    limiter_vjp(u5, pij, rmin, rmax, pmin, gl, C.lim, gU5, gP, gb);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gPp[f * ns + p] += gP[f];
+  }
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double lij = l4[p], lji = l4[G.tpos[p]];
+    const double m = fmin(lij, lji);
+    double gm = 0.0;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      const double gpp = A.gPp[f * ns + p];
+      const double pf = P[f * ns + p];
+      A.gP[f * ns + p] = (1.0 - m) * gpp + lam * m * gU5[f];
+      gm += (lam * gU5[f] - gpp) * pf;
+    }
+    A.gl4_own[p] = lij <= lji ? gm : 0.0;
+    A.gl4_tr[p] = lij <= lji ? 0.0 : gm;
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) A.gUL[f * n + r] = gU5[f];
+  A.gbnd[r] = gb[0];
+  A.gbnd[n + r] = gb[1];
+  A.gbnd[2 * n + r] = gb[2];
+}
+
+// Step 4 reverse: l4_ij = limiter(U^L, P_ij, bounds) and
+// P_ij = tau/(m_i lambda_i) (b_ij R_j - b_ji R_i + (d^H_ij - d_ij)(U_j - U_i)).
+__global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                              const double* __restrict__ UL, const double* __restrict__ P,
+                                              const double* __restrict__ l4, const double* __restrict__ d,
+                                              const double* __restrict__ alpha, const double* __restrict__ bnd,
+                                              AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double tau = G.tau[instance_of(G, r)];
+  double ul[kFields], gUL[kFields], ui[kFields];
+  double gRi[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gUi[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double gb[3] = {0.0, 0.0, 0.0};
+  load5(UL, n, r, ul);
+  load5(A.gUL, n, r, gUL);
+  load5(U, n, r, ui);
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const double a_i = alpha[r];
+  const double inv_mi = G.inv_mi[r];
+  const double scale = tau * inv_mi * (double)(len - 1);
+  double galpha_i = 0.0, gtau = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) A.gR_tr[f * ns + p] = 0.0;
+      continue;
+    }
+    double pij[kFields], gP[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = P[f * ns + p];
+      gP[f] = A.gP[f * ns + p];
+    }
+    const double gl = A.gl4_own[p] + A.gl4_tr[G.tpos[p]];
+    const double l = l4[p];
+    if (gl != 0.0 && l > 0.0 && l < 1.0) limiter_vjp(ul, pij, rmin, rmax, pmin, gl, C.lim, gUL, gP, gb);
+    double uj[kFields];
+    load5(U, n, j, uj);
+    const double m = G.mij[p];
+    const double b_ij = -m * G.inv_mi[j];
+    const double b_ji = -m * inv_mi;
+    const double dij = d[p];
+    const double Aij = (a_i + alpha[j]) * 0.5;
+    const double dd = dij * Aij - dij;
+    double gdd = 0.0, tp = 0.0;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      gRi[f] -= scale * b_ji * gP[f];
+      A.gR_tr[f * ns + p] = scale * b_ij * gP[f];
+      gdd += scale * (uj[f] - ui[f]) * gP[f];
+      A.gU_tr[f * ns + p] += scale * dd * gP[f];
+      gUi[f] -= scale * dd * gP[f];
+      tp += pij[f] * gP[f];
+    }
+    A.gd[p] += (Aij - 1.0) * gdd;
+    galpha_i += 0.5 * dij * gdd;
+    A.ga_tr[p] += 0.5 * dij * gdd;
+    if (tau > 0.0) gtau += tp / tau;  // P_ij is linear in tau
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    A.gUL[f * n + r] = gUL[f];
+    A.gR_own[f * n + r] = gRi[f];
+    A.gU_own[f * n + r] += gUi[f];
+  }
+  A.ga_own[r] = galpha_i;
+  A.gbnd[r] += gb[0];
+  A.gbnd[n + r] += gb[1];
+  A.gbnd[2 * n + r] += gb[2];
+  A.gtau_part[r] = gtau;
+}
+
+// Step 3 reverse: U^L_i = U_i + sum_j (2 tau/m_i) d_ij Ubar_ij, the bounds
+// over rho(Ubar_ij) and phi(U_j), and
+// R_i = -f_i.s_i - sum_j (f_j - f_i).c_ij + sum_j d^H_ij (U_j - U_i).
+__global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
+                                             const double* __restrict__ d, const double* __restrict__ dinv,
+                                             const double* __restrict__ alpha, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double tau = G.tau[instance_of(G, r)];
+  double ui[kFields], gUL[kFields], gR[kFields], gUi[kFields];
+  load5(U, n, r, ui);
+  load5(A.gUL, n, r, gUL);
+  load5(A.gR_own, n, r, gR);
+  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
+  // gather R's adjoint; locate the first entries attaining the bounds (the
+  // bar-state densities recomputed as in Step 3)
+  int kmin = -1, kmax = -1, kphi = -1;
+  double vmin = INFINITY, vmax = -INFINITY, vphi = INFINITY;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const int64_t pt = G.tpos[p];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) gR[f] += A.gR_tr[f * ns + pt];
+    const double dij = d[p];
+    if (dij != 0.0) {
+      double ub0 = ui[0];
+      if (j != r) {
+        double fj[kFields], fi[kFields];
+        flux_dot(U[n + j], U[2 * n + j], U[3 * n + j], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j],
+                 G.cx[p], G.cy[p], G.cz[p], fj);
+        flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, G.cx[p], G.cy[p], G.cz[p], fi);
+        ub0 = 0.5 * (ui[0] + U[j]) - (fj[0] - fi[0]) * dinv[p];
+      }
+      if (ub0 < vmin) {
+        vmin = ub0;
+        kmin = k;
+      }
+      if (ub0 > vmax) {
+        vmax = ub0;
+        kmax = k;
+      }
+    }
+    const double phj = Q[kQPhi * n + j];
+    if (phj < vphi) {
+      vphi = phj;
+      kphi = k;
+    }
+  }
+  const double g_rmin = A.gbnd[r], g_rmax = A.gbnd[n + r], g_pmin = A.gbnd[2 * n + r];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) gUi[f] = gUL[f];
+  // -f_i . s_i
+  flux_vjp(ui, G.csx[r], G.csy[r], G.csz[r], gR, -1.0, gUi);
+  const double a_i = alpha[r];
+  const double two_tau_m = 2.0 * tau * G.inv_mi[r];
+  double ga_i = 0.0, gtau = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    const double dij = d[p];
+    if (k == kphi) A.gphi_tr[p] += g_pmin;
+    if (j == r) {
+      // Ubar_ii = U_i
+      if (dij != 0.0) {
+        double ud = 0.0;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          gUi[f] += two_tau_m * dij * gUL[f];
+          ud += ui[f] * gUL[f];
+        }
+        A.gd[p] += two_tau_m * ud;
+        gtau += 2.0 * G.inv_mi[r] * dij * ud;
+        if (k == kmin) gUi[0] += g_rmin;
+        if (k == kmax) gUi[0] += g_rmax;
+      }
+      continue;
+    }
+    double uj[kFields];
+    load5(U, n, j, uj);
+    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
+    double fj[kFields], fi[kFields], df[kFields], gdf[kFields];
+    flux_dot(uj[1], uj[2], uj[3], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j], cx, cy, cz, fj);
+    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, cx, cy, cz, fi);
+    const double Aij = (a_i + alpha[j]) * 0.5;
+    const double dH = dij * Aij;
+    double gdH = 0.0;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      df[f] = fj[f] - fi[f];
+      gdf[f] = -gR[f];
+      A.gU_tr[f * ns + p] += dH * gR[f];
+      gUi[f] -= dH * gR[f];
+      gdH += (uj[f] - ui[f]) * gR[f];
+    }
+    A.gd[p] += Aij * gdH;
+    ga_i += 0.5 * dij * gdH;
+    A.ga_tr[p] += 0.5 * dij * gdH;
+    if (dij != 0.0) {
+      // Ubar_ij = (U_i + U_j)/2 - df_ij inv2d with inv2d = 1/(2 d_ij)
+      const double inv2d = dinv[p];
+      const double coef = two_tau_m * dij;
+      double gub[kFields], ud = 0.0;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        const double ub = 0.5 * (ui[f] + uj[f]) - df[f] * inv2d;
+        gub[f] = coef * gUL[f];
+        ud += ub * gUL[f];
+      }
+      if (k == kmin) gub[0] += g_rmin;
+      if (k == kmax) gub[0] += g_rmax;
+      A.gd[p] += two_tau_m * ud;
+      gtau += 2.0 * G.inv_mi[r] * dij * ud;
+      double gi2d = 0.0;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        gUi[f] += 0.5 * gub[f];
+        A.gU_tr[f * ns + p] += 0.5 * gub[f];
+        gdf[f] -= inv2d * gub[f];
+        gi2d -= df[f] * gub[f];
+      }
+      A.gd[p] -= 2.0 * inv2d * inv2d * gi2d;
+    }
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gdF[f * ns + p] = gdf[f];
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) A.gU_own[f * n + r] += gUi[f];
+  A.ga_own[r] += ga_i;
+  A.gtau_part[r] += gtau;
+}
+
+// Sum of the per-row adjoints of tau_n in a fixed order (one block).
+// gtau[1] = this stage's sum plus the carried sum when tau was computed here;
+// gtau[0] accumulates over the stages.
+__global__ void __launch_bounds__(kB) ka_tau(DeviceGraph G, AdjointBuffers A, int add_carry) {
+  __shared__ double part[kB];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) s += A.gtau_part[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)blockDim.x; ++q) t += part[q];
+    A.gtau[1] = t + (add_carry ? A.gtau[0] : 0.0);
+    A.gtau[0] += t;
+  }
+}
+
+// CFL candidates m_i / (-2 d_ii) recomputed from the traced d_ii: their
+// minimum (positive doubles order as their bits), then the first row with it.
+__device__ __forceinline__ double cfl_candidate(const DeviceGraph& G, const double* d, int64_t r) {
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) return G.mi[r] / (-2.0 * d[p]);
+  }
+  return INFINITY;
+}
+
+__global__ void __launch_bounds__(kB) ka_cfl_min(DeviceGraph G, const double* __restrict__ d, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const double c = cfl_candidate(G, d, r);
+  if (c > 0.0 && c < INFINITY) atomicMin(&A.argmin[0], (unsigned long long)__double_as_longlong(c));
+}
+
+__global__ void __launch_bounds__(kB) ka_cfl_arg(DeviceGraph G, const double* __restrict__ d, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const double c = cfl_candidate(G, d, r);
+  if ((unsigned long long)__double_as_longlong(c) == A.argmin[0]) atomicMin(&A.argmin[1], (unsigned long long)r);
+}
+
+// Step 2 reverse: d_ii = -sum_{j != i} d_ij; in the first RK stage also
+// tau_n = c_cfl m_k / (-2 d_kk) of the arg-min row k.
+__global__ void __launch_bounds__(kB) ka_diag(DeviceGraph G, StageConfig C, const double* __restrict__ d,
+                                              AdjointBuffers A, int tau_computed) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double gdii = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] != r) continue;
+    gdii = A.gd[p];
+    if (tau_computed && (unsigned long long)r == A.argmin[1]) {
+      const double dii = d[p];
+      gdii += A.gtau[1] * C.cfl * G.mi[r] / (2.0 * dii * dii);
+    }
+  }
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] != r) A.gd[p] -= gdii;
+  }
+}
+
+// Step 1 reverse: alpha_i (Sec. 3.8), the flux differences, the wavespeed
+// bound d_ij of the edges this row owns, and phi(U_i) of the bounds.
+__global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
+                                              AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double ui[kFields], gUi[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  load5(U, n, r, ui);
+  double galpha = A.ga_own[r], gphi = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t pt = G.tpos[base + 32 * (int64_t)k];
+    galpha += A.ga_tr[pt];
+    gphi += A.gphi_tr[pt];
+  }
+  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
+  const double s_i = Q[kQS * n + r];
+  // a_i and b_i of the indicator, as in Step 1
+  double a = 0.0, b[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    double fj[kFields], fi[kFields];
+    flux_dot(U[n + j], U[2 * n + j], U[3 * n + j], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j], G.cx[p],
+             G.cy[p], G.cz[p], fj);
+    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, G.cx[p], G.cy[p], G.cz[p], fi);
+    a += (Q[kQS * n + j] - s_i) * fj[0];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) b[f] += fj[f] - fi[f];
+  }
+  // alpha = |num| / D with num = a - e.b + s_i b_0,
+  // D = |a| + |e_0 - s_i||b_0| + sum_{f>0} |e_f||b_f|, e = eta'(U_i)
+  double ga = 0.0, gb[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, ge[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gs = 0.0;
+  {
+    const double sc = s_i * Q[kQInvP * n + r] * (1.0 / 6.0);
+    const double e[kFields] = {sc * ui[4], -sc * ui[1], -sc * ui[2], -sc * ui[3], sc * ui[0]};
+    const double num = a - (e[0] * b[0] + e[1] * b[1] + e[2] * b[2] + e[3] * b[3] + e[4] * b[4]) + s_i * b[0];
+    double D = fabs(a);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) D += fabs(e[f] - (f == 0 ? s_i : 0.0)) * fabs(b[f]);
+    if (D > 0.0 && galpha != 0.0) {
+      const double al = fabs(num) / D;
+      const double gD = -al / D * galpha;
+      const double gnum = sgn(num) * galpha / D;
+      ga = gnum + sgn(a) * gD;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        const double ef = e[f] - (f == 0 ? s_i : 0.0);
+        gb[f] = -e[f] * gnum + fabs(ef) * sgn(b[f]) * gD;
+        ge[f] = -b[f] * gnum + sgn(ef) * fabs(b[f]) * gD;
+      }
+      gb[0] += s_i * gnum;
+      gs = b[0] * gnum - sgn(e[0] - s_i) * fabs(b[0]) * gD;
+    }
+  }
+  // e(U_i), s(U_i) and phi(U_i)
+  {
+    Dual<5> ud[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) ud[f] = dseed<5>(ui[f], f);
+    const Dual<5> sd = entropy_s(ud);
+    const SideT<Dual<5>> side = side_of_state(ud);
+    const Dual<5> sc = sd * side.inv_p * (1.0 / 6.0);
+    const Dual<5> e0 = sc * ud[4], e1 = -(sc * ud[1]), e2 = -(sc * ud[2]), e3 = -(sc * ud[3]), e4 = sc * ud[0];
+    const Dual<5> phid = entropy_phi(ud);
+#pragma unroll
+    for (int q = 0; q < kFields; ++q)
+      gUi[q] += ge[0] * e0.d[q] + ge[1] * e1.d[q] + ge[2] * e2.d[q] + ge[3] * e3.d[q] + ge[4] * e4.d[q] +
+                gs * sd.d[q] + gphi * phid.d[q];
+  }
+  double gsi = 0.0;  // adjoint of s_i through a_i
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) continue;  // the diagonal terms of a_i and b_i vanish identically
+    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
+    double uj[kFields], gj[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gdf[kFields];
+    load5(U, n, j, uj);
+    // (f_j - f_i).c_ij: adjoint from Step 3 and from b_i
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) gdf[f] = A.gdF[f * ns + p] + gb[f];
+    flux_vjp(uj, cx, cy, cz, gdf, 1.0, gj);
+    flux_vjp(ui, cx, cy, cz, gdf, -1.0, gUi);
+    // a_i term (s_j - s_i)(m_j . c_ij)
+    if (ga != 0.0) {
+      const double mc = uj[1] * cx + uj[2] * cy + uj[3] * cz;
+      const double ds = Q[kQS * n + j] - s_i;
+      entropy_s_vjp(uj, mc * ga, gj);
+      gj[1] += ds * cx * ga;
+      gj[2] += ds * cy * ga;
+      gj[3] += ds * cz * ga;
+      gsi -= mc * ga;
+    }
+    // d_ij of an edge this row owns: adjoint of both rows' uses
+    if (G.flags[p] & kEntryUpper) {
+      const int64_t pt = G.tpos[p];
+      const double gdedge = A.gd[p] + A.gd[pt];
+      if (gdedge != 0.0) {
+        const bool skew = (G.flags[p] & kEntrySkew) != 0;
+        const double nc = G.cn[p], inv = G.inv_cn[p], nt = G.cn[pt], invt = G.inv_cn[pt];
+        const double tx = G.cx[pt], ty = G.cy[pt], tz = G.cz[pt];
+        Dual<5> a5[kFields], b5[kFields];
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          a5[f] = dseed<5>(ui[f], f);
+          b5[f] = dconst<5>(uj[f]);
+        }
+        const Dual<5> di = edge_d(a5, b5, cx, cy, cz, nc, inv, skew, tx, ty, tz, nt, invt);
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          a5[f] = dconst<5>(ui[f]);
+          b5[f] = dseed<5>(uj[f], f);
+        }
+        const Dual<5> dj = edge_d(a5, b5, cx, cy, cz, nc, inv, skew, tx, ty, tz, nt, invt);
+#pragma unroll
+        for (int q = 0; q < kFields; ++q) {
+          gUi[q] += gdedge * di.d[q];
+          gj[q] += gdedge * dj.d[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gU_tr[f * ns + p] += gj[f];
+  }
+  if (gsi != 0.0) entropy_s_vjp(ui, gsi, gUi);
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) A.gU_own[f * n + r] += gUi[f];
+}
+
+// adjoint of U_i: own part plus the neighbours' contributions stored at the
+// transposed entries
+__global__ void __launch_bounds__(kB) ka_gather(DeviceGraph G, AdjointBuffers A, double* __restrict__ gIn) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double g[kFields];
+  load5(A.gU_own, n, r, g);
+  for (int k = 0; k < len; ++k) {
+    const int64_t pt = G.tpos[base + 32 * (int64_t)k];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) g[f] += A.gU_tr[f * ns + pt];
+  }
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) gIn[f * n + r] = g[f];
+}
+
+__global__ void k_axpby(double* __restrict__ out, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = y ? a * x[i] + b * y[i] : a * x[i];
+}
+
+}  // namespace
+
+int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const AdjointBuffers& A, const StageConfig& C,
+                         const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s) {
+  const unsigned grid = (unsigned)((G.n + kB - 1) / kB);
+  const size_t n = (size_t)G.n, ns = (size_t)G.n_slots;
+  cudaMemsetAsync(A.gU_own, 0, sizeof(double) * kFields * n, s);
+  cudaMemsetAsync(A.gU_tr, 0, sizeof(double) * kFields * ns, s);
+  cudaMemsetAsync(A.gd, 0, sizeof(double) * ns, s);
+  cudaMemsetAsync(A.ga_tr, 0, sizeof(double) * ns, s);
+  cudaMemsetAsync(A.gphi_tr, 0, sizeof(double) * ns, s);
+  // traced intermediates: P and l of Step 4 (tP, tl4), the state and l
+  // after the first pass (tU5, tl5), P' of the first pass (left in B.P)
+  ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A);
+  ka_pass<<<grid, kB, 0, s>>>(G, C, B.tU5, B.tP, B.P, B.tl4, B.tl5, B.bnd, A);
+  ka_flux<<<grid, kB, 0, s>>>(G, C, Uin, B.UL, B.tP, B.tl4, B.d, B.alpha, B.bnd, A);
+  ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.alpha, A);
+  ka_tau<<<1, kB, 0, s>>>(G, A, tau_computed ? 1 : 0);
+  if (tau_computed) {
+    cudaMemsetAsync(A.argmin, 0xff, 2 * sizeof(unsigned long long), s);
+    ka_cfl_min<<<grid, kB, 0, s>>>(G, B.d, A);
+    ka_cfl_arg<<<grid, kB, 0, s>>>(G, B.d, A);
+  }
+  ka_diag<<<grid, kB, 0, s>>>(G, C, B.d, A, tau_computed ? 1 : 0);
+  ka_edge<<<grid, kB, 0, s>>>(G, Uin, B.node, A);
+  ka_gather<<<grid, kB, 0, s>>>(G, A, gIn);
+  return tau_computed ? 10 : 8;
+}
+
+void launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t count, cudaStream_t s) {
+  const int64_t blocks = (count + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 152 * 16 ? blocks : 152 * 16);
+  k_axpby<<<grid, 256, 0, s>>>(out, a, x, b, y, count);
+}
+
+}  // namespace idp

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "idp.h"
+#include "idp_adjoint.cuh"
 #include "idp_internal.h"
 #include "idp_mixed.cuh"
 #include "idp_stage.cuh"
@@ -39,6 +40,15 @@ struct idp_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0;
+  // reverse mode: adjoint buffers and scratch states (allocated on first use)
+  bool has_adjoint = false;
+  idp::AdjointBuffers A{};
+  double *a_in = nullptr, *a_out = nullptr, *a_g = nullptr, *a_acc = nullptr, *a_e = nullptr, *a_tmp = nullptr;
+  // recorded forward run: checkpoints every rec_every steps, tau_n per step,
+  // and the states of one segment (U^n, stage 1, stage 2 of each step)
+  std::vector<void*> rec_allocs;
+  int rec_steps = 0, rec_every = 0;
+  double *rec_ckpt = nullptr, *rec_tau = nullptr, *rec_seg = nullptr;
 };
 
 namespace {
@@ -85,9 +95,18 @@ void free_instances(idp_ctx* ctx) {
   ctx->inst_allocs.clear();
 }
 
+void free_record(idp_ctx* ctx) {
+  for (void* p : ctx->rec_allocs) cudaFree(p);
+  ctx->rec_allocs.clear();
+  ctx->rec_steps = ctx->rec_every = 0;
+  ctx->rec_ckpt = ctx->rec_tau = ctx->rec_seg = nullptr;
+}
+
 void free_all(idp_ctx* ctx) {
   drop_graph(ctx);
   free_instances(ctx);
+  free_record(ctx);
+  ctx->has_adjoint = false;
   for (void* p : ctx->allocations) cudaFree(p);
   ctx->allocations.clear();
 }
@@ -138,6 +157,53 @@ idp_status device_status(idp_ctx* ctx, bool clear) {
   if (st & idp::kStatusCfl) return fail(ctx, IDP_ERR_CFL, "tau of the first RK stage violates the CFL bound of a later stage");
   if (st & idp::kStatusNonFinite) return fail(ctx, IDP_ERR_NONFINITE, "non-finite value in the state");
   if (st & idp::kStatusTimeout) return fail(ctx, IDP_ERR_TIMEOUT, "device wait timed out");
+  return IDP_OK;
+}
+
+// Trace copies of the stage intermediates (allocated on first traced stage).
+idp_status ensure_trace(idp_ctx* ctx) {
+  if (ctx->has_trace) return IDP_OK;
+  idp::StageBuffers& B = ctx->B;
+  const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
+  idp_status st;
+  if ((st = dalloc(ctx, &B.tP, 5 * ns)) || (st = dalloc(ctx, &B.tl4, ns)) || (st = dalloc(ctx, &B.tU5, 5 * n)) ||
+      (st = dalloc(ctx, &B.tl5, ns)) || (st = dalloc(ctx, &B.tUlim, 5 * n)))
+    return st;
+  ctx->has_trace = true;
+  return IDP_OK;
+}
+
+// The reverse mode covers the FP64 stage with two limiter passes on one instance.
+idp_status adjoint_supported(idp_ctx* ctx) {
+  if (!ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (ctx->mixed) return fail(ctx, IDP_ERR_ARG, "the adjoint needs the FP64 precision mode");
+  if (ctx->C.limiter_passes != 2) return fail(ctx, IDP_ERR_ARG, "the adjoint needs limiter_passes = 2");
+  if (ctx->G.n_inst != 1) return fail(ctx, IDP_ERR_ARG, "the adjoint needs a single instance");
+  return IDP_OK;
+}
+
+idp_status ensure_adjoint(idp_ctx* ctx) {
+  idp_status st = ensure_trace(ctx);
+  if (st != IDP_OK || ctx->has_adjoint) return st;
+  idp::AdjointBuffers& A = ctx->A;
+  const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
+  if ((st = dalloc(ctx, &A.gU5, 5 * n)) || (st = dalloc(ctx, &A.gUL, 5 * n)) || (st = dalloc(ctx, &A.gR_own, 5 * n)) ||
+      (st = dalloc(ctx, &A.gU_own, 5 * n)) || (st = dalloc(ctx, &A.gbnd, 3 * n)) || (st = dalloc(ctx, &A.ga_own, n)) ||
+      (st = dalloc(ctx, &A.gtau_part, n)) || (st = dalloc(ctx, &A.gPp, 5 * ns)) || (st = dalloc(ctx, &A.gP, 5 * ns)) ||
+      (st = dalloc(ctx, &A.gR_tr, 5 * ns)) || (st = dalloc(ctx, &A.gU_tr, 5 * ns)) || (st = dalloc(ctx, &A.gdF, 5 * ns)) ||
+      (st = dalloc(ctx, &A.gl5_own, ns)) || (st = dalloc(ctx, &A.gl5_tr, ns)) || (st = dalloc(ctx, &A.gl4_own, ns)) ||
+      (st = dalloc(ctx, &A.gl4_tr, ns)) || (st = dalloc(ctx, &A.gd, ns)) || (st = dalloc(ctx, &A.ga_tr, ns)) ||
+      (st = dalloc(ctx, &A.gphi_tr, ns)) || (st = dalloc(ctx, &A.gtau, 2)) || (st = dalloc(ctx, &A.argmin, 2)) ||
+      (st = dalloc(ctx, &ctx->a_in, 5 * n)) || (st = dalloc(ctx, &ctx->a_out, 5 * n)) ||
+      (st = dalloc(ctx, &ctx->a_g, 5 * n)) || (st = dalloc(ctx, &ctx->a_acc, 5 * n)) ||
+      (st = dalloc(ctx, &ctx->a_e, 5 * n)) || (st = dalloc(ctx, &ctx->a_tmp, 5 * n)))
+    return st;
+  // entries no kernel writes (padding slots) are read by none either; start clean
+  IDP_CUDA(ctx, cudaMemset(A.gl5_own, 0, sizeof(double) * ns));
+  IDP_CUDA(ctx, cudaMemset(A.gl5_tr, 0, sizeof(double) * ns));
+  IDP_CUDA(ctx, cudaMemset(A.gl4_own, 0, sizeof(double) * ns));
+  IDP_CUDA(ctx, cudaMemset(A.gl4_tr, 0, sizeof(double) * ns));
+  ctx->has_adjoint = true;
   return IDP_OK;
 }
 
@@ -319,7 +385,10 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
         (st = dalloc(ctx, &B.alpha, n)) || (st = dalloc(ctx, &B.R, 5 * n)) || (st = dalloc(ctx, &B.P, 5 * ns)) ||
         (st = dalloc(ctx, &B.l[0], ns)) || (st = dalloc(ctx, &B.l[1], ns)))
       return st;
+    // d_ij of padding slots and 1/(2 d_ii) of the diagonal are never written
+    // by the kernels: the diagonal bar state U_i reads a zero there
     IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
+    IDP_CUDA(ctx, cudaMemset(B.dinv, 0, sizeof(double) * ns));
   } else {
     auto to_float = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
     float *fcx, *fcy, *fcz, *fm, *fcn, *finv, *fimi;
@@ -335,6 +404,7 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
         (st = dalloc(ctx, &X.l[1], ns)) || (st = dalloc(ctx, &X.alpha, n)) || (st = dalloc(ctx, &X.R, 5 * n)))
       return st;
     IDP_CUDA(ctx, cudaMemset(X.d, 0, sizeof(float) * ns));
+    IDP_CUDA(ctx, cudaMemset(X.dinv, 0, sizeof(float) * ns));
   }
   B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
@@ -440,13 +510,9 @@ idp_status idp_euler_step(idp_ctx* ctx, double tau, int trace, double* tau_out) 
   if (!ctx) return IDP_ERR_ARG;
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
   idp::StageBuffers& B = ctx->B;
-  if (trace && !ctx->has_trace) {
-    const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
-    idp_status st;
-    if ((st = dalloc(ctx, &B.tP, 5 * ns)) || (st = dalloc(ctx, &B.tl4, ns)) || (st = dalloc(ctx, &B.tU5, 5 * n)) ||
-        (st = dalloc(ctx, &B.tl5, ns)) || (st = dalloc(ctx, &B.tUlim, 5 * n)))
-      return st;
-    ctx->has_trace = true;
+  if (trace) {
+    idp_status st = ensure_trace(ctx);
+    if (st != IDP_OK) return st;
   }
   if (tau > 0.0) {
     std::vector<double> t(ctx->G.n_inst, tau);
@@ -658,5 +724,134 @@ idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out) {
 }
 
 int64_t idp_launch_count(const idp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, const double* gE, double* gU,
+                                  double* g_tau, int on_device) {
+  if (!ctx || !U || !gE || !gU) return fail(ctx, IDP_ERR_ARG, "null argument");
+  idp_status st = adjoint_supported(ctx);
+  if (st != IDP_OK || (st = ensure_adjoint(ctx)) != IDP_OK) return st;
+  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
+  const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaStream_t s = ctx->stream;
+  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->a_in, U, bytes, in, s));
+  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->a_e, gE, bytes, in, s));
+  if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
+  IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
+  int64_t launches = launch(ctx, ctx->a_in, ctx->a_out, ctx->a_in, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false,
+                            true, s, nullptr);
+  launches += idp::launch_adjoint_stage(ctx->G, ctx->B, ctx->A, ctx->C, ctx->a_in, ctx->a_e, ctx->a_tmp, !(tau > 0.0), s);
+  ctx->launches = launches;
+  IDP_CUDA(ctx, cudaGetLastError());
+  IDP_CUDA(ctx, cudaMemcpyAsync(gU, ctx->a_tmp, bytes, out, s));
+  double gt = 0.0;
+  IDP_CUDA(ctx, cudaMemcpyAsync(&gt, ctx->A.gtau, sizeof(double), cudaMemcpyDeviceToHost, s));
+  st = device_status(ctx, true);  // synchronises the stream
+  if (g_tau) *g_tau = gt;
+  return st;
+}
+
+idp_status idp_adjoint_record(idp_ctx* ctx, int n_steps, int checkpoint_every) {
+  if (!ctx) return IDP_ERR_ARG;
+  idp_status st = adjoint_supported(ctx);
+  if (st != IDP_OK) return st;
+  if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
+  if (n_steps < 1 || checkpoint_every < 1) return fail(ctx, IDP_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (checkpoint_every > n_steps) checkpoint_every = n_steps;
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  free_record(ctx);
+  const size_t n5 = (size_t)5 * ctx->G.n;
+  const size_t n_ckpt = (size_t)((n_steps + checkpoint_every - 1) / checkpoint_every);
+  auto get = [&](double** p, size_t count) -> idp_status {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(double) * count);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, IDP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ctx->rec_allocs.push_back(q);
+    *p = static_cast<double*>(q);
+    return IDP_OK;
+  };
+  if ((st = get(&ctx->rec_ckpt, n_ckpt * n5)) || (st = get(&ctx->rec_tau, (size_t)n_steps)) ||
+      (st = get(&ctx->rec_seg, (size_t)3 * checkpoint_every * n5))) {
+    free_record(ctx);
+    return st;
+  }
+  cudaStream_t s = ctx->stream;
+  int64_t launches = 0;
+  for (int q = 0; q < n_steps; ++q) {
+    if (q % checkpoint_every == 0)
+      IDP_CUDA(ctx, cudaMemcpyAsync(ctx->rec_ckpt + (size_t)(q / checkpoint_every) * n5, ctx->B.U,
+                                    sizeof(double) * n5, cudaMemcpyDeviceToDevice, s));
+    launches += launch_rk3(ctx, s, &ctx->prof);
+    IDP_CUDA(ctx, cudaMemcpyAsync(ctx->rec_tau + q, ctx->G.tau, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  ctx->launches = launches;
+  IDP_CUDA(ctx, cudaGetLastError());
+  ctx->rec_steps = n_steps;
+  ctx->rec_every = checkpoint_every;
+  return device_status(ctx, true);
+}
+
+idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU_initial, int on_device) {
+  if (!ctx || !gU_final || !gU_initial) return fail(ctx, IDP_ERR_ARG, "null argument");
+  idp_status st = adjoint_supported(ctx);
+  if (st != IDP_OK) return st;
+  if (ctx->rec_steps < 1) return fail(ctx, IDP_ERR_STATE, "no recorded forward run");
+  if ((st = ensure_adjoint(ctx)) != IDP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const idp::DeviceGraph& G = ctx->G;
+  const idp::StageBuffers& B = ctx->B;
+  const size_t n5 = (size_t)5 * G.n, bytes = sizeof(double) * n5;
+  const int n_steps = ctx->rec_steps, every = ctx->rec_every;
+  const int n_ckpt = (n_steps + every - 1) / every;
+  double* g = ctx->a_g;     // adjoint of the current step's output
+  double* acc = ctx->a_acc; // adjoint of U^n through the RK blends
+  double* gE = ctx->a_e;
+  double* tmp = ctx->a_tmp;
+  double* scr = ctx->a_out;
+  auto U0 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q) * n5; };
+  auto U1 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q + 1) * n5; };
+  auto U2 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q + 2) * n5; };
+  IDP_CUDA(ctx, cudaMemcpyAsync(g, gU_final, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  int64_t launches = 0;
+  for (int c = n_ckpt - 1; c >= 0; --c) {
+    const int first = c * every;
+    const int len = n_steps - first < every ? n_steps - first : every;
+    // recompute the segment's step inputs and first two stage states
+    IDP_CUDA(ctx, cudaMemcpyAsync(U0(0), ctx->rec_ckpt + (size_t)c * n5, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int q = 0; q < len; ++q) {
+      launches += launch(ctx, U0(q), U1(q), U0(q), idp::kBlendNone, 0, false, false, false, s, nullptr);
+      launches += launch(ctx, U1(q), U2(q), U0(q), idp::kBlendStage2, 1, false, false, false, s, nullptr);
+      if (q + 1 < len)
+        launches += launch(ctx, U2(q), U0(q + 1), U0(q), idp::kBlendStage3, 1, false, false, false, s, nullptr);
+    }
+    for (int q = len - 1; q >= 0; --q) {
+      IDP_CUDA(ctx, cudaMemcpyAsync(G.tau, ctx->rec_tau + first + q, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
+      // stage 3: U^{n+1} = U^n/3 + 2/3 E(U2)
+      launches += launch(ctx, U2(q), scr, U2(q), idp::kBlendNone, 1, false, false, true, s, nullptr);
+      idp::launch_axpby(gE, 2.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
+      idp::launch_axpby(acc, 1.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U2(q), gE, tmp, false, s);
+      // stage 2: U2 = 3/4 U^n + 1/4 E(U1)
+      launches += launch(ctx, U1(q), scr, U1(q), idp::kBlendNone, 1, false, false, true, s, nullptr);
+      idp::launch_axpby(gE, 0.25, tmp, 0.0, nullptr, (int64_t)n5, s);
+      idp::launch_axpby(acc, 0.75, tmp, 1.0, acc, (int64_t)n5, s);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U1(q), gE, tmp, false, s);
+      // stage 1: U1 = E(U^n), tau_n computed here
+      launches += launch(ctx, U0(q), scr, U0(q), idp::kBlendNone, 0, false, false, true, s, nullptr);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U0(q), tmp, gE, true, s);
+      idp::launch_axpby(g, 1.0, gE, 1.0, acc, (int64_t)n5, s);
+      launches += 5;  // the blends
+    }
+  }
+  IDP_CUDA(ctx, cudaMemcpyAsync(G.tau, ctx->rec_tau + n_steps - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  IDP_CUDA(ctx, cudaGetLastError());
+  IDP_CUDA(ctx, cudaMemcpyAsync(gU_initial, g, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  ctx->launches = launches;
+  return device_status(ctx, true);
+}
 
 }  // extern "C"

@@ -22,20 +22,6 @@ __device__ __forceinline__ void load5(const double* U, int64_t n, int64_t i, dou
   for (int f = 0; f < kFields; ++f) u[f] = U[f * n + i];
 }
 
-// f(U) . c of eq. (flux): (m.c, v (m.c) + p c, (E+p)/rho (m.c)), with an
-// operation sequence pinned by rounding intrinsics so that equal states give
-// bitwise equal fluxes (differences f_j - f_i then vanish exactly, as in the
-// oracle).
-__device__ __forceinline__ void flux_dot(double m1, double m2, double m3, double inv_rho, double p, double h,
-                                         double cx, double cy, double cz, double* f) {
-  const double mc = __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
-  f[0] = mc;
-  f[1] = __fma_rn(p, cx, __dmul_rn(__dmul_rn(m1, inv_rho), mc));
-  f[2] = __fma_rn(p, cy, __dmul_rn(__dmul_rn(m2, inv_rho), mc));
-  f[3] = __fma_rn(p, cz, __dmul_rn(__dmul_rn(m3, inv_rho), mc));
-  f[4] = __dmul_rn(h, mc);
-}
-
 __device__ __forceinline__ Side load_side(const double* U, const double* Q, int64_t n, int64_t i) {
   Side s;
   s.rho = U[i];

@@ -31,7 +31,8 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_upload_mesh_hex", "idp_mesh_info", "idp_get_matrices", "idp_init_state", "idp_get_state",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
-            "idp_get_instance_times", "idp_set_schedule", "idp_autotune"]
+            "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
+            "idp_adjoint_record", "idp_adjoint_backward"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final"]
 
@@ -98,6 +99,9 @@ def load(path: str = LIB_PATH):
     L.idp_get_instance_times.argtypes = [_vp, _dp, _dp]
     L.idp_set_schedule.argtypes = [_vp, C.c_int, C.c_int]
     L.idp_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]
+    L.idp_adjoint_euler_step.argtypes = [_vp, _vp, C.c_double, _vp, _vp, _dp, C.c_int]
+    L.idp_adjoint_record.argtypes = [_vp, C.c_int, C.c_int]
+    L.idp_adjoint_backward.argtypes = [_vp, _vp, _vp, C.c_int]
     _lib = L
     return L
 
@@ -279,3 +283,80 @@ class Solver:
         b, g, ms = C.c_int(), C.c_int(), C.c_double()
         _check(self._ctx, load().idp_autotune(self._ctx, int(steps), C.byref(b), C.byref(g), C.byref(ms)))
         return b.value, bool(g.value), ms.value
+
+    # -- reverse mode ---------------------------------------------------------
+
+    def _arrays(self, *arrays):
+        """Pointers of (5, n) float64 arrays: all CUDA tensors (on_device=1)
+        or all numpy arrays (on_device=0)."""
+        dev = hasattr(arrays[0], "data_ptr")
+        ptrs = []
+        for a in arrays:
+            if dev:
+                assert a.is_cuda and a.dtype.itemsize == 8 and a.is_contiguous() and a.numel() == 5 * self.n
+                ptrs.append(a.data_ptr())
+            else:
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == 5 * self.n
+                ptrs.append(a.ctypes.data)
+        return ptrs, int(dev)
+
+    def adjoint_euler_step(self, U, gE, tau=None, out=None):
+        """Adjoint of one euler_step at input U for the output adjoint gE;
+        returns (gU, dJ/dtau).  tau=None: tau_n computed from U."""
+        if out is None:
+            out = gE.new_empty(gE.shape) if hasattr(gE, "data_ptr") else np.empty((5, self.n))
+        if not hasattr(U, "data_ptr"):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            gE = np.ascontiguousarray(gE, dtype=np.float64)
+        (pu, pg, po), dev = self._arrays(U, gE, out)
+        gt = C.c_double(0.0)
+        _check(self._ctx, load().idp_adjoint_euler_step(self._ctx, pu, 0.0 if tau is None else float(tau), pg, po,
+                                                        C.byref(gt), dev))
+        return out, gt.value
+
+    def adjoint_record(self, n_steps, checkpoint_every=10):
+        """Advances n_steps SSP-RK3 steps, keeping checkpoints for adjoint_backward."""
+        _check(self._ctx, load().idp_adjoint_record(self._ctx, int(n_steps), int(checkpoint_every)))
+
+    def adjoint_backward(self, gU_final, out=None):
+        """Adjoint of the recorded run's initial state for the final-state adjoint gU_final."""
+        if out is None:
+            out = gU_final.new_empty(gU_final.shape) if hasattr(gU_final, "data_ptr") else np.empty((5, self.n))
+        if not hasattr(gU_final, "data_ptr"):
+            gU_final = np.ascontiguousarray(gU_final, dtype=np.float64)
+        (pg, po), dev = self._arrays(gU_final, out)
+        _check(self._ctx, load().idp_adjoint_backward(self._ctx, pg, po, dev))
+        return out
+
+
+def _rollout_function():
+    import torch
+
+    class Rollout(torch.autograd.Function):
+        """U^N(U^0) of n_steps SSP-RK3 steps; backward runs the library's adjoint."""
+
+        @staticmethod
+        def forward(ctx, U0, solver, n_steps, checkpoint_every):
+            solver.init_state(U0.detach().contiguous())
+            solver.adjoint_record(n_steps, checkpoint_every)
+            ctx.solver = solver
+            return solver.get_state(torch.empty_like(U0))
+
+        @staticmethod
+        def backward(ctx, g):
+            return ctx.solver.adjoint_backward(g.contiguous()), None, None, None
+
+    return Rollout
+
+
+_ROLLOUT = None
+
+
+def rollout(solver, U0, n_steps, checkpoint_every=10):
+    """Differentiable run of n_steps SSP-RK3 steps from U0 (a (5, n) float64
+    CUDA tensor): returns U^N; torch.autograd gradients flow back through the
+    discrete adjoint (idp_adjoint_record / idp_adjoint_backward)."""
+    global _ROLLOUT
+    if _ROLLOUT is None:
+        _ROLLOUT = _rollout_function()
+    return _ROLLOUT.apply(U0, solver, int(n_steps), int(checkpoint_every))
