@@ -126,7 +126,7 @@ def pattern_mixed(stream, args):
         ms, prof = _time_steps(s, stream, args.pattern_steps, args.warmup)
         states[name] = s.get_state()
         entry = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                 "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
+                 "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
         if prec == 1:
             dom = max(prof, key=lambda k: prof[k][0])
             dom_ms, dom_n = prof[dom]
@@ -146,6 +146,80 @@ def pattern_mixed(stream, args):
     out["fp32_mixed"]["l1_error_vs_fp64"] = {f: float(e) for f, e in zip(["rho", "m_x", "m_y", "m_z", "E"], err)}
     out["fp32_mixed"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_mixed"]["ms_per_step"]
     return out
+
+
+def pattern_adjoint(stream, args):
+    """Gradient of J = sum_{x_i in [0.4,0.6]^3} m_i p_i(U^N) with respect to U^0
+    through N FP64 SSP-RK3 steps on the 64^3 periodic vortex with eight
+    Gaussian density bumps, checkpoints every 10 steps: cost of the recorded
+    forward run and of the reverse sweep against a plain forward run, and a
+    central-difference check along random directions."""
+    import numpy as np
+    import torch
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+    from paper_2007_00094_gb300.objectives import BoxPressure
+
+    mesh = W.vortex_mesh(args.adj_n)
+    U0 = W.bumpy_vortex_state(mesh)
+    N, every = args.adj_steps, 10
+    s = Solver(mesh, stream=stream)
+    J = BoxPressure(mesh.x, s.matrices()[4])
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    s.init_state(U0)
+    s.step(args.warmup)
+    s.synchronize()
+    s.init_state(U0)
+    fwd_ms, _ = timed(lambda: s.step(N))
+    s.synchronize()
+    s.init_state(U0)
+    rec_ms, _ = timed(lambda: s.adjoint_record(N, every))
+    seed = torch.as_tensor(J.gradient(s.get_state()), device="cuda")
+    s.profile(True)
+    bwd_ms, g = timed(lambda: s.adjoint_backward(seed))
+    prof = s.profile_read()
+    s.profile(False)
+    g = g.cpu().numpy()
+
+    def run(V):
+        s.init_state(V)
+        s.step(N)
+        return J(s.get_state())
+
+    # central differences of the forward run; the map is piecewise smooth,
+    # so the agreement is limited by the branch points a difference crosses
+    rng = np.random.default_rng(16)
+    fd_err = {1e-6: [], 1e-8: []}
+    for _ in range(args.adj_fd_directions):
+        v = rng.standard_normal(U0.shape) * np.abs(U0)
+        ad = float((g * v).sum())
+        for eps in fd_err:
+            fd = (run(U0 + eps * v) - run(U0 - eps * v)) / (2 * eps)
+            fd_err[eps].append(abs(fd - ad) / abs(ad))
+    s.close()
+    node_stages = mesh.n_nodes * 3 * N
+    adj = {k: v for k, v in prof.items() if k.startswith("adj_") and v[1]}
+    return {"config": {"workload": f"bumpy_vortex_{args.adj_n}^3_periodic_8_bumps_seed5", "nodes": mesh.n_nodes,
+                       "steps": N, "checkpoint_every": every,
+                       "functional": "sum over x_i in [0.4,0.6]^3 of m_i p_i(U^N)", "box_nodes": J.n_inside},
+            "value": node_stages / ((rec_ms + bwd_ms) * 1e-3), "unit": "node-stage gradient updates/s",
+            "forward_ms": fwd_ms, "record_ms": rec_ms, "backward_ms": bwd_ms,
+            "backward_over_forward": bwd_ms / fwd_ms, "gradient_over_forward": (rec_ms + bwd_ms) / fwd_ms,
+            "reverse_kernels_ms_per_launch": {k: v[0] / v[1] for k, v in adj.items()},
+            "backward_share_forward_recompute": sum(v[0] for k, v in prof.items() if not k.startswith("adj_"))
+            / sum(v[0] for v in prof.values()),
+            "fd_check": {"directions": args.adj_fd_directions,
+                         "max_rel_err": {f"{e:.0e}": (max(v) if v else None) for e, v in fd_err.items()}}}
 
 
 def _dist():
@@ -300,6 +374,9 @@ def main():
     ap.add_argument("--pattern-steps", type=int, default=5)
     ap.add_argument("--sod-n", type=int, default=128)
     ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
+    ap.add_argument("--adj-steps", type=int, default=100)
+    ap.add_argument("--adj-fd-directions", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -412,12 +489,13 @@ def main():
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "peak_source": "FP64 pipe from unit counts and max clock (nominal 1.25 TFLOP/s)",
                          "work": f"{FLOP_PER_NNZ[dom]:.0f} flop/nnz x {nnz} nnz per launch"},
-            "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
-            "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items()},
+            "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+            "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
             "clocks": clocks,
         }
         if not args.no_patterns:
-            line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args)}
+            line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
+                                "adjoint": pattern_adjoint(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -165,7 +165,8 @@ int64_t idp_launch_count(const idp_ctx* ctx);
  * on the context's stream around every kernel launch (Alg. 1 steps 0-6);
  * idp_profile(ctx, 0) stops recording.  idp_profile_read synchronises and
  * writes, per kernel id, the summed event time in milliseconds and the
- * launch count since recording started (arrays of IDP_N_KERNELS). */
+ * launch count since recording started (arrays of IDP_N_KERNELS); the
+ * reverse-mode calls record their kernels too. */
 enum {
   IDP_KERNEL_NODE = 0,        /* Step 0: per-node quantities */
   IDP_KERNEL_EDGE = 1,        /* Step 1: d_ij and alpha_i */
@@ -174,7 +175,16 @@ enum {
   IDP_KERNEL_FLUX_LIMIT = 4,  /* Step 4: P_ij and l_ij */
   IDP_KERNEL_LIMITER_PASS = 5,/* Step 5: limiter pass with new l_ij */
   IDP_KERNEL_FINAL = 6,       /* Step 6: last pass, boundary values, RK blend */
-  IDP_N_KERNELS = 7
+  /* reverse mode (idp_adjoint_*): one id per reversed step */
+  IDP_KERNEL_ADJ_FINAL = 7,   /* Step 6 reversed: boundary values, last pass */
+  IDP_KERNEL_ADJ_PASS = 8,    /* Step 5 reversed */
+  IDP_KERNEL_ADJ_FLUX = 9,    /* Step 4 reversed: P_ij, first limiter */
+  IDP_KERNEL_ADJ_LOW = 10,    /* Step 3 reversed: U^L, R_i, bounds */
+  IDP_KERNEL_ADJ_TAU = 11,    /* adjoint of tau_n: sum, CFL arg-min */
+  IDP_KERNEL_ADJ_DIAG = 12,   /* Step 2 reversed */
+  IDP_KERNEL_ADJ_EDGE = 13,   /* Step 1 reversed: alpha_i, fluxes, d_ij */
+  IDP_KERNEL_ADJ_GATHER = 14, /* transposed-entry gather of the input adjoint */
+  IDP_N_KERNELS = 15
 };
 idp_status idp_profile(idp_ctx* ctx, int enable);
 idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches);

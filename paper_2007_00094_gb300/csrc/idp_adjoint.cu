@@ -37,78 +37,160 @@ __device__ __forceinline__ void load5(const double* U, int64_t n, int64_t i, dou
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 // gl times the derivative of limiter(U, P, rho_min, rho_max, phi_min),
-// added to gU, gP and gb = (g rho_min, g rho_max, g phi_min).
+// added to gU, gP and gb = (g rho_min, g rho_max, g phi_min): one dual pass
+// over the eight scalars the limiter depends on (U0, P0, the coefficients
+// a0, a1, a2 of rho eps(t) and the three bounds), then the chain rule
+// through a0 = U0 U4 - |m_U|^2/2, a1 = U0 P4 + P0 U4 - m_U.m_P and
+// a2 = P0 P4 - |m_P|^2/2.
 __device__ void limiter_vjp(const double* U, const double* P, double rmin, double rmax, double pmin, double gl,
                             const LimiterParams& prm, double* gU, double* gP, double* gb) {
-  {
-    Dual<5> Ud[kFields], Pd[kFields];
+  LimiterLine<8> L;
+  L.U = U;
+  L.P = P;
+  L.U0 = dseed<8>(U[0], 0);
+  L.P0 = dseed<8>(P[0], 1);
+  L.a0 = dseed<8>(U[0] * U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]), 2);
+  L.a1 = dseed<8>(U[0] * P[4] + P[0] * U[4] - (U[1] * P[1] + U[2] * P[2] + U[3] * P[3]), 3);
+  L.a2 = dseed<8>(P[0] * P[4] - 0.5 * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]), 4);
+  const Dual<8> t = limiter_line(L, dseed<8>(rmin, 5), dseed<8>(rmax, 6), dseed<8>(pmin, 7), prm);
+  const double g0 = gl * t.d[2], g1 = gl * t.d[3], g2 = gl * t.d[4];
+  gU[0] += gl * t.d[0] + g0 * U[4] + g1 * P[4];
+  gP[0] += gl * t.d[1] + g1 * U[4] + g2 * P[4];
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      Ud[f] = dseed<5>(U[f], f);
-      Pd[f] = dconst<5>(P[f]);
-    }
-    const Dual<5> t = limiter_t(Ud, Pd, dconst<5>(rmin), dconst<5>(rmax), dconst<5>(pmin), prm);
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) gU[f] += gl * t.d[f];
+  for (int f = 1; f < 4; ++f) {
+    gU[f] -= g0 * U[f] + g1 * P[f];
+    gP[f] -= g1 * U[f] + g2 * P[f];
   }
-  {
-    Dual<5> Ud[kFields], Pd[kFields];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      Ud[f] = dconst<5>(U[f]);
-      Pd[f] = dseed<5>(P[f], f);
-    }
-    const Dual<5> t = limiter_t(Ud, Pd, dconst<5>(rmin), dconst<5>(rmax), dconst<5>(pmin), prm);
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) gP[f] += gl * t.d[f];
-  }
-  {
-    Dual<3> Ud[kFields], Pd[kFields];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      Ud[f] = dconst<3>(U[f]);
-      Pd[f] = dconst<3>(P[f]);
-    }
-    const Dual<3> t = limiter_t(Ud, Pd, dseed<3>(rmin, 0), dseed<3>(rmax, 1), dseed<3>(pmin, 2), prm);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) gb[q] += gl * t.d[q];
-  }
+  gU[4] += g0 * U[0] + g1 * P[0];
+  gP[4] += g1 * U[0] + g2 * P[0];
+  gb[0] += gl * t.d[5];
+  gb[1] += gl * t.d[6];
+  gb[2] += gl * t.d[7];
 }
 
-// out += sign * J^T g, J the Jacobian of U -> f(U).c at state u
-__device__ void flux_vjp(const double* u, double cx, double cy, double cz, const double* g, double sign, double* out) {
-  Dual<5> ud[kFields], F[kFields];
-#pragma unroll
-  for (int f = 0; f < kFields; ++f) ud[f] = dseed<5>(u[f], f);
-  flux_dot_t(ud, cx, cy, cz, F);
-#pragma unroll
-  for (int q = 0; q < kFields; ++q) {
-    double acc = 0.0;
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) acc += F[f].d[q] * g[f];
-    out[q] += sign * acc;
+// out += sign * J^T g, J the Jacobian of U -> f(U).c (eq. flux) at the state
+// u with 1/rho and H = (E + p)/rho.  With v = m/rho, A = g_m.m, B = g_m.c
+// and T = B + g_E v.c:
+//   d/drho = -(A/rho) v.c + 0.2|v|^2 T - g_E H v.c
+//   d/dm   = c (g_rho + A/rho + g_E H) + g_m v.c - 0.4 v T
+//   d/dE   = 0.4 T + g_E v.c
+__device__ __forceinline__ void flux_vjp(const double* u, double inv_rho, double H, double cx, double cy, double cz,
+                                         const double* g, double sign, double* out) {
+  const double vx = u[1] * inv_rho, vy = u[2] * inv_rho, vz = u[3] * inv_rho;
+  const double vc = vx * cx + vy * cy + vz * cz;
+  const double Ai = (g[1] * u[1] + g[2] * u[2] + g[3] * u[3]) * inv_rho;
+  const double T = g[1] * cx + g[2] * cy + g[3] * cz + g[4] * vc;
+  const double cc = g[0] + Ai + g[4] * H;
+  out[0] += sign * (0.2 * (vx * vx + vy * vy + vz * vz) * T - (Ai + g[4] * H) * vc);
+  out[1] += sign * (cx * cc + g[1] * vc - 0.4 * vx * T);
+  out[2] += sign * (cy * cc + g[2] * vc - 0.4 * vy * T);
+  out[3] += sign * (cz * cc + g[3] * vc - 0.4 * vz * T);
+  out[4] += sign * (0.4 * T + g[4] * vc);
+}
+
+// out += g * grad s(U), s = eta/rho: grad s = (s/(6 p rho)) (E, -m, rho) - (s/rho) e_rho
+__device__ __forceinline__ void entropy_s_vjp(const double* u, double s, double inv_rho, double inv_p, double g,
+                                              double* out) {
+  const double sc = g * s * inv_p * inv_rho * (1.0 / 6.0);
+  out[0] += sc * u[4] - g * s * inv_rho;
+  out[1] -= sc * u[1];
+  out[2] -= sc * u[2];
+  out[3] -= sc * u[3];
+  out[4] += sc * u[0];
+}
+
+__device__ __forceinline__ Side load_side(const double* U, const double* Q, int64_t n, int64_t i) {
+  Side s;
+  s.rho = U[i];
+  s.mx = U[n + i];
+  s.my = U[2 * n + i];
+  s.mz = U[3 * n + i];
+  s.inv_rho = Q[kQInvRho * n + i];
+  s.p = Q[kQP * n + i];
+  s.c = Q[kQC * n + i];
+  s.pm = Q[kQPm * n + i];
+  s.inv_p = Q[kQInvP * n + i];
+  return s;
+}
+
+// Adjoints of one side's primitives (normal velocity u, sound speed c,
+// pressure p, p^(-1/7)) to its conserved state, added to out.
+__device__ __forceinline__ void side_vjp(double nx, double ny, double nz, const Side& S, double gu, double gc,
+                                         double gp, double gpm, double* out) {
+  const double vx = S.mx * S.inv_rho, vy = S.my * S.inv_rho, vz = S.mz * S.inv_rho;
+  const double u = vx * nx + vy * ny + vz * nz;
+  // c = sqrt(1.4 p / rho), pm = p^(-1/7), u = m.n/rho, p = 0.4 (E - |m|^2/(2 rho))
+  const double gpt = gp + (0.5 * gc * S.c - gpm * S.pm * (1.0 / 7.0)) * S.inv_p;
+  out[0] += (-0.5 * gc * S.c - gu * u) * S.inv_rho + 0.2 * (vx * vx + vy * vy + vz * vz) * gpt;
+  out[1] += gu * nx * S.inv_rho - 0.4 * vx * gpt;
+  out[2] += gu * ny * S.inv_rho - 0.4 * vy * gpt;
+  out[3] += gu * nz * S.inv_rho - 0.4 * vz * gpt;
+  out[4] += 0.4 * gpt;
+}
+
+// Reverse of lambda_max (idp_device.cuh): adds g d lambda/dU_L to gL and
+// g d lambda/dU_R to gR, on the branches the forward evaluation takes.
+__device__ void lambda_max_vjp(double nx, double ny, double nz, const Side& L, const Side& R, double g, double* gL,
+                               double* gR) {
+  const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
+  const double uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
+  const double num0 = L.c + R.c - 0.2 * (uR - uL);
+  const double num = num0 > 0.0 ? num0 : 0.0;
+  const double den = L.c * L.pm + R.c * R.pm;
+  const double x = num / den;
+  const double x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
+  const double p_tr = x6 * x;
+  const bool left_high = L.p >= R.p;
+  const double p_max = left_high ? L.p : R.p;
+  const double p_low = left_high ? R.p : L.p;
+  const double rho_low = left_high ? R.rho : L.rho;
+  const double du = uR - uL;
+  const double dp = p_max - p_low;
+  const bool psi_negative = du < 0.0 && 2.0 * dp * dp < du * du * (rho_low * (2.4 * p_max + 0.4 * p_low));
+  const bool star_is_max = !psi_negative && p_max <= p_tr;
+  const double p_star = star_is_max ? p_max : p_tr;
+  const double k = 6.0 / 7.0;
+  const double zL = (p_star - L.p) * L.inv_p, zR = (p_star - R.p) * R.inv_p;
+  const double SL = sqrt(1.0 + k * fmax(zL, 0.0)), SR = sqrt(1.0 + k * fmax(zR, 0.0));
+  const double lam1 = uL - L.c * SL, lam3 = uR + R.c * SR;
+  const double a = fmax(-lam1, 0.0), b = fmax(lam3, 0.0);
+  double g1 = 0.0, g3 = 0.0;  // adjoints of lam1, lam3
+  if (a >= b) {
+    if (-lam1 >= 0.0) g1 = -g;
+  } else if (lam3 >= 0.0) {
+    g3 = g;
   }
-}
-
-// out += g * grad s(u), s = eta/rho
-__device__ void entropy_s_vjp(const double* u, double g, double* out) {
-  Dual<5> ud[kFields];
-#pragma unroll
-  for (int f = 0; f < kFields; ++f) ud[f] = dseed<5>(u[f], f);
-  const Dual<5> s = entropy_s(ud);
-#pragma unroll
-  for (int q = 0; q < kFields; ++q) out[q] += g * s.d[q];
-}
-
-// d_ij of the edge {i, j} (Step 1) as a function of the two states
-template <typename T>
-__device__ __forceinline__ T edge_d(const T* ui, const T* uj, double cx, double cy, double cz, double nc, double inv,
-                                    bool skew, double tx, double ty, double tz, double nt, double invt) {
-  const SideT<T> si = side_of_state(ui), sj = side_of_state(uj);
-  T dij = ui[0] * 0.0;
-  if (nc > 0.0) dij = lambda_max_t(cx * inv, cy * inv, cz * inv, si, sj) * nc;
-  if (!skew && nt > 0.0) dij = fmax(dij, lambda_max_t(tx * invt, ty * invt, tz * invt, sj, si) * nt);
-  return dij;
+  if (g1 == 0.0 && g3 == 0.0) return;
+  double guL = g1, guR = g3, gcL = -g1 * SL, gcR = g3 * SR, gpL = 0.0, gpR = 0.0, gstar = 0.0;
+  if (g1 != 0.0 && zL >= 0.0) {
+    const double gz = -g1 * L.c * k / (2.0 * SL);
+    gstar += gz * L.inv_p;
+    gpL -= gz * p_star * L.inv_p * L.inv_p;
+  }
+  if (g3 != 0.0 && zR >= 0.0) {
+    const double gz = g3 * R.c * k / (2.0 * SR);
+    gstar += gz * R.inv_p;
+    gpR -= gz * p_star * R.inv_p * R.inv_p;
+  }
+  double gpmL = 0.0, gpmR = 0.0;
+  if (star_is_max) {
+    if (left_high) gpL += gstar; else gpR += gstar;
+  } else if (gstar != 0.0) {
+    const double gx = 7.0 * x6 * gstar;
+    const double gnum = gx / den, gden = -x / den * gx;
+    gcL += L.pm * gden;
+    gcR += R.pm * gden;
+    gpmL = L.c * gden;
+    gpmR = R.c * gden;
+    if (num0 >= 0.0) {
+      gcL += gnum;
+      gcR += gnum;
+      guL += 0.2 * gnum;
+      guR -= 0.2 * gnum;
+    }
+  }
+  side_vjp(nx, ny, nz, L, guL, gcL, gpL, gpmL, gL);
+  side_vjp(nx, ny, nz, R, guR, gcR, gpR, gpmR, gR);
 }
 
 // Step 6 reverse: boundary post-processing and the last limiter pass
@@ -339,7 +421,7 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
 #pragma unroll
   for (int f = 0; f < kFields; ++f) gUi[f] = gUL[f];
   // -f_i . s_i
-  flux_vjp(ui, G.csx[r], G.csy[r], G.csz[r], gR, -1.0, gUi);
+  flux_vjp(ui, inv_rho_i, h_i, G.csx[r], G.csy[r], G.csz[r], gR, -1.0, gUi);
   const double a_i = alpha[r];
   const double two_tau_m = 2.0 * tau * G.inv_mi[r];
   double ga_i = 0.0, gtau = 0.0;
@@ -557,6 +639,12 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
       gUi[q] += ge[0] * e0.d[q] + ge[1] * e1.d[q] + ge[2] * e2.d[q] + ge[3] * e3.d[q] + ge[4] * e4.d[q] +
                 gs * sd.d[q] + gphi * phid.d[q];
   }
+  // per-entry terms; U_i's flux adjoint is collected per direction,
+  // sum_j J(U_i; c_ij)^T g_ij = sum_d J(U_i; e_d)^T (sum_j c_ij,d g_ij)
+  const Side si = load_side(U, Q, n, r);
+  const double inv_p_i = Q[kQInvP * n + r];
+  double Gx[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, Gy[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0},
+         Gz[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
   double gsi = 0.0;  // adjoint of s_i through a_i
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
@@ -565,16 +653,22 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
     const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
     double uj[kFields], gj[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gdf[kFields];
     load5(U, n, j, uj);
+    const double inv_rho_j = Q[kQInvRho * n + j];
     // (f_j - f_i).c_ij: adjoint from Step 3 and from b_i
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) gdf[f] = A.gdF[f * ns + p] + gb[f];
-    flux_vjp(uj, cx, cy, cz, gdf, 1.0, gj);
-    flux_vjp(ui, cx, cy, cz, gdf, -1.0, gUi);
+    for (int f = 0; f < kFields; ++f) {
+      gdf[f] = A.gdF[f * ns + p] + gb[f];
+      Gx[f] += cx * gdf[f];
+      Gy[f] += cy * gdf[f];
+      Gz[f] += cz * gdf[f];
+    }
+    flux_vjp(uj, inv_rho_j, Q[kQH * n + j], cx, cy, cz, gdf, 1.0, gj);
     // a_i term (s_j - s_i)(m_j . c_ij)
     if (ga != 0.0) {
       const double mc = uj[1] * cx + uj[2] * cy + uj[3] * cz;
-      const double ds = Q[kQS * n + j] - s_i;
-      entropy_s_vjp(uj, mc * ga, gj);
+      const double sj = Q[kQS * n + j];
+      const double ds = sj - s_i;
+      entropy_s_vjp(uj, sj, inv_rho_j, Q[kQInvP * n + j], mc * ga, gj);
       gj[1] += ds * cx * ga;
       gj[2] += ds * cy * ga;
       gj[3] += ds * cz * ga;
@@ -585,33 +679,32 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
       const int64_t pt = G.tpos[p];
       const double gdedge = A.gd[p] + A.gd[pt];
       if (gdedge != 0.0) {
-        const bool skew = (G.flags[p] & kEntrySkew) != 0;
-        const double nc = G.cn[p], inv = G.inv_cn[p], nt = G.cn[pt], invt = G.inv_cn[pt];
-        const double tx = G.cx[pt], ty = G.cy[pt], tz = G.cz[pt];
-        Dual<5> a5[kFields], b5[kFields];
-#pragma unroll
-        for (int f = 0; f < kFields; ++f) {
-          a5[f] = dseed<5>(ui[f], f);
-          b5[f] = dconst<5>(uj[f]);
+        const Side sj = load_side(U, Q, n, j);
+        const double nc = G.cn[p];
+        bool transposed = false;
+        if (!(G.flags[p] & kEntrySkew) && G.cn[pt] > 0.0) {
+          const double d1 = nc > 0.0 ? lambda_max(cx * G.inv_cn[p], cy * G.inv_cn[p], cz * G.inv_cn[p], si, sj) * nc
+                                     : 0.0;
+          const double it = G.inv_cn[pt];
+          const double d2 = lambda_max(G.cx[pt] * it, G.cy[pt] * it, G.cz[pt] * it, sj, si) * G.cn[pt];
+          transposed = !(d1 >= d2);
         }
-        const Dual<5> di = edge_d(a5, b5, cx, cy, cz, nc, inv, skew, tx, ty, tz, nt, invt);
-#pragma unroll
-        for (int f = 0; f < kFields; ++f) {
-          a5[f] = dconst<5>(ui[f]);
-          b5[f] = dseed<5>(uj[f], f);
-        }
-        const Dual<5> dj = edge_d(a5, b5, cx, cy, cz, nc, inv, skew, tx, ty, tz, nt, invt);
-#pragma unroll
-        for (int q = 0; q < kFields; ++q) {
-          gUi[q] += gdedge * di.d[q];
-          gj[q] += gdedge * dj.d[q];
+        if (transposed) {
+          const double it = G.inv_cn[pt];
+          lambda_max_vjp(G.cx[pt] * it, G.cy[pt] * it, G.cz[pt] * it, sj, si, gdedge * G.cn[pt], gj, gUi);
+        } else if (nc > 0.0) {
+          const double inv = G.inv_cn[p];
+          lambda_max_vjp(cx * inv, cy * inv, cz * inv, si, sj, gdedge * nc, gUi, gj);
         }
       }
     }
 #pragma unroll
     for (int f = 0; f < kFields; ++f) A.gU_tr[f * ns + p] += gj[f];
   }
-  if (gsi != 0.0) entropy_s_vjp(ui, gsi, gUi);
+  flux_vjp(ui, inv_rho_i, h_i, 1.0, 0.0, 0.0, Gx, -1.0, gUi);
+  flux_vjp(ui, inv_rho_i, h_i, 0.0, 1.0, 0.0, Gy, -1.0, gUi);
+  flux_vjp(ui, inv_rho_i, h_i, 0.0, 0.0, 1.0, Gz, -1.0, gUi);
+  if (gsi != 0.0) entropy_s_vjp(ui, s_i, inv_rho_i, inv_p_i, gsi, gUi);
 #pragma unroll
   for (int f = 0; f < kFields; ++f) A.gU_own[f * n + r] += gUi[f];
 }
@@ -644,9 +737,17 @@ __global__ void k_axpby(double* __restrict__ out, double a, const double* __rest
 }  // namespace
 
 int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const AdjointBuffers& A, const StageConfig& C,
-                         const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s) {
+                         const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s,
+                         Profiler* prof) {
   const unsigned grid = (unsigned)((G.n + kB - 1) / kB);
   const size_t n = (size_t)G.n, ns = (size_t)G.n_slots;
+  const bool timed = prof && prof->enabled;
+  int launches = 0;
+  auto run = [&](int id, auto&& launch) {
+    if (timed) prof->begin(id, s);
+    launch();
+    if (timed) prof->end(s);
+  };
   cudaMemsetAsync(A.gU_own, 0, sizeof(double) * kFields * n, s);
   cudaMemsetAsync(A.gU_tr, 0, sizeof(double) * kFields * ns, s);
   cudaMemsetAsync(A.gd, 0, sizeof(double) * ns, s);
@@ -654,20 +755,24 @@ int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const Adjo
   cudaMemsetAsync(A.gphi_tr, 0, sizeof(double) * ns, s);
   // traced intermediates: P and l of Step 4 (tP, tl4), the state and l
   // after the first pass (tU5, tl5), P' of the first pass (left in B.P)
-  ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A);
-  ka_pass<<<grid, kB, 0, s>>>(G, C, B.tU5, B.tP, B.P, B.tl4, B.tl5, B.bnd, A);
-  ka_flux<<<grid, kB, 0, s>>>(G, C, Uin, B.UL, B.tP, B.tl4, B.d, B.alpha, B.bnd, A);
-  ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.alpha, A);
-  ka_tau<<<1, kB, 0, s>>>(G, A, tau_computed ? 1 : 0);
-  if (tau_computed) {
-    cudaMemsetAsync(A.argmin, 0xff, 2 * sizeof(unsigned long long), s);
-    ka_cfl_min<<<grid, kB, 0, s>>>(G, B.d, A);
-    ka_cfl_arg<<<grid, kB, 0, s>>>(G, B.d, A);
-  }
-  ka_diag<<<grid, kB, 0, s>>>(G, C, B.d, A, tau_computed ? 1 : 0);
-  ka_edge<<<grid, kB, 0, s>>>(G, Uin, B.node, A);
-  ka_gather<<<grid, kB, 0, s>>>(G, A, gIn);
-  return tau_computed ? 10 : 8;
+  run(kKAdjFinal, [&] { ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A); });
+  run(kKAdjPass, [&] { ka_pass<<<grid, kB, 0, s>>>(G, C, B.tU5, B.tP, B.P, B.tl4, B.tl5, B.bnd, A); });
+  run(kKAdjFlux, [&] { ka_flux<<<grid, kB, 0, s>>>(G, C, Uin, B.UL, B.tP, B.tl4, B.d, B.alpha, B.bnd, A); });
+  run(kKAdjLow, [&] { ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.alpha, A); });
+  launches += 4;
+  run(kKAdjTau, [&] {
+    ka_tau<<<1, kB, 0, s>>>(G, A, tau_computed ? 1 : 0);
+    if (tau_computed) {
+      cudaMemsetAsync(A.argmin, 0xff, 2 * sizeof(unsigned long long), s);
+      ka_cfl_min<<<grid, kB, 0, s>>>(G, B.d, A);
+      ka_cfl_arg<<<grid, kB, 0, s>>>(G, B.d, A);
+    }
+  });
+  launches += tau_computed ? 3 : 1;
+  run(kKAdjDiag, [&] { ka_diag<<<grid, kB, 0, s>>>(G, C, B.d, A, tau_computed ? 1 : 0); });
+  run(kKAdjEdge, [&] { ka_edge<<<grid, kB, 0, s>>>(G, Uin, B.node, A); });
+  run(kKAdjGather, [&] { ka_gather<<<grid, kB, 0, s>>>(G, A, gIn); });
+  return launches + 3;
 }
 
 void launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t count, cudaStream_t s) {

@@ -46,7 +46,8 @@ struct AdjointBuffers {
 // Otherwise this stage's adjoint of tau_n is added to A.gtau[0].
 // Returns the number of kernel launches.
 int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const AdjointBuffers& A, const StageConfig& C,
-                         const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s);
+                         const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s,
+                         Profiler* prof = nullptr);
 
 // out = a x + b y over count doubles (y may be null: out = a x).
 void launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t count, cudaStream_t s);

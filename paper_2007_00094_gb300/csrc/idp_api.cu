@@ -739,8 +739,9 @@ idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, con
   if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
   IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
   int64_t launches = launch(ctx, ctx->a_in, ctx->a_out, ctx->a_in, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false,
-                            true, s, nullptr);
-  launches += idp::launch_adjoint_stage(ctx->G, ctx->B, ctx->A, ctx->C, ctx->a_in, ctx->a_e, ctx->a_tmp, !(tau > 0.0), s);
+                            true, s, &ctx->prof);
+  launches += idp::launch_adjoint_stage(ctx->G, ctx->B, ctx->A, ctx->C, ctx->a_in, ctx->a_e, ctx->a_tmp, !(tau > 0.0), s,
+                                        &ctx->prof);
   ctx->launches = launches;
   IDP_CUDA(ctx, cudaGetLastError());
   IDP_CUDA(ctx, cudaMemcpyAsync(gU, ctx->a_tmp, bytes, out, s));
@@ -822,27 +823,27 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
     // recompute the segment's step inputs and first two stage states
     IDP_CUDA(ctx, cudaMemcpyAsync(U0(0), ctx->rec_ckpt + (size_t)c * n5, bytes, cudaMemcpyDeviceToDevice, s));
     for (int q = 0; q < len; ++q) {
-      launches += launch(ctx, U0(q), U1(q), U0(q), idp::kBlendNone, 0, false, false, false, s, nullptr);
-      launches += launch(ctx, U1(q), U2(q), U0(q), idp::kBlendStage2, 1, false, false, false, s, nullptr);
+      launches += launch(ctx, U0(q), U1(q), U0(q), idp::kBlendNone, 0, false, false, false, s, &ctx->prof);
+      launches += launch(ctx, U1(q), U2(q), U0(q), idp::kBlendStage2, 1, false, false, false, s, &ctx->prof);
       if (q + 1 < len)
-        launches += launch(ctx, U2(q), U0(q + 1), U0(q), idp::kBlendStage3, 1, false, false, false, s, nullptr);
+        launches += launch(ctx, U2(q), U0(q + 1), U0(q), idp::kBlendStage3, 1, false, false, false, s, &ctx->prof);
     }
     for (int q = len - 1; q >= 0; --q) {
       IDP_CUDA(ctx, cudaMemcpyAsync(G.tau, ctx->rec_tau + first + q, sizeof(double), cudaMemcpyDeviceToDevice, s));
       IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
       // stage 3: U^{n+1} = U^n/3 + 2/3 E(U2)
-      launches += launch(ctx, U2(q), scr, U2(q), idp::kBlendNone, 1, false, false, true, s, nullptr);
+      launches += launch(ctx, U2(q), scr, U2(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
       idp::launch_axpby(gE, 2.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
       idp::launch_axpby(acc, 1.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U2(q), gE, tmp, false, s);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U2(q), gE, tmp, false, s, &ctx->prof);
       // stage 2: U2 = 3/4 U^n + 1/4 E(U1)
-      launches += launch(ctx, U1(q), scr, U1(q), idp::kBlendNone, 1, false, false, true, s, nullptr);
+      launches += launch(ctx, U1(q), scr, U1(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
       idp::launch_axpby(gE, 0.25, tmp, 0.0, nullptr, (int64_t)n5, s);
       idp::launch_axpby(acc, 0.75, tmp, 1.0, acc, (int64_t)n5, s);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U1(q), gE, tmp, false, s);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U1(q), gE, tmp, false, s, &ctx->prof);
       // stage 1: U1 = E(U^n), tau_n computed here
-      launches += launch(ctx, U0(q), scr, U0(q), idp::kBlendNone, 0, false, false, true, s, nullptr);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U0(q), tmp, gE, true, s);
+      launches += launch(ctx, U0(q), scr, U0(q), idp::kBlendNone, 0, false, false, true, s, &ctx->prof);
+      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U0(q), tmp, gE, true, s, &ctx->prof);
       idp::launch_axpby(g, 1.0, gE, 1.0, acc, (int64_t)n5, s);
       launches += 5;  // the blends
     }

@@ -1,11 +1,11 @@
-// Forward-mode dual numbers and the stage's per-entry functions written for
-// a generic scalar type, for the local Jacobians of the adjoint.
+// Forward-mode dual numbers for the local derivatives of the adjoint: the
+// per-node quantities of Step 0 and the limiter (Alg. 2 / Alg. 3).
 //
-// Dual<N> carries a value and N directional derivatives.  Every function
-// below mirrors its FP64 counterpart in idp_device.cuh / idp_stage.cu
-// operation by operation; branches (min, max, clamps, the limiter's exits)
-// are decided on values, so the derivatives are those of the branch the
-// forward pass takes.
+// Dual<N> carries a value and N directional derivatives.  The functions
+// below mirror their FP64 counterparts in idp_device.cuh / idp_stage.cu
+// operation by operation; branches (clamps, the limiter's exits) are decided
+// on values, so the derivatives are those of the branch the forward pass
+// takes.
 #pragma once
 #include "idp_device.cuh"
 
@@ -221,126 +221,107 @@ __device__ __forceinline__ T entropy_phi(const T* u) {
   return eps * r7;
 }
 
-// f(U) . c of eq. (flux)
-template <typename T>
-__device__ __forceinline__ void flux_dot_t(const T* u, double cx, double cy, double cz, T* f) {
-  const T inv_rho = 1.0 / u[0];
-  const T eps = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * inv_rho;
-  const T p = 0.4 * eps;
-  const T h = (u[4] + p) * inv_rho;
-  const T mc = u[1] * cx + u[2] * cy + u[3] * cz;
-  f[0] = mc;
-  f[1] = u[1] * inv_rho * mc + p * cx;
-  f[2] = u[2] * inv_rho * mc + p * cy;
-  f[3] = u[3] * inv_rho * mc + p * cz;
-  f[4] = h * mc;
+// ---------------------------------------------------------------------------
+// The limiter as a function of its line scalars
+// ---------------------------------------------------------------------------
+
+// limiter(U, P, bounds) depends on U and P only through rho(t) = U0 + t P0
+// and the quadratic rho eps(t) = a0 + a1 t + a2 t^2 along U + t P, with
+// a0 = rho eps(U), a1 = U0 P4 + P0 U4 - m_U.m_P, a2 = P0 P4 - |m_P|^2/2.
+// LimiterLine carries these five scalars as duals (plus U and P in FP64):
+// values, and with them every branch, are evaluated exactly as in the FP64
+// limiter, derivatives through the line scalars.
+template <int N>
+struct LimiterLine {
+  const double* U;
+  const double* P;
+  Dual<N> U0, P0, a0, a1, a2;
+};
+
+template <int N>
+__device__ __forceinline__ Dual<N> line_rho_eps(const LimiterLine<N>& L, const Dual<N>& t, Dual<N>* rho) {
+  double r;
+  Dual<N> out;
+  out.v = rho_eps_at(L.U, L.P, t.v, &r);
+  rho->v = r;
+  const double slope = L.a1.v + 2.0 * L.a2.v * t.v;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    rho->d[q] = L.U0.d[q] + t.v * L.P0.d[q] + L.P0.v * t.d[q];
+    out.d[q] = L.a0.d[q] + t.v * (L.a1.d[q] + t.v * L.a2.d[q]) + slope * t.d[q];
+  }
+  return out;
 }
 
-// two-rarefaction bound of Sec. 3.7 (mirror of lambda_max)
-template <typename T>
-__device__ __forceinline__ T lambda_max_t(double nx, double ny, double nz, const SideT<T>& L, const SideT<T>& R) {
-  const T uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
-  const T uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
-  T num = L.c + R.c - 0.2 * (uR - uL);
-  if (val(num) < 0.0) num = num * 0.0;
-  const T x = num / (L.c * L.pm + R.c * R.pm);
-  const T x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
-  const T p_tr = x6 * x;
-  const bool left_high = val(L.p) >= val(R.p);
-  const T p_max = left_high ? L.p : R.p;
-  const T p_low = left_high ? R.p : L.p;
-  const T rho_low = left_high ? R.rho : L.rho;
-  const double du = val(uR) - val(uL);
-  const double dp = val(p_max) - val(p_low);
-  const bool psi_negative =
-      du < 0.0 && 2.0 * dp * dp < du * du * (val(rho_low) * (2.4 * val(p_max) + 0.4 * val(p_low)));
-  const T p_star = psi_negative ? p_tr : fmin(p_max, p_tr);
-  const double k = 6.0 / 7.0;
-  const T lam1 = uL - L.c * sqrt(1.0 + k * fmax((p_star - L.p) * L.inv_p, 0.0));
-  const T lam3 = uR + R.c * sqrt(1.0 + k * fmax((p_star - R.p) * R.inv_p, 0.0));
-  return fmax(fmax(-lam1, 0.0), fmax(lam3, 0.0));
+template <int N>
+__device__ __forceinline__ Dual<N> line_drho_eps(const LimiterLine<N>& L, const Dual<N>& t) {
+  Dual<N> out;
+  out.v = drho_eps_at(L.U, L.P, t.v);
+#pragma unroll
+  for (int q = 0; q < N; ++q) out.d[q] = L.a1.d[q] + 2.0 * (t.v * L.a2.d[q] + L.a2.v * t.d[q]);
+  return out;
 }
 
-template <typename T>
-__device__ __forceinline__ T rho_eps_at_t(const T* U, const T* P, const T& t, T* rho_out) {
-  const T r = U[0] + t * P[0];
-  const T m1 = U[1] + t * P[1], m2 = U[2] + t * P[2], m3 = U[3] + t * P[3];
-  const T E = U[4] + t * P[4];
-  *rho_out = r;
-  return r * E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3);
-}
-
-template <typename T>
-__device__ __forceinline__ T drho_eps_at_t(const T* U, const T* P, const T& t) {
-  const T r = U[0] + t * P[0];
-  const T m1 = U[1] + t * P[1], m2 = U[2] + t * P[2], m3 = U[3] + t * P[3];
-  const T E = U[4] + t * P[4];
-  return P[0] * E + r * P[4] - (m1 * P[1] + m2 * P[2] + m3 * P[3]);
-}
-
-template <typename T>
-__device__ __forceinline__ double psi_slack_t(const T& rho_eps, const T& phi_term) {
-  return 1e-13 * (::fabs(val(rho_eps)) + ::fabs(val(phi_term)));
-}
-
-// limiter.compute of Alg. 2 / Alg. 3 (mirror of limiter in idp_device.cuh)
-template <typename T>
-__device__ __forceinline__ T limiter_t(const T* U, const T* P, const T& rho_min, const T& rho_max, const T& phi_min,
-                                       const LimiterParams& prm) {
-  T tL = U[0] * 0.0, tR = tL + 1.0;
-  const T rhoU = U[0], rhoP = P[0];
-  if (val(rhoU) + val(tR) * val(rhoP) > val(rho_max) && val(rhoP) != 0.0) tR = fabs(rho_max - rhoU) / fabs(rhoP);
-  if (val(rhoU) + val(tR) * val(rhoP) < val(rho_min) && val(rhoP) != 0.0) tR = fabs(rho_min - rhoU) / fabs(rhoP);
-  if (val(tR) < 0.0) tR = tR * 0.0;
-  if (val(tR) > 1.0) tR = tR * 0.0 + 1.0;
-  T psiL = tL, powL = tL;
+// Mirror of limiter() in idp_device.cuh (Alg. 2 / Alg. 3 with the same
+// safeguards, margins and exits), returning t_L as a dual.
+template <int N>
+__device__ __forceinline__ Dual<N> limiter_line(const LimiterLine<N>& L, const Dual<N>& rho_min,
+                                                const Dual<N>& rho_max, const Dual<N>& phi_min,
+                                                const LimiterParams& prm) {
+  Dual<N> tL = dconst<N>(0.0), tR = dconst<N>(1.0);
+  const Dual<N>&rhoU = L.U0, &rhoP = L.P0;
+  if (rhoU.v + tR.v * rhoP.v > rho_max.v && rhoP.v != 0.0) tR = fabs(rho_max - rhoU) / fabs(rhoP);
+  if (rhoU.v + tR.v * rhoP.v < rho_min.v && rhoP.v != 0.0) tR = fabs(rho_min - rhoU) / fabs(rhoP);
+  if (tR.v < 0.0) tR = dconst<N>(0.0);
+  if (tR.v > 1.0) tR = dconst<N>(1.0);
+  Dual<N> psiL = tL, powL = tL;
   bool haveL = false;
   for (int step = 0; step < prm.newton_max; ++step) {
-    T rR;
-    const T reR = rho_eps_at_t(U, P, tR, &rR);
-    const T powR = pow_12_5_t(rR);
-    const T psiR = reR - phi_min * powR;
-    if (val(psiR) >= -psi_slack_t(reR, phi_min * powR)) {
+    Dual<N> rR;
+    const Dual<N> reR = line_rho_eps(L, tR, &rR);
+    const Dual<N> powR = pow_12_5_t(rR);
+    const Dual<N> psiR = reR - phi_min * powR;
+    if (psiR.v >= -psi_slack(reR.v, phi_min.v * powR.v)) {
       tL = tR;
       break;
     }
     if (!haveL) {
-      T rL;
-      const T reL = rho_eps_at_t(U, P, tL, &rL);
+      Dual<N> rL;
+      const Dual<N> reL = line_rho_eps(L, tL, &rL);
       powL = pow_12_5_t(rL);
       psiL = reL - phi_min * powL;
       haveL = true;
     }
     const double tol =
-        prm.newton_tol * (val(U[0]) * val(U[4]) - 0.5 * (val(U[1]) * val(U[1]) + val(U[2]) * val(U[2]) + val(U[3]) * val(U[3])));
-    if (val(psiL) <= tol) break;
-    const T rhoL = U[0] + tL * P[0];
-    const T dpsiL = drho_eps_at_t(U, P, tL) - phi_min * 2.4 * (powL / rhoL) * P[0];
-    const T dpsiR = drho_eps_at_t(U, P, tR) - phi_min * 2.4 * (powR / rR) * P[0];
-    const T scaling = 1.0 / (tR - tL + prm.newton_eps);
-    const T d12 = (psiR - psiL) * scaling;
-    const T d112 = (d12 - dpsiL) * scaling;
-    const T d122 = (dpsiR - d12) * scaling;
-    T lamL = dpsiL * dpsiL - 4.0 * psiL * d112;
-    T lamR = dpsiR * dpsiR - 4.0 * psiR * d122;
-    if (val(lamL) < 0.0) lamL = lamL * 0.0;
-    if (val(lamR) < 0.0) lamR = lamR * 0.0;
-    T nL = tL - 2.0 * psiL / (dpsiL - sqrt(lamL));
-    T nR = tR - 2.0 * psiR / (dpsiR - sqrt(lamR));
-    if (!(val(nL) >= val(tL))) nL = tL;
-    if (!(val(nL) <= val(tR))) nL = tR;
-    T rN;
-    const T reN = rho_eps_at_t(U, P, nL, &rN);
-    const T powN = pow_12_5_t(rN);
-    const T psiN = reN - phi_min * powN;
-    if (val(psiN) < -psi_slack_t(reN, phi_min * powN)) {
+        prm.newton_tol * (L.U[0] * L.U[4] - 0.5 * (L.U[1] * L.U[1] + L.U[2] * L.U[2] + L.U[3] * L.U[3]));
+    if (psiL.v <= tol) break;
+    const Dual<N> rhoL = rhoU + tL * rhoP;
+    const Dual<N> dpsiL = line_drho_eps(L, tL) - phi_min * 2.4 * (powL / rhoL) * rhoP;
+    const Dual<N> dpsiR = line_drho_eps(L, tR) - phi_min * 2.4 * (powR / rR) * rhoP;
+    const Dual<N> scaling = 1.0 / (tR - tL + prm.newton_eps);
+    const Dual<N> d12 = (psiR - psiL) * scaling;
+    const Dual<N> d112 = (d12 - dpsiL) * scaling;
+    const Dual<N> d122 = (dpsiR - d12) * scaling;
+    Dual<N> lamL = dpsiL * dpsiL - 4.0 * psiL * d112;
+    Dual<N> lamR = dpsiR * dpsiR - 4.0 * psiR * d122;
+    if (lamL.v < 0.0) lamL = dconst<N>(0.0);
+    if (lamR.v < 0.0) lamR = dconst<N>(0.0);
+    Dual<N> nL = tL - 2.0 * psiL / (dpsiL - sqrt(lamL));
+    Dual<N> nR = tR - 2.0 * psiR / (dpsiR - sqrt(lamR));
+    if (!(nL.v >= tL.v)) nL = tL;
+    if (!(nL.v <= tR.v)) nL = tR;
+    Dual<N> rN;
+    const Dual<N> reN = line_rho_eps(L, nL, &rN);
+    const Dual<N> powN = pow_12_5_t(rN);
+    const Dual<N> psiN = reN - phi_min * powN;
+    if (psiN.v < -psi_slack(reN.v, phi_min.v * powN.v)) {
       nL = tL;
     } else {
       psiL = psiN;
       powL = powN;
     }
-    if (!(val(nR) >= val(nL))) nR = nL;
-    if (!(val(nR) <= val(tR))) nR = tR;
+    if (!(nR.v >= nL.v)) nR = nL;
+    if (!(nR.v <= tR.v)) nR = tR;
     tL = nL;
     tR = nR;
   }

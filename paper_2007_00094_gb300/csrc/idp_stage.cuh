@@ -134,7 +134,25 @@ __device__ __forceinline__ void reduce_tau_candidate(const DeviceGraph& G, int64
 }
 
 // Kernel ids of one euler_step (also the order of idp_profile_read).
-enum KernelId : int { kKNode = 0, kKEdge, kKDiag, kKLowOrder, kKFluxLimit, kKLimiterPass, kKFinal, kNumKernels };
+enum KernelId : int {
+  kKNode = 0,
+  kKEdge,
+  kKDiag,
+  kKLowOrder,
+  kKFluxLimit,
+  kKLimiterPass,
+  kKFinal,
+  // reverse mode
+  kKAdjFinal,
+  kKAdjPass,
+  kKAdjFlux,
+  kKAdjLow,
+  kKAdjTau,
+  kKAdjDiag,
+  kKAdjEdge,
+  kKAdjGather,
+  kNumKernels
+};
 
 // Optional per-kernel timing: CUDA events recorded on the launch stream
 // around each kernel; read back (and synchronised) by the owner.

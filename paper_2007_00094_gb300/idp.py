@@ -34,7 +34,8 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
             "idp_adjoint_record", "idp_adjoint_backward"]
 NOALLOC_MAX_NODES = 2097152
-KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final"]
+KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
+           "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
 
 
 class IdpConfig(C.Structure):

@@ -228,3 +228,77 @@ def test_adjoint_rejects_unsupported_configurations():
     with pytest.raises(IdpError) as e:
         s.adjoint_record(0)
     assert e.value.status == 1
+
+
+def _box_pressure_case():
+    from paper_2007_00094_gb300.objectives import BoxPressure
+    mesh = W.vortex_mesh(16, jitter=0.2, seed=3)
+    U = W.bumpy_vortex_state(mesh)
+    s = _solver(mesh)
+    return mesh, U, s, BoxPressure(mesh.x, s.matrices()[4])
+
+
+def test_box_pressure_gradient_matches_reference_gradient():
+    """The adjoint workload at reduced size (16^3 jittered periodic vortex with
+    eight density bumps, J = sum_{x_i in [0.4,0.6]^3} m_i p_i after two
+    SSP-RK3 steps) against torch.autograd through the PyTorch restatement.
+    Measured: 2e-11 relative (2-norm) after 8 steps; the isentropic vortex
+    keeps the limiter near its ill-conditioned point, where rounding of the
+    traced values is amplified."""
+    import oracle as O
+    from oracle import torch_stage as T
+    mesh, U, s, J = _box_pressure_case()
+    s.init_state(U)
+    s.adjoint_record(2, checkpoint_every=1)
+    UN = s.get_state()
+    g = s.adjoint_backward(J.gradient(UN))
+    tm = T.TorchMesh(O.assemble(mesh))
+    U0 = torch.as_tensor(U).clone().requires_grad_(True)
+    V = U0
+    for _ in range(2):
+        V, _ = T.ssprk3_step(tm, V)
+    (g_ref,) = torch.autograd.grad((torch.as_tensor(J.gradient(V.detach().numpy())) * V).sum(), (U0,))
+    err = rel_field_err_l2(g, g_ref.numpy())
+    assert err.max() <= 1e-9, err
+
+
+def test_box_pressure_gradient_against_finite_differences():
+    """The same workload over six steps (checkpoints every 5): the gradient
+    against central differences of the CUDA forward run with eps = 1e-7
+    (relative to the state) along 16 random directions and along 64 random
+    single components.  The map is only piecewise smooth (limiter branches and
+    Newton exits, min/max of bounds and wavespeeds, the CFL arg-min), and
+    differences of that width cross branch points; measured errors stay below
+    1e-2 of the largest directional derivative (directions) and of the largest
+    gradient entry of the field (components), and shrink as eps does, while
+    the adjoint itself matches the reference gradient to rounding."""
+    mesh, U, s, J = _box_pressure_case()
+    steps = 6
+    s.init_state(U)
+    s.adjoint_record(steps, checkpoint_every=5)
+    g = s.adjoint_backward(J.gradient(s.get_state()))
+    assert np.all(np.isfinite(g)) and np.abs(g).max() > 0.0
+
+    def run(V):
+        s.init_state(V)
+        s.step(steps)
+        return J(s.get_state())
+
+    rng = np.random.default_rng(12)
+    eps = 1e-7
+    fd, ad = [], []
+    for _ in range(16):
+        v = rng.standard_normal(U.shape) * np.abs(U)
+        fd.append((run(U + eps * v) - run(U - eps * v)) / (2 * eps))
+        ad.append(float((g * v).sum()))
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.abs(fd - ad).max() <= 1e-2 * np.abs(ad).max(), (fd, ad)
+    gmax = np.abs(g).max(axis=1)
+    for _ in range(64):
+        f, i = int(rng.integers(5)), int(rng.integers(mesh.n_nodes))
+        h = eps * max(abs(U[f, i]), 1e-3)
+        Up, Um = U.copy(), U.copy()
+        Up[f, i] += h
+        Um[f, i] -= h
+        d = (run(Up) - run(Um)) / (2 * h)
+        assert abs(d - g[f, i]) <= 1e-2 * gmax[f], (f, i, d, g[f, i])
