@@ -377,6 +377,8 @@ def main():
     ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
     ap.add_argument("--adj-steps", type=int, default=100)
     ap.add_argument("--adj-fd-directions", type=int, default=2)
+    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint"],
+                    help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
@@ -396,6 +398,11 @@ def main():
     from paper_2007_00094_gb300.idp import Solver
 
     torch.cuda.set_device(local)
+    if args.only:
+        build.build()
+        run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint}[args.only]
+        print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
+        return
     dist = None
     if ws > 1:
         import torch.distributed as dist

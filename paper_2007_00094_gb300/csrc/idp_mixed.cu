@@ -14,9 +14,9 @@
 //     margin m = 1e-6 (|rho eps| + phi_min rho^(gamma+1)), several times the
 //     FP32 error of that deviation, so an accepted t keeps Psi >= 0 in FP64;
 //     the density interval cuts against FP64 gaps rho_max - rho(U), rho_min -
-//     rho(U) computed once per row, and a returned t whose FP32
-//     Psi is within a few margins of the bound is re-checked in FP64 (t = 0
-//     if it fails).
+//     rho(U) computed once per row, and a returned t is re-checked in FP64
+//     (t = 0 if it fails) where a rounding bound of the FP32 Psi reaches the
+//     margin.
 #include <cfloat>
 
 #include "idp_internal.h"
@@ -132,6 +132,7 @@ __device__ __forceinline__ PsiAnchor make_anchor(const double* U, double rho_min
 //   rho(U + tP)^(12/5) = rho^(12/5) (1 + q),  q = (1 + t P_rho/rho)^(12/5) - 1.
 struct PsiLine {
   float g, h, sr;  // sr = P_rho / rho
+  float gabs, habs;  // sums of the magnitudes of the terms of g and h
 };
 
 __device__ __forceinline__ PsiLine make_line(const PsiAnchor& a, const float* P) {
@@ -139,15 +140,38 @@ __device__ __forceinline__ PsiLine make_line(const PsiAnchor& a, const float* P)
   L.g = P[0] * a.u[4] + a.u[0] * P[4] - (a.u[1] * P[1] + a.u[2] * P[2] + a.u[3] * P[3]);
   L.h = P[0] * P[4] - 0.5f * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
   L.sr = P[0] * a.inv_rho0;
+  L.gabs = fabsf(P[0] * a.u[4]) + fabsf(a.u[0] * P[4]) + fabsf(a.u[1] * P[1]) + fabsf(a.u[2] * P[2]) +
+           fabsf(a.u[3] * P[3]);
+  L.habs = fabsf(P[0] * P[4]) + 0.5f * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
   return L;
 }
 
-__device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, float t, float* dpsi) {
+// Psi(t) - margin; also dPsi/dt and lg = log1p(s), q (for the error bound)
+__device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, float t, float* dpsi, float* lg_out,
+                                        float* q_out) {
   const float s = t * L.sr;  // > -1 inside the density interval
   const float lg = log1pf(s);
   const float q = expm1f(2.4f * lg);
   if (dpsi) *dpsi = L.g + 2.0f * t * L.h - a.phi_pow0 * 2.4f * ((1.0f + q) / (1.0f + s)) * L.sr;
+  *lg_out = lg;
+  *q_out = q;
   return a.psi0 + t * (L.g + t * L.h) - a.phi_pow0 * q - a.margin;
+}
+
+// Bound on |psi_at(t) - (Psi(t) - margin)|, Psi in exact arithmetic along
+// U + tP with the FP64 U and the FP32 P, from the rounding of every FP32
+// operation (unit roundoff u = 2^-24): the FP32 copies of U and Psi(0), g and
+// h (a few roundings of their terms each), s = t P_rho/rho, log1p/expm1
+// (about one ulp each, amplified by 2.4 (1 + q) through q = (1 + s)^2.4 - 1)
+// and the seven operations that combine them, each at most u times the sum
+// S of the magnitudes involved.
+__device__ __forceinline__ float psi_error_bound(const PsiAnchor& a, const PsiLine& L, float t, float lg, float q) {
+  const float s = t * L.sr;
+  const float tg = t * L.gabs, th = t * t * L.habs;
+  const float qa = fabsf(q);
+  const float S = fabsf(a.psi0) + tg + th + a.phi_pow0 * qa + a.margin;
+  const float dq = (1.0f + q) * (4.8f * fabsf(lg) + 7.2f * fabsf(s) / fmaxf(1.0f + s, 1e-30f)) + 3.0f * qa;
+  return 5.9604645e-8f * (7.0f * S + fabsf(a.psi0) + 7.0f * tg + 5.0f * th + a.phi_pow0 * dq);
 }
 
 // limiter.compute of Alg. 2 for the mixed path.  U (FP64) is the row state,
@@ -164,19 +188,21 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
   tR = fminf(fmaxf(tR, 0.0f), 1.0f);
   float tL = 0.0f;
   const PsiLine L = make_line(A, P);
-  float psiL = 0.0f, dpsiL = 0.0f, psiAtL;
+  float psiL = 0.0f, dpsiL = 0.0f, psiAtL, lgL = 0.0f, qL = 0.0f;
   bool haveL = false, accepted = false;
   for (int step = 0; step < prm.newton_max; ++step) {
-    float dpsiR;
-    const float psiR = psi_at(A, L, tR, &dpsiR);
+    float dpsiR, lgR, qR;
+    const float psiR = psi_at(A, L, tR, &dpsiR, &lgR, &qR);
     if (psiR >= 0.0f) {
       tL = tR;
       psiAtL = psiR;
+      lgL = lgR;
+      qL = qR;
       accepted = true;
       break;
     }
     if (!haveL) {
-      psiL = psi_at(A, L, tL, &dpsiL);
+      psiL = psi_at(A, L, tL, &dpsiL, &lgL, &qL);
       haveL = true;
     }
     const float tol = (float)prm.newton_tol * (A.psi0 + A.phi_pow0);
@@ -191,11 +217,13 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
     float nR = tR - 2.0f * psiR / (dpsiR - sqrtf(lamR));
     if (!(nL >= tL)) nL = tL;
     if (!(nL <= tR)) nL = tR;
-    float dpsiN;
-    const float psiN = psi_at(A, L, nL, &dpsiN);
+    float dpsiN, lgN, qN;
+    const float psiN = psi_at(A, L, nL, &dpsiN, &lgN, &qN);
     if (psiN >= 0.0f) {
       psiL = psiN;
       dpsiL = dpsiN;
+      lgL = lgN;
+      qL = qN;
     } else {
       nL = tL;
     }
@@ -204,9 +232,11 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
     tL = nL;
     tR = nR;
   }
-  if (!accepted) psiAtL = haveL ? psiL : psi_at(A, L, tL, nullptr);
-  // final FP64 check of the entropy bound where the FP32 value is close to it
-  if (tL > 0.0f && psiAtL < 3.0f * A.margin) {
+  if (!accepted) psiAtL = haveL ? psiL : psi_at(A, L, tL, nullptr, &lgL, &qL);
+  // FP64 check of the entropy bound where the FP32 evaluation cannot
+  // guarantee it: psiAtL >= 0 means Psi(t) >= margin - error, so the check is
+  // needed only when the rounding bound reaches the margin
+  if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, lgL, qL) >= A.margin)) {
     double V[kFields];
 #pragma unroll
     for (int f = 0; f < kFields; ++f) V[f] = U[f] + (double)tL * (double)P[f];
