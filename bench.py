@@ -99,11 +99,21 @@ def pattern_batched(stream, args):
         s = Solver(mesh, stream=stream, precision=prec)
         s.set_instances(off)
         s.init_state(U0)
-        block, graph, ms_tuned = s.autotune(steps=1)
+        block, graph, persistent, ms_tuned = s.autotune(steps=1)
         ms, _ = _time_steps(s, stream, args.pattern_steps, args.warmup, profile=False)
         out[name] = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                     "schedule": {"block": block, "cuda_graph": graph, "autotune_ms_per_step": ms_tuned},
-                     "gpu_launches_per_step": 21}
+                     "schedule": {"block": block, "cuda_graph": graph, "persistent": persistent,
+                                  "autotune_ms_per_step": ms_tuned},
+                     "gpu_launches_per_step": 3 if persistent else 21}
+        # every schedule on the same batch, for the record
+        sched = {}
+        for pers in (False, True):
+            for g in (False, True):
+                s.set_schedule(block, g, pers)
+                s.init_state(U0)
+                sched[f"{'persistent' if pers else 'per_step'}_{'graph' if g else 'stream'}"] = \
+                    _time_steps(s, stream, 2, 3, profile=False)[0]
+        out[name]["ms_per_step_by_schedule_at_block"] = sched
         s.close()
     return out
 

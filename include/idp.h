@@ -203,14 +203,30 @@ idp_status idp_set_instances(idp_ctx* ctx, int64_t n_instances, const int64_t* n
 idp_status idp_get_instance_times(idp_ctx* ctx, double* t, double* last_tau);
 
 /* Launch schedule of the stage kernels: block_size 64, 128 or 256 threads
- * (one row per thread), and use_graph != 0 to capture one SSP-RK3 step in a
- * CUDA graph on first use and replay it in idp_step (per-kernel profiling
- * then runs without the graph).  Results do not depend on the schedule. */
-idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph);
-/* Times every schedule for `steps` SSP-RK3 steps on the current state, keeps
- * the fastest and restores the state and clocks; writes the choice and its
- * milliseconds per step (any output pointer may be NULL); synchronises. */
-idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, double* ms_per_step);
+ * (one row per thread); use_graph != 0 captures one SSP-RK3 step in a CUDA
+ * graph on first use and replays it in idp_step; persistent != 0 runs each
+ * euler_step as ONE cooperative launch (all blocks co-resident, grid-stride
+ * over the rows, a grid barrier where the paper's global synchronisations
+ * are, Fig. 2).  A barrier wait is bounded by idp_config.barrier_spin_limit
+ * polls; one that runs out ends the launch and latches IDP_ERR_TIMEOUT.
+ * Traced and profiled stages always take the per-step kernels.  Results do
+ * not depend on the schedule. */
+idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph, int persistent);
+/* Self-test of the persistent schedule's grid barrier: a cooperative launch
+ * of `blocks` blocks (64 threads) that pass `rounds` barriers, each wait
+ * bounded by spin_limit polls; with skip_block0 != 0 block 0 never arrives,
+ * so the others' waits run out.  *passes (may be NULL) receives the number
+ * of block-passes (blocks x rounds when nothing is skipped).  Returns
+ * IDP_ERR_TIMEOUT when a wait ran out (the context stays usable), IDP_ERR_CUDA
+ * when the device cannot hold the blocks at once; synchronises. */
+idp_status idp_barrier_selftest(idp_ctx* ctx, int blocks, int rounds, int skip_block0, long long spin_limit,
+                                int* passes);
+/* Times every schedule (block size x graph replay x persistent) for `steps`
+ * SSP-RK3 steps on the current state, skips schedules the device cannot run,
+ * keeps the fastest and restores the state and clocks; writes the choice and
+ * its milliseconds per step (any output pointer may be NULL); synchronises. */
+idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, int* persistent,
+                        double* ms_per_step);
 
 /* Reverse mode (discrete adjoint) of the FP64 scheme, for gradients of a
  * functional J(U^N) with respect to the state U^0 it evolved from.  The

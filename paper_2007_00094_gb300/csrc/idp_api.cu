@@ -37,6 +37,8 @@ struct idp_ctx {
   // schedule: block size of the stage kernels and CUDA-graph replay of idp_step
   int block = 128;
   bool use_graph = false;
+  bool persistent = false;            // one cooperative launch per euler_step
+  idp::GridBarrier* bar = nullptr;   // its grid barrier (device)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0;
@@ -210,11 +212,12 @@ idp_status ensure_adjoint(idp_ctx* ctx) {
 // One euler_step in the context's precision.
 int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int blend, int tau_mode, bool acc_time,
            bool skip_write_on_error, bool trace, cudaStream_t s, idp::Profiler* prof) {
+  idp::GridBarrier* bar = ctx->persistent ? ctx->bar : nullptr;
   if (ctx->mixed)
     return idp::launch_euler_step_mixed(ctx->G, ctx->MG, ctx->B, ctx->MB, ctx->C, Uin, Uout, Un, blend, tau_mode,
-                                        acc_time, skip_write_on_error, trace, s, prof, ctx->block);
+                                        acc_time, skip_write_on_error, trace, s, prof, ctx->block, bar);
   return idp::launch_euler_step(ctx->G, ctx->B, ctx->C, Uin, Uout, Un, blend, tau_mode, acc_time, skip_write_on_error,
-                                trace, s, prof, ctx->block);
+                                trace, s, prof, ctx->block, bar);
 }
 
 // The three euler_steps of one SSP-RK3 step (eq. ssprk3) on stream s.
@@ -307,6 +310,7 @@ idp_status idp_create(const idp_config* cfg, void* cuda_stream, idp_ctx** out) {
   ctx->C.lim.newton_max = c.newton_max;
   ctx->C.lim.newton_tol = c.newton_tol;
   ctx->C.lim.newton_eps = c.newton_eps;
+  ctx->C.spin_limit = c.barrier_spin_limit > 0 ? (long long)c.barrier_spin_limit : (1LL << 26);
   *out = ctx;
   return IDP_OK;
 }
@@ -378,7 +382,8 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   B = idp::StageBuffers{};
   if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) || (st = dalloc(ctx, &B.UL, 5 * n)) ||
       (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
-      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)) || (st = dalloc(ctx, &ctx->check_acc, 5)))
+      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)) || (st = dalloc(ctx, &ctx->check_acc, 5)) ||
+      (st = dalloc(ctx, &ctx->bar, 1)))
     return st;
   if (!ctx->mixed) {
     if ((st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) || (st = dalloc(ctx, &B.dinv, ns)) ||
@@ -581,16 +586,18 @@ idp_status idp_get_instance_times(idp_ctx* ctx, double* t, double* last_tau) {
   return IDP_OK;
 }
 
-idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph) {
+idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph, int persistent) {
   if (!ctx) return IDP_ERR_ARG;
   if (block_size != 64 && block_size != 128 && block_size != 256) return fail(ctx, IDP_ERR_ARG, "block size");
-  if (block_size != ctx->block) drop_graph(ctx);
+  if (block_size != ctx->block || (persistent != 0) != ctx->persistent) drop_graph(ctx);
   ctx->block = block_size;
   ctx->use_graph = use_graph != 0;
+  ctx->persistent = persistent != 0;
   return IDP_OK;
 }
 
-idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, double* ms_per_step) {
+idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph, int* persistent,
+                        double* ms_per_step) {
   if (!ctx) return IDP_ERR_ARG;
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
   if (steps < 1) return fail(ctx, IDP_ERR_ARG, "steps");
@@ -602,35 +609,53 @@ idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph
   if (st != IDP_OK) return st;
   const int blocks[3] = {64, 128, 256};
   double best = 1e300;
-  int best_b = ctx->block, best_g = ctx->use_graph ? 1 : 0;
+  int best_b = ctx->block, best_g = ctx->use_graph ? 1 : 0, best_p = ctx->persistent ? 1 : 0;
   cudaEvent_t a, b;
   IDP_CUDA(ctx, cudaEventCreate(&a));
   IDP_CUDA(ctx, cudaEventCreate(&b));
-  for (int g = 0; g < 2; ++g)
-    for (int q = 0; q < 3; ++q) {
-      if ((st = idp_set_schedule(ctx, blocks[q], g))) break;
-      if ((st = idp_step(ctx, 1))) break;  // warm-up (and graph capture)
-      IDP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
-      if ((st = idp_step(ctx, steps))) break;
-      IDP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
-      IDP_CUDA(ctx, cudaEventSynchronize(b));
-      float ms = 0.0f;
-      IDP_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
-      if (ms / steps < best) {
-        best = ms / steps;
-        best_b = blocks[q];
-        best_g = g;
+  for (int pers = 0; pers < 2 && st == IDP_OK; ++pers)
+    for (int g = 0; g < 2 && st == IDP_OK; ++g)
+      for (int q = 0; q < 3 && st == IDP_OK; ++q) {
+        if ((st = idp_set_schedule(ctx, blocks[q], g, pers))) break;
+        // a schedule this device or driver cannot run (e.g. a cooperative
+        // launch in a captured graph) is skipped, not fatal
+        idp_status trial = idp_step(ctx, 1);  // warm-up (and graph capture)
+        float ms = -1.0f;
+        if (trial == IDP_OK) {
+          IDP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
+          trial = idp_step(ctx, steps);
+          IDP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
+          if (trial == IDP_OK) {
+            IDP_CUDA(ctx, cudaEventSynchronize(b));
+            IDP_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
+          }
+        }
+        if (trial == IDP_ERR_CUDA) {
+          cudaGetLastError();
+          drop_graph(ctx);
+        } else if (trial != IDP_OK) {
+          st = trial;
+          break;
+        }
+        if (ms >= 0.0f && ms / steps < best) {
+          best = ms / steps;
+          best_b = blocks[q];
+          best_g = g;
+          best_p = pers;
+        }
+        IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        IDP_CUDA(ctx, cudaMemcpyAsync(ctx->B.U, U0.data(), sizeof(double) * 5 * n, cudaMemcpyHostToDevice, ctx->stream));
+        IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.time, t0.data(), sizeof(double) * ni, cudaMemcpyHostToDevice, ctx->stream));
+        IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       }
-      IDP_CUDA(ctx, cudaMemcpyAsync(ctx->B.U, U0.data(), sizeof(double) * 5 * n, cudaMemcpyHostToDevice, ctx->stream));
-      IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.time, t0.data(), sizeof(double) * ni, cudaMemcpyHostToDevice, ctx->stream));
-      IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (st != IDP_OK) return st;
-  if ((st = idp_set_schedule(ctx, best_b, best_g))) return st;
+  if (best >= 1e300) return fail(ctx, IDP_ERR_CUDA, "no schedule ran");
+  if ((st = idp_set_schedule(ctx, best_b, best_g, best_p))) return st;
   if (block_size) *block_size = best_b;
   if (use_graph) *use_graph = best_g;
+  if (persistent) *persistent = best_p;
   if (ms_per_step) *ms_per_step = best;
   return device_status(ctx, true);
 }
@@ -724,6 +749,20 @@ idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out) {
 }
 
 int64_t idp_launch_count(const idp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+idp_status idp_barrier_selftest(idp_ctx* ctx, int blocks, int rounds, int skip_block0, long long spin_limit,
+                                int* passes) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (blocks < 1 || rounds < 0 || spin_limit < 0) return fail(ctx, IDP_ERR_ARG, "bad self-test arguments");
+  unsigned int* d_passes = reinterpret_cast<unsigned int*>(ctx->check_acc);  // scratch word
+  IDP_CUDA(ctx, idp::launch_barrier_selftest(ctx->bar, spin_limit, blocks, rounds, skip_block0 ? 1 : 0, d_passes,
+                                             ctx->B.scal, ctx->stream));
+  unsigned int h = 0;
+  IDP_CUDA(ctx, cudaMemcpyAsync(&h, d_passes, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  idp_status st = device_status(ctx, true);
+  if (passes) *passes = (int)h;
+  return st;
+}
 
 idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, const double* gE, double* gU,
                                   double* g_tau, int on_device) {

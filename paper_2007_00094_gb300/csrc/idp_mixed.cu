@@ -248,10 +248,8 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
 }
 
 // Step 0: per-node quantities (FP32 copies) and an FP32 copy of the state.
-__global__ void __launch_bounds__(kMaxBlock) k_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
-                                                   float* __restrict__ Uf, DeviceScalars* scal) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void row_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
+                                           float* __restrict__ Uf, DeviceScalars* scal, int64_t i) {
   double u[kFields];
   load5(U, n, i, u);
   const double rho = u[0];
@@ -272,14 +270,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_node_m(int64_t n, const double* _
   for (int f = 0; f < kFields; ++f) Uf[f * n + i] = (float)u[f];
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
+                                                   float* __restrict__ Uf, DeviceScalars* scal) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) row_node_m(n, U, Q, Uf, scal, i);
+}
+
 // Step 1 in FP32: d_ij (upper edges) with 1/(2 d_ij), flux differences and alpha_i.
-__global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph M, const float* __restrict__ U,
-                                                   const float* __restrict__ Q, float* __restrict__ d,
-                                                   float* __restrict__ dinv, float* __restrict__ dF,
-                                                   float* __restrict__ alpha, DeviceScalars* scal) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGraph& M, const float* __restrict__ U,
+                                           const float* __restrict__ Q, float* __restrict__ d,
+                                           float* __restrict__ dinv, float* __restrict__ dF,
+                                           float* __restrict__ alpha, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -336,50 +337,57 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph 
   alpha[r] = D > 0.0f ? fabsf(num) / D : 0.0f;
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph M, const float* __restrict__ U,
+                                                   const float* __restrict__ Q, float* __restrict__ d,
+                                                   float* __restrict__ dinv, float* __restrict__ dF,
+                                                   float* __restrict__ alpha, DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;
+  if (r < G.n) row_edge_m(G, M, U, Q, d, dinv, dF, alpha, r);
+}
+
 // Step 2: lower half of d and 1/(2d), and the CFL bound min_i m_i/(-2 d_ii)
 // with d_ii summed in FP64.
+__device__ __forceinline__ double row_diag_m(const DeviceGraph& G, float* __restrict__ d, float* __restrict__ dinv,
+                                             int64_t r) {
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double sum = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) continue;
+    float v;
+    if (j < r) {
+      const int64_t pt = G.tpos[p];
+      v = d[pt];
+      d[p] = v;
+      dinv[p] = dinv[pt];
+    } else {
+      v = d[p];
+    }
+    sum += (double)v;
+  }
+  return G.mi[r] / (2.0 * sum);
+}
+
 __global__ void __launch_bounds__(kMaxBlock) k_diag_m(DeviceGraph G, float* __restrict__ d, float* __restrict__ dinv,
                                                    DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double cand = INFINITY;
-  if (r < G.n) {
-    const int64_t base = slot_base(G, r);
-    const int len = G.row_len[r];
-    double sum = 0.0;
-    for (int k = 0; k < len; ++k) {
-      const int64_t p = base + 32 * (int64_t)k;
-      const int64_t j = G.col[p];
-      if (j == r) continue;
-      float v;
-      if (j < r) {
-        const int64_t pt = G.tpos[p];
-        v = d[pt];
-        d[p] = v;
-        dinv[p] = dinv[pt];
-      } else {
-        v = d[p];
-      }
-      sum += (double)v;
-    }
-    cand = G.mi[r] / (2.0 * sum);
-  }
-  reduce_tau_candidate(G, r, cand);
+  reduce_tau_candidate(G, r, r < G.n ? row_diag_m(G, d, dinv, r) : INFINITY);
 }
 
 // Step 3: U^L_i = U_i + sum_j (2 tau d_ij/m_i)(Ubar_ij - U_i) with
 // Ubar_ij - U_i = (U_j - U_i)/2 - df_ij/(2 d_ij) summed in FP32 and added to
 // the FP64 state; bounds rho_i + min/max_j (Ubar_ij - U_i)_rho and phi_min;
 // R_i = -sum_j df_ij - f_i.s_i + sum_j d^H_ij (U_j - U_i) in FP32.
-__global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,
-                                                        const float* __restrict__ Uf, const float* __restrict__ Q,
-                                                        const float* __restrict__ d, const float* __restrict__ dinv,
-                                                        const float* __restrict__ dF, const float* __restrict__ alpha,
-                                                        double* __restrict__ UL, float* __restrict__ R,
-                                                        double* __restrict__ bnd, DeviceScalars* scal, int tau_mode,
-                                                        int accumulate_time) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_low_order_m(const DeviceGraph& G, const StageConfig& C,
+                                                const double* __restrict__ U, const float* __restrict__ Uf,
+                                                const float* __restrict__ Q, const float* __restrict__ d,
+                                                const float* __restrict__ dinv, const float* __restrict__ dF,
+                                                const float* __restrict__ alpha, double* __restrict__ UL,
+                                                float* __restrict__ R, double* __restrict__ bnd, int tau_mode,
+                                                int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -438,15 +446,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageC
   bnd[2 * n + r] = (double)phi_min;
 }
 
-// Step 4 in FP32: P_ij and the first limiter values.
-__global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
-                                                         const float* __restrict__ Uf, const float* __restrict__ d,
-                                                         const float* __restrict__ alpha, const double* __restrict__ UL,
-                                                         const float* __restrict__ R, const double* __restrict__ bnd,
-                                                         float* __restrict__ P, float* __restrict__ l,
-                                                         const DeviceScalars* scal, int tau_mode) {
+__global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                        const float* __restrict__ Uf, const float* __restrict__ Q,
+                                                        const float* __restrict__ d, const float* __restrict__ dinv,
+                                                        const float* __restrict__ dF, const float* __restrict__ alpha,
+                                                        double* __restrict__ UL, float* __restrict__ R,
+                                                        double* __restrict__ bnd, DeviceScalars* scal, int tau_mode,
+                                                        int accumulate_time) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
+  if (r < G.n) row_low_order_m(G, C, U, Uf, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
+}
+
+// Step 4 in FP32: P_ij and the first limiter values.
+__device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const MixedGraph& M, const StageConfig& C,
+                                                 const float* __restrict__ Uf, const float* __restrict__ d,
+                                                 const float* __restrict__ alpha, const double* __restrict__ UL,
+                                                 const float* __restrict__ R, const double* __restrict__ bnd,
+                                                 float* __restrict__ P, float* __restrict__ l, int tau_mode,
+                                                 int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -485,14 +503,23 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, Mixed
   }
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
+                                                         const float* __restrict__ Uf, const float* __restrict__ d,
+                                                         const float* __restrict__ alpha, const double* __restrict__ UL,
+                                                         const float* __restrict__ R, const double* __restrict__ bnd,
+                                                         float* __restrict__ P, float* __restrict__ l,
+                                                         const DeviceScalars* scal, int tau_mode) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n) row_flux_limit_m(G, M, C, Uf, d, alpha, UL, R, bnd, P, l, tau_mode, r);
+}
+
 // Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
 // FP32, added to FP64), P_ij <- (1 - min) P_ij and new l_ij.
-__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
-                                                           double* __restrict__ Unext, float* __restrict__ P,
-                                                           const float* __restrict__ lold, float* __restrict__ lnew,
-                                                           const double* __restrict__ bnd) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const StageConfig& C,
+                                                   const double* __restrict__ Ucur, double* __restrict__ Unext,
+                                                   float* __restrict__ P, const float* __restrict__ lold,
+                                                   float* __restrict__ lnew, const double* __restrict__ bnd,
+                                                   int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -532,14 +559,20 @@ __global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, Sta
   }
 }
 
-// Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
-__global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
-                                                    const float* __restrict__ P, const float* __restrict__ l,
-                                                    const double* __restrict__ Un, double* __restrict__ Uout,
-                                                    double* __restrict__ Ulim, DeviceScalars* scal, int blend,
-                                                    int skip_write_on_error) {
+__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                           double* __restrict__ Unext, float* __restrict__ P,
+                                                           const float* __restrict__ lold, float* __restrict__ lnew,
+                                                           const double* __restrict__ bnd) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+  if (r < G.n) row_limiter_pass_m(G, C, Ucur, Unext, P, lold, lnew, bnd, r);
+}
+
+// Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
+__device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageConfig& C,
+                                            const double* __restrict__ Ucur, const float* __restrict__ P,
+                                            const float* __restrict__ l, const double* __restrict__ Un,
+                                            double* __restrict__ Uout, double* __restrict__ Ulim, DeviceScalars* scal,
+                                            int blend, int skip_write_on_error, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -584,15 +617,88 @@ __global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, StageConfi
   for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                    const float* __restrict__ P, const float* __restrict__ l,
+                                                    const double* __restrict__ Un, double* __restrict__ Uout,
+                                                    double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+                                                    int skip_write_on_error) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n) row_final_m(G, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
+}
+
+struct PersistentStageMixed {
+  PersistentStage a;
+  MixedGraph M;
+  MixedBuffers X;
+};
+
+// One FP32-mixed euler_step in a single cooperative launch (see
+// k_stage_persistent in idp_stage.cu for the barrier placement).
+__global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStageMixed pm) {
+  const PersistentStage& a = pm.a;
+  const DeviceGraph& G = a.G;
+  const StageConfig& C = a.C;
+  const StageBuffers& B = a.B;
+  const MixedGraph& M = pm.M;
+  const MixedBuffers& X = pm.X;
+  const int64_t n = G.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < n; i += stride) row_node_m(n, a.Uin, X.Q, X.Uf, B.scal, i);
+  for (int64_t i = t0; i < G.n_inst; i += stride) G.tau_min[i] = 0x7ff0000000000000ull;
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride) row_edge_m(G, M, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, r);
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
+    const int64_t r = b0 + threadIdx.x;
+    reduce_tau_candidate(G, r, r < n ? row_diag_m(G, X.d, X.dinv, r) : INFINITY);
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride) {
+    instance_books(G, r, a.tau_mode, C.cfl, a.accumulate_time, B.scal);
+    row_low_order_m(G, C, a.Uin, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.UL, X.R, B.bnd, a.tau_mode, r);
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride)
+    row_flux_limit_m(G, M, C, X.Uf, X.d, X.alpha, B.UL, X.R, B.bnd, X.P, X.l[0], a.tau_mode, r);
+  const double* cur = B.UL;
+  int lbuf = 0, wbuf = 0;
+  for (int pass = 1; pass < C.limiter_passes; ++pass) {
+    if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+    double* next = B.Uw[wbuf];
+    for (int64_t r = t0; r < n; r += stride)
+      row_limiter_pass_m(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd, r);
+    cur = next;
+    wbuf ^= 1;
+    lbuf ^= 1;
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride)
+    row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+}
+
 }  // namespace
+
+const void* persistent_kernel_mixed() { return (const void*)k_stage_persistent_m; }
 
 int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B, const MixedBuffers& X,
                             const StageConfig& C, const double* Uin, double* Uout, const double* Un, int blend,
                             int tau_mode, bool accumulate_time, bool skip_write_on_error, bool trace, cudaStream_t s,
-                            Profiler* prof, int block) {
+                            Profiler* prof, int block, GridBarrier* bar) {
   const int kBlock = block;
   const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
   const bool p = prof && prof->enabled;
+  if (bar && !trace && !p) {
+    PersistentStageMixed pm{{G, C, B, Uin, Uout, Un, bar, blend, tau_mode, accumulate_time ? 1 : 0,
+                             skip_write_on_error ? 1 : 0},
+                            M, X};
+    const int limit = persistent_grid_limit(kBlock, true);
+    const unsigned pgrid = (unsigned)(limit < (int)grid ? limit : grid);
+    cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+    void* args[] = {&pm};
+    cudaLaunchCooperativeKernel((const void*)k_stage_persistent_m, dim3(pgrid), dim3(kBlock), args, 0, s);
+    return 1;
+  }
   int launches = 0;
   auto run = [&](int id, auto&& launch) {
     if (p) prof->begin(id, s);

@@ -30,6 +30,6 @@ struct MixedBuffers {
 int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B, const MixedBuffers& X,
                             const StageConfig& C, const double* Uin, double* Uout, const double* Un, int blend,
                             int tau_mode, bool accumulate_time, bool skip_write_on_error, bool trace, cudaStream_t s,
-                            Profiler* prof, int block = 128);
+                            Profiler* prof, int block = 128, GridBarrier* bar = nullptr);
 
 }  // namespace idp

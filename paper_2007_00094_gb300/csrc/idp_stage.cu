@@ -38,10 +38,8 @@ __device__ __forceinline__ Side load_side(const double* U, const double* Q, int6
 
 // Step 0: per-node quantities (Sec. 2): 1/rho, p, c, p^(-1/7), 1/p,
 // eta/rho with eta = (rho eps)^(5/12), (E + p)/rho and phi = eps rho^(-7/5).
-__global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
-                                                 DeviceScalars* scal) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void row_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
+                                         DeviceScalars* scal, int64_t i) {
   double u[kFields];
   load5(U, n, i, u);
   const double rho = u[0];
@@ -67,17 +65,20 @@ __global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __r
   Q[kQPhi * n + i] = eps * r7;
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
+                                                 DeviceScalars* scal) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) row_node(n, U, Q, scal, i);
+}
+
 // Step 1: d^L_ij for the edges this row owns (j > i), stored with 1/(2 d_ij),
 // and the indicator alpha_i (Sec. 3.8) over all j in I(i).  The flux
 // differences (f_j - f_i).c_ij computed for the indicator are stored (in the
 // P buffer, free until Step 4) for the bar states and R_i of Step 3.
-__global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
-                                                 const double* __restrict__ Q, double* __restrict__ d,
-                                                 double* __restrict__ dinv, double* __restrict__ dF,
-                                                 double* __restrict__ alpha, DeviceScalars* scal) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;  // +inf, read by the next kernel
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* __restrict__ U,
+                                         const double* __restrict__ Q, double* __restrict__ d,
+                                         double* __restrict__ dinv, double* __restrict__ dF,
+                                         double* __restrict__ alpha, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -135,39 +136,49 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double*
   alpha[r] = D > 0.0 ? fabs(num) / D : 0.0;
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
+                                                 const double* __restrict__ Q, double* __restrict__ d,
+                                                 double* __restrict__ dinv, double* __restrict__ dF,
+                                                 double* __restrict__ alpha, DeviceScalars* scal) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;  // +inf, read by the next kernel
+  if (r < G.n) row_edge(G, U, Q, d, dinv, dF, alpha, r);
+}
+
 // Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
 // CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
+__device__ __forceinline__ double row_diag(const DeviceGraph& G, double* __restrict__ d, double* __restrict__ dinv,
+                                           int64_t r) {
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double sum = 0.0;
+  int64_t pd = base;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    const int64_t j = G.col[p];
+    if (j == r) {
+      pd = p;
+      continue;
+    }
+    double v;
+    if (j < r) {
+      const int64_t pt = G.tpos[p];
+      v = d[pt];
+      d[p] = v;
+      dinv[p] = dinv[pt];
+    } else {
+      v = d[p];
+    }
+    sum += v;
+  }
+  d[pd] = -sum;
+  return G.mi[r] / (2.0 * sum);
+}
+
 __global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, double* __restrict__ d, double* __restrict__ dinv,
                                                  DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double cand = INFINITY;
-  if (r < G.n) {
-    const int64_t base = slot_base(G, r);
-    const int len = G.row_len[r];
-    double sum = 0.0;
-    int64_t pd = base;
-    for (int k = 0; k < len; ++k) {
-      const int64_t p = base + 32 * (int64_t)k;
-      const int64_t j = G.col[p];
-      if (j == r) {
-        pd = p;
-        continue;
-      }
-      double v;
-      if (j < r) {
-        const int64_t pt = G.tpos[p];
-        v = d[pt];
-        d[p] = v;
-        dinv[p] = dinv[pt];
-      } else {
-        v = d[p];
-      }
-      sum += v;
-    }
-    d[pd] = -sum;
-    cand = G.mi[r] / (2.0 * sum);
-  }
-  reduce_tau_candidate(G, r, cand);
+  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, d, dinv, r) : INFINITY);
 }
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
@@ -176,15 +187,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, double* __res
 // flux differences df_ij = (f_j - f_i).c_ij of Step 1,
 // Ubar_ij = (U_i + U_j)/2 - df_ij/(2 d_ij) and, since sum_j c_ij = s_i,
 // sum_j -f_j.c_ij = -sum_j df_ij - f_i.s_i (s_i is zero up to rounding).
-__global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
-                                                      const double* __restrict__ Q, const double* __restrict__ d,
-                                                      const double* __restrict__ dinv, const double* __restrict__ dF,
-                                                      const double* __restrict__ alpha, double* __restrict__ UL,
-                                                      double* __restrict__ R, double* __restrict__ bnd,
-                                                      DeviceScalars* scal, int tau_mode, int accumulate_time) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageConfig& C, const double* __restrict__ U,
+                                              const double* __restrict__ Q, const double* __restrict__ d,
+                                              const double* __restrict__ dinv, const double* __restrict__ dF,
+                                              const double* __restrict__ alpha, double* __restrict__ UL,
+                                              double* __restrict__ R, double* __restrict__ bnd, int tau_mode,
+                                              int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -240,16 +248,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageCon
   bnd[2 * n + r] = phi_min;
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                      const double* __restrict__ Q, const double* __restrict__ d,
+                                                      const double* __restrict__ dinv, const double* __restrict__ dF,
+                                                      const double* __restrict__ alpha, double* __restrict__ UL,
+                                                      double* __restrict__ R, double* __restrict__ bnd,
+                                                      DeviceScalars* scal, int tau_mode, int accumulate_time) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
+  if (r < G.n) row_low_order(G, C, U, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
+}
+
 // Step 4: antidiffusive fluxes P_ij (eq. def-p) with b_ij = -m_ij/m_j,
 // b_ji = -m_ij/m_i (j != i) and the first limiter values l_ij.
-__global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageConfig C, const double* __restrict__ U,
-                                                       const double* __restrict__ d, const double* __restrict__ alpha,
-                                                       const double* __restrict__ UL, const double* __restrict__ R,
-                                                       const double* __restrict__ bnd, double* __restrict__ P,
-                                                       double* __restrict__ l, const DeviceScalars* scal,
-                                                       int tau_mode) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const StageConfig& C,
+                                               const double* __restrict__ U, const double* __restrict__ d,
+                                               const double* __restrict__ alpha, const double* __restrict__ UL,
+                                               const double* __restrict__ R, const double* __restrict__ bnd,
+                                               double* __restrict__ P, double* __restrict__ l, int tau_mode,
+                                               int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -288,14 +305,22 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageCo
   }
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageConfig C, const double* __restrict__ U,
+                                                       const double* __restrict__ d, const double* __restrict__ alpha,
+                                                       const double* __restrict__ UL, const double* __restrict__ R,
+                                                       const double* __restrict__ bnd, double* __restrict__ P,
+                                                       double* __restrict__ l, const DeviceScalars* scal,
+                                                       int tau_mode) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n) row_flux_limit(G, C, U, d, alpha, UL, R, bnd, P, l, tau_mode, r);
+}
+
 // Steps 5, 6, ...: U_i += sum_j lambda_i min(l_ij, l_ji) P_ij, then (not in
 // the last pass) P_ij <- (1 - min(l_ij, l_ji)) P_ij and new l_ij.
-__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
-                                                         double* __restrict__ Unext, double* __restrict__ P,
-                                                         const double* __restrict__ lold, double* __restrict__ lnew,
-                                                         const double* __restrict__ bnd) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const StageConfig& C,
+                                                 const double* __restrict__ Ucur, double* __restrict__ Unext,
+                                                 double* __restrict__ P, const double* __restrict__ lold,
+                                                 double* __restrict__ lnew, const double* __restrict__ bnd, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -334,16 +359,22 @@ __global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, Stage
   }
 }
 
+__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                         double* __restrict__ Unext, double* __restrict__ P,
+                                                         const double* __restrict__ lold, double* __restrict__ lnew,
+                                                         const double* __restrict__ bnd) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n) row_limiter_pass(G, C, Ucur, Unext, P, lold, lnew, bnd, r);
+}
+
 // Last limiter pass, boundary post-processing (slip walls drop the flagged
 // normal momentum components, inflow nodes take the inflow state) and the
 // SSP-RK3 blend (Sec. 3.6): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
-__global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
-                                                  const double* __restrict__ P, const double* __restrict__ l,
-                                                  const double* __restrict__ Un, double* __restrict__ Uout,
-                                                  double* __restrict__ Ulim, DeviceScalars* scal, int blend,
-                                                  int skip_write_on_error) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
+__device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfig& C, const double* __restrict__ Ucur,
+                                          const double* __restrict__ P, const double* __restrict__ l,
+                                          const double* __restrict__ Un, double* __restrict__ Uout,
+                                          double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+                                          int skip_write_on_error, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -385,6 +416,73 @@ __global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig 
   if (skip_write_on_error && *(volatile int*)&scal->status != 0) return;
 #pragma unroll
   for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
+}
+
+__global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+                                                  const double* __restrict__ P, const double* __restrict__ l,
+                                                  const double* __restrict__ Un, double* __restrict__ Uout,
+                                                  double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+                                                  int skip_write_on_error) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < G.n) row_final(G, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
+}
+
+// One euler_step in a single cooperative launch: the phases of the kernels
+// above run over all rows (grid-stride) with a grid barrier between them,
+// where the kernel boundaries were.  Data a phase reads was written before
+// the barrier that precedes it (or before the launch), never earlier in the
+// launch by another block, so no block can hold a stale copy of it.
+__global__ void __launch_bounds__(kMaxBlock) k_stage_persistent(PersistentStage a) {
+  const DeviceGraph& G = a.G;
+  const StageConfig& C = a.C;
+  const StageBuffers& B = a.B;
+  const int64_t n = G.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < n; i += stride) row_node(n, a.Uin, B.node, B.scal, i);
+  for (int64_t i = t0; i < G.n_inst; i += stride) G.tau_min[i] = 0x7ff0000000000000ull;
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride) row_edge(G, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, r);
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  // whole warps iterate together: the CFL reduction shuffles across the warp
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
+    const int64_t r = b0 + threadIdx.x;
+    reduce_tau_candidate(G, r, r < n ? row_diag(G, B.d, B.dinv, r) : INFINITY);
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride) {
+    instance_books(G, r, a.tau_mode, C.cfl, a.accumulate_time, B.scal);
+    row_low_order(G, C, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, a.tau_mode, r);
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride)
+    row_flux_limit(G, C, a.Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], a.tau_mode, r);
+  const double* cur = B.UL;
+  int lbuf = 0, wbuf = 0;
+  for (int pass = 1; pass < C.limiter_passes; ++pass) {
+    if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+    double* next = B.Uw[wbuf];
+    for (int64_t r = t0; r < n; r += stride)
+      row_limiter_pass(G, C, cur, next, B.P, B.l[lbuf], B.l[lbuf ^ 1], B.bnd, r);
+    cur = next;
+    wbuf ^= 1;
+    lbuf ^= 1;
+  }
+  if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
+  for (int64_t r = t0; r < n; r += stride)
+    row_final(G, C, cur, B.P, B.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+}
+
+// Self-test of the grid barrier: every block passes `rounds` barriers and
+// counts its passes; with skip_block0 block 0 never arrives, so the other
+// blocks' waits run out after spin_limit polls.
+__global__ void k_barrier_selftest(GridBarrier* bar, long long spin_limit, int rounds, int skip_block0,
+                                   unsigned int* passes, DeviceScalars* scal) {
+  if (skip_block0 && blockIdx.x == 0) return;
+  for (int k = 0; k < rounds; ++k) {
+    if (!grid_barrier(bar, spin_limit, scal)) return;
+    if (threadIdx.x == 0) atomicAdd(passes, 1u);
+  }
 }
 
 // Order-preserving map of doubles to unsigned 64-bit keys (negative values
@@ -466,10 +564,21 @@ void Profiler::clear() {
 
 int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
-                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof, int block) {
+                      bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof, int block,
+                      GridBarrier* bar) {
   const int kBlock = block;  // block size of this schedule (<= kMaxBlock)
   const unsigned grid = (unsigned)((G.n + kBlock - 1) / kBlock);
   const bool p = prof && prof->enabled;
+  if (bar && !trace && !p) {
+    PersistentStage a{G, C, B, Uin, Uout, Un, bar, blend, tau_mode, accumulate_time ? 1 : 0,
+                      skip_write_on_error ? 1 : 0};
+    const int limit = persistent_grid_limit(kBlock, false);
+    const unsigned pgrid = (unsigned)(limit < (int)grid ? limit : grid);
+    cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+    void* args[] = {&a};
+    cudaLaunchCooperativeKernel((const void*)k_stage_persistent, dim3(pgrid), dim3(kBlock), args, 0, s);
+    return 1;
+  }
   int launches = 0;
   auto run = [&](int id, auto&& launch) {
     if (p) prof->begin(id, s);
@@ -510,6 +619,30 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
                                     skip_write_on_error ? 1 : 0);
   });
   return launches;
+}
+
+cudaError_t launch_barrier_selftest(GridBarrier* bar, long long spin_limit, int blocks, int rounds, int skip_block0,
+                                    unsigned int* passes, DeviceScalars* scal, cudaStream_t s) {
+  cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+  cudaMemsetAsync(passes, 0, sizeof(unsigned int), s);
+  void* args[] = {&bar, &spin_limit, &rounds, &skip_block0, &passes, &scal};
+  return cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(blocks), dim3(64), args, 0, s);
+}
+
+int persistent_grid_limit(int block, bool mixed) {
+  // occupancy is a property of the kernel and the block size: cache it
+  static int cache[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  const int slot = block == 64 ? 0 : (block == 128 ? 1 : 2);
+  int& v = cache[mixed ? 1 : 0][slot];
+  if (v == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed ? persistent_kernel_mixed() : (const void*)k_stage_persistent,
+                                                  block, 0);
+    v = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  return v;
 }
 
 void launch_check_state(const double* U, int64_t n, double* out, unsigned long long* acc, cudaStream_t s) {

@@ -87,6 +87,7 @@ struct StageConfig {
   int limiter_passes;
   LimiterParams lim;
   double inflow[5];
+  long long spin_limit;  // bound on the polls of a grid-barrier wait
 };
 
 enum Blend : int { kBlendNone = 0, kBlendStage2 = 1, kBlendStage3 = 2 };
@@ -96,8 +97,10 @@ constexpr int kMaxBlock = 256;
 
 // tau of row r's instance: c_cfl times the CFL bound in the first RK stage,
 // the stored tau_n in the later ones.
+// (The reduction word is read through L2: in a persistent launch other
+// blocks updated it with atomics after this block may have touched it.)
 __device__ __forceinline__ double stage_tau(const DeviceGraph& G, int ins, int tau_mode, double cfl) {
-  return tau_mode == 0 ? cfl * __longlong_as_double((long long)G.tau_min[ins]) : G.tau[ins];
+  return tau_mode == 0 ? cfl * __longlong_as_double((long long)__ldcg(&G.tau_min[ins])) : G.tau[ins];
 }
 
 // Thread r < n_inst keeps instance r's books after the CFL reduction: the
@@ -105,7 +108,7 @@ __device__ __forceinline__ double stage_tau(const DeviceGraph& G, int ins, int t
 __device__ __forceinline__ void instance_books(const DeviceGraph& G, int64_t r, int tau_mode, double cfl,
                                                int accumulate_time, DeviceScalars* scal) {
   if (r >= G.n_inst) return;
-  const double tmax = __longlong_as_double((long long)G.tau_min[r]);
+  const double tmax = __longlong_as_double((long long)__ldcg(&G.tau_min[r]));
   G.tau_max[r] = tmax;
   if (tau_mode == 0) {
     const double tau = cfl * tmax;
@@ -132,6 +135,64 @@ __device__ __forceinline__ void reduce_tau_candidate(const DeviceGraph& G, int64
     atomicMin(&G.tau_min[ins], (unsigned long long)__double_as_longlong(cand));
   }
 }
+
+// Grid-wide barrier of a cooperative (co-resident) launch.  Thread 0 of each
+// block arrives on a counter in device memory; the last arrival resets it
+// and advances the generation, the others poll the generation at most
+// spin_limit times.  A wait that runs out sets the abort flag and
+// kStatusTimeout; every block then leaves at its next barrier.  Returns
+// false once the launch is aborted.  count and abort start at zero.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* b, long long spin_limit, DeviceScalars* scal) {
+  __shared__ int s_go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &b->gen;
+    volatile int* vabort = &b->abort;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == g) {
+        if (*vabort || ++polls > spin_limit) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (!ok && !*vabort) {
+      atomicExch(&b->abort, 1);
+      atomicOr(&scal->status, kStatusTimeout);
+    }
+    __threadfence();
+    s_go = ok && !*vabort;
+  }
+  __syncthreads();
+  return s_go != 0;
+}
+
+// Arguments of the persistent (one launch per euler_step) kernel.
+struct PersistentStage {
+  DeviceGraph G;
+  StageConfig C;
+  StageBuffers B;
+  const double* Uin;
+  double* Uout;
+  const double* Un;
+  GridBarrier* bar;
+  int blend, tau_mode, accumulate_time, skip_write_on_error;
+};
 
 // Kernel ids of one euler_step (also the order of idp_profile_read).
 enum KernelId : int {
@@ -172,10 +233,22 @@ struct Profiler {
 // tau_mode 1: the stored tau is used and checked (stages 2, 3, fixed tau).
 // accumulate_time adds tau to the simulated time (once per RK step).
 // Returns the number of kernel launches.
+// persistent (with bar, device memory): the whole euler_step as one
+// cooperative launch of k_stage_persistent (not with trace or profiling,
+// which take the per-step kernels).
 int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
                       bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof = nullptr,
-                      int block = 128);
+                      int block = 128, GridBarrier* bar = nullptr);
+
+// Blocks of the persistent stage kernel that fit on the device at once.
+int persistent_grid_limit(int block, bool mixed);
+// The FP32-mixed persistent stage kernel (idp_mixed.cu).
+const void* persistent_kernel_mixed();
+// Grid-barrier self-test (cooperative launch of `blocks` blocks, `rounds`
+// barriers, optionally with block 0 absent); passes counts block passes.
+cudaError_t launch_barrier_selftest(GridBarrier* bar, long long spin_limit, int blocks, int rounds, int skip_block0,
+                                    unsigned int* passes, DeviceScalars* scal, cudaStream_t s);
 
 // Counts nodes with rho <= 0, epsilon <= 0, non-finite values; writes
 // {count_rho, count_eps, count_nonfinite} as doubles plus rho_min, eps_min

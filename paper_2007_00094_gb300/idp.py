@@ -32,7 +32,7 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
-            "idp_adjoint_record", "idp_adjoint_backward"]
+            "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -98,11 +98,12 @@ def load(path: str = LIB_PATH):
     L.idp_tau_max_noalloc.argtypes = [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.idp_set_instances.argtypes = [_vp, C.c_int64, _i64p]
     L.idp_get_instance_times.argtypes = [_vp, _dp, _dp]
-    L.idp_set_schedule.argtypes = [_vp, C.c_int, C.c_int]
-    L.idp_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]
+    L.idp_set_schedule.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
+    L.idp_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _dp]
     L.idp_adjoint_euler_step.argtypes = [_vp, _vp, C.c_double, _vp, _vp, _dp, C.c_int]
     L.idp_adjoint_record.argtypes = [_vp, C.c_int, C.c_int]
     L.idp_adjoint_backward.argtypes = [_vp, _vp, _vp, C.c_int]
+    L.idp_barrier_selftest.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_longlong, C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -276,14 +277,24 @@ class Solver:
         _check(self._ctx, load().idp_get_instance_times(self._ctx, _ptr(t), _ptr(tau)))
         return t, tau
 
-    def set_schedule(self, block_size=128, use_graph=False):
-        _check(self._ctx, load().idp_set_schedule(self._ctx, int(block_size), int(bool(use_graph))))
+    def set_schedule(self, block_size=128, use_graph=False, persistent=False):
+        _check(self._ctx, load().idp_set_schedule(self._ctx, int(block_size), int(bool(use_graph)),
+                                                  int(bool(persistent))))
 
     def autotune(self, steps=2):
-        """Times every schedule and keeps the fastest; returns (block, graph, ms/step)."""
-        b, g, ms = C.c_int(), C.c_int(), C.c_double()
-        _check(self._ctx, load().idp_autotune(self._ctx, int(steps), C.byref(b), C.byref(g), C.byref(ms)))
-        return b.value, bool(g.value), ms.value
+        """Times every schedule and keeps the fastest; returns
+        (block, graph, persistent, ms/step)."""
+        b, g, p, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(self._ctx, load().idp_autotune(self._ctx, int(steps), C.byref(b), C.byref(g), C.byref(p),
+                                              C.byref(ms)))
+        return b.value, bool(g.value), bool(p.value), ms.value
+
+    def barrier_selftest(self, blocks, rounds, skip_block0=False, spin_limit=1 << 20):
+        """Runs the grid-barrier self-test; returns (status, block-passes)."""
+        passes = C.c_int(0)
+        st = load().idp_barrier_selftest(self._ctx, int(blocks), int(rounds), int(bool(skip_block0)),
+                                         int(spin_limit), C.byref(passes))
+        return st, passes.value
 
     # -- reverse mode ---------------------------------------------------------
 

@@ -71,40 +71,61 @@ def test_batch_matches_oracle(batch, n_threads):
         assert rel_field_err(got, ref).max() <= 1e-11
 
 
-def test_schedules_and_graph_replay_are_bitwise_equal(batch):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_schedules_and_graph_replay_are_bitwise_equal(batch, precision):
+    """Per-step kernels and the persistent (one cooperative launch per
+    euler_step) schedule, each with and without graph replay, at every
+    block size, give bitwise the same states."""
     parts, mesh, off, U = batch
     outs = []
-    for block in (64, 128, 256):
-        for graph in (False, True):
-            s = _solver(mesh)
-            s.set_instances(off)
-            s.set_schedule(block, graph)
-            s.init_state(U)
-            s.step(3)
-            s.synchronize()
-            outs.append(s.get_state())
-            if graph:
-                assert s.launch_count() == 3 * 21
+    for persistent in (False, True):
+        for block in (64, 128, 256):
+            for graph in (False, True):
+                s = _solver(mesh, precision=precision)
+                s.set_instances(off)
+                s.set_schedule(block, graph, persistent)
+                s.init_state(U)
+                s.step(3)
+                s.synchronize()
+                outs.append(s.get_state())
+                assert s.launch_count() == 3 * (3 if persistent else 21)
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
 
 
-def test_autotune_keeps_state_and_picks_a_schedule(batch):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_persistent_schedule_on_a_large_mesh(precision):
+    """More rows than co-resident threads: the persistent kernel's blocks loop
+    over rows (grid-stride); results equal the per-step kernels bitwise."""
+    mesh = W.vortex_mesh(48)
+    U = W.bumpy_vortex_state(mesh)
+    out = []
+    for persistent in (False, True):
+        s = _solver(mesh, precision=precision)
+        s.set_schedule(256, False, persistent)
+        s.init_state(U)
+        s.step(2)
+        s.synchronize()
+        out.append(s.get_state())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_grid_barrier_selftest_and_timeout(batch):
+    """The persistent schedule's grid barrier: all blocks pass every round;
+    with one block absent the other blocks' bounded waits run out, the call
+    reports IDP_ERR_TIMEOUT and the context stays usable."""
     parts, mesh, off, U = batch
     s = _solver(mesh)
+    st, passes = s.barrier_selftest(blocks=152, rounds=10)
+    assert st == 0 and passes == 1520
+    st, passes = s.barrier_selftest(blocks=152, rounds=10, skip_block0=True, spin_limit=1000)
+    assert st == 8  # IDP_ERR_TIMEOUT
+    assert passes == 0
     s.set_instances(off)
     s.init_state(U)
-    block, graph, ms = s.autotune(steps=1)
-    assert block in (64, 128, 256) and ms > 0
-    np.testing.assert_array_equal(s.get_state(), U)
-    assert np.all(s.instance_times()[0] == 0.0)
     s.step(1)
     s.synchronize()
-    ref = _solver(mesh)
-    ref.set_instances(off)
-    ref.init_state(U)
-    ref.step(1)
-    np.testing.assert_array_equal(s.get_state(), ref.get_state())
+    assert np.all(np.isfinite(s.get_state()))
 
 
 def test_instances_must_not_share_entries(batch):
