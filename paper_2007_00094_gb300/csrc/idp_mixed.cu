@@ -248,8 +248,8 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
 }
 
 // Step 0: per-node quantities (FP32 copies) and an FP32 copy of the state.
-__device__ __forceinline__ void row_node_m(int64_t n, const double* __restrict__ U, float* __restrict__ Q,
-                                           float* __restrict__ Uf, DeviceScalars* scal, int64_t i) {
+__device__ __forceinline__ void row_node_m(int64_t n, const double* U, float* Q,
+                                           float* Uf, DeviceScalars* scal, int64_t i) {
   double u[kFields];
   load5(U, n, i, u);
   const double rho = u[0];
@@ -277,10 +277,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_node_m(int64_t n, const double* _
 }
 
 // Step 1 in FP32: d_ij (upper edges) with 1/(2 d_ij), flux differences and alpha_i.
-__device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGraph& M, const float* __restrict__ U,
-                                           const float* __restrict__ Q, float* __restrict__ d,
-                                           float* __restrict__ dinv, float* __restrict__ dF,
-                                           float* __restrict__ alpha, int64_t r) {
+__device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGraph& M, const float* U,
+                                           const float* Q, float* d,
+                                           float* dinv, float* dF,
+                                           float* alpha, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph 
 
 // Step 2: lower half of d and 1/(2d), and the CFL bound min_i m_i/(-2 d_ii)
 // with d_ii summed in FP64.
-__device__ __forceinline__ double row_diag_m(const DeviceGraph& G, float* __restrict__ d, float* __restrict__ dinv,
+__device__ __forceinline__ double row_diag_m(const DeviceGraph& G, float* d, float* dinv,
                                              int64_t r) {
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -382,11 +382,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_diag_m(DeviceGraph G, float* __re
 // the FP64 state; bounds rho_i + min/max_j (Ubar_ij - U_i)_rho and phi_min;
 // R_i = -sum_j df_ij - f_i.s_i + sum_j d^H_ij (U_j - U_i) in FP32.
 __device__ __forceinline__ void row_low_order_m(const DeviceGraph& G, const StageConfig& C,
-                                                const double* __restrict__ U, const float* __restrict__ Uf,
-                                                const float* __restrict__ Q, const float* __restrict__ d,
-                                                const float* __restrict__ dinv, const float* __restrict__ dF,
-                                                const float* __restrict__ alpha, double* __restrict__ UL,
-                                                float* __restrict__ R, double* __restrict__ bnd, int tau_mode,
+                                                const double* U, const float* Uf,
+                                                const float* Q, const float* d,
+                                                const float* dinv, const float* dF,
+                                                const float* alpha, double* UL,
+                                                float* R, double* bnd, int tau_mode,
                                                 int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
@@ -460,10 +460,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageC
 
 // Step 4 in FP32: P_ij and the first limiter values.
 __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const MixedGraph& M, const StageConfig& C,
-                                                 const float* __restrict__ Uf, const float* __restrict__ d,
-                                                 const float* __restrict__ alpha, const double* __restrict__ UL,
-                                                 const float* __restrict__ R, const double* __restrict__ bnd,
-                                                 float* __restrict__ P, float* __restrict__ l, int tau_mode,
+                                                 const float* Uf, const float* d,
+                                                 const float* alpha, const double* UL,
+                                                 const float* R, const double* bnd,
+                                                 float* P, float* l, int tau_mode,
                                                  int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
@@ -516,9 +516,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, Mixed
 // Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
 // FP32, added to FP64), P_ij <- (1 - min) P_ij and new l_ij.
 __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const StageConfig& C,
-                                                   const double* __restrict__ Ucur, double* __restrict__ Unext,
-                                                   float* __restrict__ P, const float* __restrict__ lold,
-                                                   float* __restrict__ lnew, const double* __restrict__ bnd,
+                                                   const double* Ucur, double* Unext,
+                                                   float* P, const float* lold,
+                                                   float* lnew, const double* bnd,
                                                    int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -569,9 +569,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, Sta
 
 // Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
 __device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageConfig& C,
-                                            const double* __restrict__ Ucur, const float* __restrict__ P,
-                                            const float* __restrict__ l, const double* __restrict__ Un,
-                                            double* __restrict__ Uout, double* __restrict__ Ulim, DeviceScalars* scal,
+                                            const double* Ucur, const float* P,
+                                            const float* l, const double* Un,
+                                            double* Uout, double* Ulim, DeviceScalars* scal,
                                             int blend, int skip_write_on_error, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -633,7 +633,10 @@ struct PersistentStageMixed {
 };
 
 // One FP32-mixed euler_step in a single cooperative launch (see
-// k_stage_persistent in idp_stage.cu for the barrier placement).
+// k_stage_persistent in idp_stage.cu for the barriers and the work list).
+// No register cap: under one, ptxas fuses the FP32 limiter arithmetic
+// differently, and rounding-level changes move limiter decisions, so the
+// schedules would no longer agree bitwise.
 __global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStageMixed pm) {
   const PersistentStage& a = pm.a;
   const DeviceGraph& G = a.G;
@@ -642,39 +645,45 @@ __global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStag
   const MixedGraph& M = pm.M;
   const MixedBuffers& X = pm.X;
   const int64_t n = G.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t i = t0; i < n; i += stride) row_node_m(n, a.Uin, X.Q, X.Uf, B.scal, i);
-  for (int64_t i = t0; i < G.n_inst; i += stride) G.tau_min[i] = 0x7ff0000000000000ull;
+  unsigned int* tile = a.bar->tile;
+  for_each_row_tile(&tile[0], n, [&](int64_t i) {
+    if (i < n) row_node_m(n, a.Uin, X.Q, X.Uf, B.scal, i);
+    if (i < G.n_inst) G.tau_min[i] = 0x7ff0000000000000ull;
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride) row_edge_m(G, M, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, r);
+  for_each_row_tile(&tile[1], n, [&](int64_t r) {
+    if (r < n) row_edge_m(G, M, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, r);
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
-    const int64_t r = b0 + threadIdx.x;
+  for_each_row_tile(&tile[2], n, [&](int64_t r) {
     reduce_tau_candidate(G, r, r < n ? row_diag_m(G, X.d, X.dinv, r) : INFINITY);
-  }
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride) {
+  for_each_row_tile(&tile[3], n, [&](int64_t r) {
     instance_books(G, r, a.tau_mode, C.cfl, a.accumulate_time, B.scal);
-    row_low_order_m(G, C, a.Uin, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.UL, X.R, B.bnd, a.tau_mode, r);
-  }
+    if (r < n) row_low_order_m(G, C, a.Uin, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.UL, X.R, B.bnd, a.tau_mode, r);
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride)
-    row_flux_limit_m(G, M, C, X.Uf, X.d, X.alpha, B.UL, X.R, B.bnd, X.P, X.l[0], a.tau_mode, r);
+  for_each_row_tile(&tile[4], n, [&](int64_t r) {
+    if (r < n) row_flux_limit_m(G, M, C, X.Uf, X.d, X.alpha, B.UL, X.R, B.bnd, X.P, X.l[0], a.tau_mode, r);
+  });
   const double* cur = B.UL;
   int lbuf = 0, wbuf = 0;
   for (int pass = 1; pass < C.limiter_passes; ++pass) {
     if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
     double* next = B.Uw[wbuf];
-    for (int64_t r = t0; r < n; r += stride)
-      row_limiter_pass_m(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd, r);
+    const int ph = 4 + pass < 11 ? 4 + pass : 11;
+    for_each_row_tile(&tile[ph], n, [&](int64_t r) {
+      if (r < n) row_limiter_pass_m(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd, r);
+    });
     cur = next;
     wbuf ^= 1;
     lbuf ^= 1;
   }
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride)
-    row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+  for_each_row_tile(&tile[11], n, [&](int64_t r) {
+    if (r < n) row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+  });
 }
 
 }  // namespace

@@ -38,7 +38,7 @@ __device__ __forceinline__ Side load_side(const double* U, const double* Q, int6
 
 // Step 0: per-node quantities (Sec. 2): 1/rho, p, c, p^(-1/7), 1/p,
 // eta/rho with eta = (rho eps)^(5/12), (E + p)/rho and phi = eps rho^(-7/5).
-__device__ __forceinline__ void row_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
+__device__ __forceinline__ void row_node(int64_t n, const double* U, double* Q,
                                          DeviceScalars* scal, int64_t i) {
   double u[kFields];
   load5(U, n, i, u);
@@ -75,10 +75,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __r
 // and the indicator alpha_i (Sec. 3.8) over all j in I(i).  The flux
 // differences (f_j - f_i).c_ij computed for the indicator are stored (in the
 // P buffer, free until Step 4) for the bar states and R_i of Step 3.
-__device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* __restrict__ U,
-                                         const double* __restrict__ Q, double* __restrict__ d,
-                                         double* __restrict__ dinv, double* __restrict__ dF,
-                                         double* __restrict__ alpha, int64_t r) {
+__device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
+                                         const double* Q, double* d,
+                                         double* dinv, double* dF,
+                                         double* alpha, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double*
 
 // Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
 // CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
-__device__ __forceinline__ double row_diag(const DeviceGraph& G, double* __restrict__ d, double* __restrict__ dinv,
+__device__ __forceinline__ double row_diag(const DeviceGraph& G, double* d, double* dinv,
                                            int64_t r) {
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, double* __res
 // flux differences df_ij = (f_j - f_i).c_ij of Step 1,
 // Ubar_ij = (U_i + U_j)/2 - df_ij/(2 d_ij) and, since sum_j c_ij = s_i,
 // sum_j -f_j.c_ij = -sum_j df_ij - f_i.s_i (s_i is zero up to rounding).
-__device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageConfig& C, const double* __restrict__ U,
-                                              const double* __restrict__ Q, const double* __restrict__ d,
-                                              const double* __restrict__ dinv, const double* __restrict__ dF,
-                                              const double* __restrict__ alpha, double* __restrict__ UL,
-                                              double* __restrict__ R, double* __restrict__ bnd, int tau_mode,
+__device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageConfig& C, const double* U,
+                                              const double* Q, const double* d,
+                                              const double* dinv, const double* dF,
+                                              const double* alpha, double* UL,
+                                              double* R, double* bnd, int tau_mode,
                                               int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageCon
 // Step 4: antidiffusive fluxes P_ij (eq. def-p) with b_ij = -m_ij/m_j,
 // b_ji = -m_ij/m_i (j != i) and the first limiter values l_ij.
 __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const StageConfig& C,
-                                               const double* __restrict__ U, const double* __restrict__ d,
-                                               const double* __restrict__ alpha, const double* __restrict__ UL,
-                                               const double* __restrict__ R, const double* __restrict__ bnd,
-                                               double* __restrict__ P, double* __restrict__ l, int tau_mode,
+                                               const double* U, const double* d,
+                                               const double* alpha, const double* UL,
+                                               const double* R, const double* bnd,
+                                               double* P, double* l, int tau_mode,
                                                int64_t r) {
   const double tau = stage_tau(G, instance_of(G, r), tau_mode, C.cfl);
   const int64_t n = G.n, ns = G.n_slots;
@@ -318,9 +318,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageCo
 // Steps 5, 6, ...: U_i += sum_j lambda_i min(l_ij, l_ji) P_ij, then (not in
 // the last pass) P_ij <- (1 - min(l_ij, l_ji)) P_ij and new l_ij.
 __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const StageConfig& C,
-                                                 const double* __restrict__ Ucur, double* __restrict__ Unext,
-                                                 double* __restrict__ P, const double* __restrict__ lold,
-                                                 double* __restrict__ lnew, const double* __restrict__ bnd, int64_t r) {
+                                                 const double* Ucur, double* Unext,
+                                                 double* P, const double* lold,
+                                                 double* lnew, const double* bnd, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -370,10 +370,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, Stage
 // Last limiter pass, boundary post-processing (slip walls drop the flagged
 // normal momentum components, inflow nodes take the inflow state) and the
 // SSP-RK3 blend (Sec. 3.6): stage 2 3/4 U^n + 1/4 E, stage 3 1/3 U^n + 2/3 E.
-__device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfig& C, const double* __restrict__ Ucur,
-                                          const double* __restrict__ P, const double* __restrict__ l,
-                                          const double* __restrict__ Un, double* __restrict__ Uout,
-                                          double* __restrict__ Ulim, DeviceScalars* scal, int blend,
+__device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfig& C, const double* Ucur,
+                                          const double* P, const double* l,
+                                          const double* Un, double* Uout,
+                                          double* Ulim, DeviceScalars* scal, int blend,
                                           int skip_write_on_error, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
@@ -428,49 +428,55 @@ __global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig 
 }
 
 // One euler_step in a single cooperative launch: the phases of the kernels
-// above run over all rows (grid-stride) with a grid barrier between them,
-// where the kernel boundaries were.  Data a phase reads was written before
-// the barrier that precedes it (or before the launch), never earlier in the
-// launch by another block, so no block can hold a stale copy of it.
-__global__ void __launch_bounds__(kMaxBlock) k_stage_persistent(PersistentStage a) {
+// above run over all rows (tiles of 32 rows handed out dynamically) with a
+// grid barrier between them, where the kernel boundaries were.  Data a phase
+// reads was written before the barrier that precedes it (or before the
+// launch), never earlier in the launch by another block, so no block can
+// hold a stale copy of it.
+__global__ void __launch_bounds__(kMaxBlock, 2) k_stage_persistent(PersistentStage a) {
   const DeviceGraph& G = a.G;
   const StageConfig& C = a.C;
   const StageBuffers& B = a.B;
   const int64_t n = G.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int64_t i = t0; i < n; i += stride) row_node(n, a.Uin, B.node, B.scal, i);
-  for (int64_t i = t0; i < G.n_inst; i += stride) G.tau_min[i] = 0x7ff0000000000000ull;
+  unsigned int* tile = a.bar->tile;
+  for_each_row_tile(&tile[0], n, [&](int64_t i) {
+    if (i < n) row_node(n, a.Uin, B.node, B.scal, i);
+    if (i < G.n_inst) G.tau_min[i] = 0x7ff0000000000000ull;
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride) row_edge(G, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, r);
+  for_each_row_tile(&tile[1], n, [&](int64_t r) {
+    if (r < n) row_edge(G, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, r);
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  // whole warps iterate together: the CFL reduction shuffles across the warp
-  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
-    const int64_t r = b0 + threadIdx.x;
+  for_each_row_tile(&tile[2], n, [&](int64_t r) {
     reduce_tau_candidate(G, r, r < n ? row_diag(G, B.d, B.dinv, r) : INFINITY);
-  }
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride) {
+  for_each_row_tile(&tile[3], n, [&](int64_t r) {
     instance_books(G, r, a.tau_mode, C.cfl, a.accumulate_time, B.scal);
-    row_low_order(G, C, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, a.tau_mode, r);
-  }
+    if (r < n) row_low_order(G, C, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, a.tau_mode, r);
+  });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride)
-    row_flux_limit(G, C, a.Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], a.tau_mode, r);
+  for_each_row_tile(&tile[4], n, [&](int64_t r) {
+    if (r < n) row_flux_limit(G, C, a.Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], a.tau_mode, r);
+  });
   const double* cur = B.UL;
   int lbuf = 0, wbuf = 0;
   for (int pass = 1; pass < C.limiter_passes; ++pass) {
     if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
     double* next = B.Uw[wbuf];
-    for (int64_t r = t0; r < n; r += stride)
-      row_limiter_pass(G, C, cur, next, B.P, B.l[lbuf], B.l[lbuf ^ 1], B.bnd, r);
+    const int ph = 4 + pass < 11 ? 4 + pass : 11;
+    for_each_row_tile(&tile[ph], n, [&](int64_t r) {
+      if (r < n) row_limiter_pass(G, C, cur, next, B.P, B.l[lbuf], B.l[lbuf ^ 1], B.bnd, r);
+    });
     cur = next;
     wbuf ^= 1;
     lbuf ^= 1;
   }
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
-  for (int64_t r = t0; r < n; r += stride)
-    row_final(G, C, cur, B.P, B.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+  for_each_row_tile(&tile[11], n, [&](int64_t r) {
+    if (r < n) row_final(G, C, cur, B.P, B.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+  });
 }
 
 // Self-test of the grid barrier: every block passes `rounds` barriers and

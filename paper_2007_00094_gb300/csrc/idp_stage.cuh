@@ -146,6 +146,7 @@ struct GridBarrier {
   unsigned int count;
   unsigned int gen;
   int abort;
+  unsigned int tile[12];  // next row tile of each phase (dynamic work list)
 };
 
 __device__ __forceinline__ bool grid_barrier(GridBarrier* b, long long spin_limit, DeviceScalars* scal) {
@@ -180,6 +181,23 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* b, long long spin_limi
   }
   __syncthreads();
   return s_go != 0;
+}
+
+// Dynamic work list of a persistent phase: each warp takes the next tile of
+// 32 rows (one sliced-ELL slice) from the phase's counter until none are
+// left, so blocks that drew cheap rows take more tiles.  f(r) is called by
+// all 32 lanes of the warp, also for r >= n (padding rows of the last tile).
+template <typename F>
+__device__ __forceinline__ void for_each_row_tile(unsigned int* counter, int64_t n, F&& f) {
+  const int64_t tiles = (n + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if ((int64_t)t >= tiles) break;
+    f(((int64_t)t << 5) + lane);
+  }
 }
 
 // Arguments of the persistent (one launch per euler_step) kernel.
