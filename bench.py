@@ -40,9 +40,14 @@ FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "fl
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s; a dependent-free DFMA
 # stream measured 1.197 TFLOP/s at 1.97 GHz on this machine).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by kernel; None until captured for the current kernel source.
-NCU_TRAFFIC_BYTES = {}
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# for the workloads of this file, keyed by kernel.  Captured on smaller meshes
+# of the same workloads (the full-size inputs are too large for an ncu replay)
+# and scaled by the number of matrix entries (profiles/ holds the captures):
+# FP64 k_flux_limit 1.266 GB at h = 1/80 (17,679,673 entries) -> h = 1/120;
+# FP32-mixed k_limiter_pass_m 1.976 GB at 96^3 (23,393,656 entries) -> 128^3.
+NCU_TRAFFIC_BYTES = {"flux_limit": 1.265932e9 * 59373973 / 17679673}
+NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 1.976342e9 * 55742968 / 23393656}
 
 
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
@@ -144,8 +149,9 @@ def pattern_mixed(stream, args):
             bytes_per_launch = per_slot * s.nnz + per_node * mesh.n_nodes
             peak, src = _hbm_peak()
             achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+            traffic = NCU_TRAFFIC_BYTES_MIXED.get(dom) if args.sod_n == 128 else None
             entry["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": achieved / peak, "traffic": None, "peak_source": src,
+                                 "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                                  "work": f"{per_slot} B/entry x {s.nnz} + {per_node} B/node x {mesh.n_nodes}"}
         out[name] = entry
         s.close()
@@ -493,7 +499,7 @@ def main():
         dom_ms, dom_n = prof[dom]
         per_launch_s = dom_ms / dom_n * 1e-3
         achieved = FLOP_PER_NNZ[dom] * nnz / per_launch_s / 1e12
-        traffic = NCU_TRAFFIC_BYTES.get(dom)
+        traffic = NCU_TRAFFIC_BYTES.get(dom) if args.m == 120 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
