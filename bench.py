@@ -133,13 +133,20 @@ def pattern_mixed(stream, args):
     mesh = W.sod_cube_mesh(args.sod_n)
     U0 = W.sod_state(mesh)
     out = {"config": {"workload": f"sod_tube_{args.sod_n}^3_slip_walls", "nodes": mesh.n_nodes,
-                      "steps_timed": args.pattern_steps, "warmup": args.warmup}}
-    states = {}
+                      "steps_timed": args.pattern_steps, "warmup": args.warmup,
+                      "accuracy_steps": max(args.sod_steps, args.pattern_steps + args.warmup)}}
+    states, times, bounds = {}, {}, {}
     for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
         s = Solver(mesh, stream=stream, precision=prec)
         s.init_state(U0)
         ms, prof = _time_steps(s, stream, args.pattern_steps, args.warmup)
+        # untimed: continue to the accuracy horizon
+        s.step(max(args.sod_steps - args.pattern_steps - args.warmup, 0))
+        s.synchronize()
         states[name] = s.get_state()
+        times[name] = s.time()[0]
+        st, rep = s.check_bounds()
+        bounds[name] = {"status": st, "rho_min": rep.rho_min, "eps_min": rep.eps_min}
         entry = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                  "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
         if prec == 1:
@@ -160,6 +167,8 @@ def pattern_mixed(stream, args):
     scale = np.where(scale > 1e-12 * scale.max(), scale, scale.max())
     err = np.abs(states["fp32_mixed"] - ref).mean(axis=1) / scale
     out["fp32_mixed"]["l1_error_vs_fp64"] = {f: float(e) for f, e in zip(["rho", "m_x", "m_y", "m_z", "E"], err)}
+    out["fp32_mixed"]["accuracy_time"] = {"fp64": times["fp64"], "fp32_mixed": times["fp32_mixed"]}
+    out["fp32_mixed"]["invariants"] = bounds
     out["fp32_mixed"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_mixed"]["ms_per_step"]
     return out
 
@@ -389,6 +398,8 @@ def main():
     ap.add_argument("--no-patterns", action="store_true", help="skip the FP32-mixed / batched / adjoint lines")
     ap.add_argument("--pattern-steps", type=int, default=5)
     ap.add_argument("--sod-n", type=int, default=128)
+    ap.add_argument("--sod-steps", type=int, default=100,
+                    help="total steps (timed ones included) after which the mixed path is compared with FP64")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
     ap.add_argument("--adj-steps", type=int, default=100)

@@ -20,12 +20,26 @@ __device__ __forceinline__ double ipow(double w) {
 }
 
 // x^(-1/K) for x > 0.  A single-precision seed w0 = powf(x, -1/K) (relative
-// error below 3e-7) is corrected with the second-order series of
+// error below 3e-7; x enters and w0 leaves FP32 by exponent and mantissa bit
+// arithmetic on the integer pipe, the FP64 pipe being the bottleneck) is
+// corrected with the second-order series of
 // (1 - delta)^(-1/K) = 1 + delta/K + (K+1) delta^2/(2K^2) + O(delta^3), where
 // delta = 1 - x w0^K; the neglected term is ~delta^3 < 1e-17 for K <= 12.
 template <int K>
 __device__ __forceinline__ double inv_root(double x) {
-  const double w0 = (double)powf((float)x, -1.0f / (float)K);
+  double w0;
+  {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023 + 127;
+    if (e > 0 && e < 255) {
+      const float xf = __int_as_float((e << 23) | (int)((b >> 29) & 0x7fffff));
+      const int wb = __float_as_int(powf(xf, -1.0f / (float)K));
+      w0 = __longlong_as_double(((long long)(((wb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                ((long long)(wb & 0x7fffff) << 29));
+    } else {
+      w0 = (double)powf((float)x, -1.0f / (float)K);
+    }
+  }
   const double delta = 1.0 - x * ipow<K>(w0);
   const double c1 = 1.0 / (double)K, c2 = (double)(K + 1) / (2.0 * (double)K * (double)K);
   return fma(w0, fma(c2, delta, c1) * delta, w0);
@@ -129,8 +143,85 @@ __device__ __forceinline__ double drho_eps_at(const double* U, const double* P, 
 // a Psi within rounding of zero is arbitrary; Psi >= -1e-13 (|rho eps| +
 // |phi_min rho^(gamma+1)|) counts as admissible, a margin far above rounding
 // and far below the tolerance of the invariant checks.
+// (|x| by clearing the sign bit, on the integer pipe)
 __device__ __forceinline__ double psi_slack(double rho_eps, double phi_term) {
-  return 1e-13 * (fabs(rho_eps) + fabs(phi_term));
+  return 1e-13 * (__longlong_as_double(__double_as_longlong(rho_eps) & 0x7fffffffffffffffLL) +
+                  __longlong_as_double(__double_as_longlong(phi_term) & 0x7fffffffffffffffLL));
+}
+
+// Double to float rounded toward zero by bit arithmetic (integer pipe): the
+// sign, the exponent rebiased and the top 23 mantissa bits; relative error
+// below 2^-23.  Zero maps to zero; doubles outside the normal float range
+// take the conversion instruction.
+__device__ __forceinline__ float to_float_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e > 0 && e < 255)
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7fffffu));
+  if ((b << 1) == 0ull) return 0.0f;
+  return __double2float_rz(x);
+}
+
+// FP32 pre-check of the FP64 limiter's acceptance test.  Per row, Psi(0) =
+// rho eps(U) - phi_min rho^(gamma+1) and phi_min rho^(gamma+1) come from FP64;
+// per entry Psi(t) = Psi(0) + t (g + t h) - phi_min rho^(gamma+1) q along
+// U + tP (g, h the coefficients of rho eps(U + tP), q = (1 + t P_rho/rho)^2.4
+// - 1) is evaluated in FP32 with a bound on its error: the roundings of the
+// FP32 copies of U, P, t and of the anchor (u = 2^-24, 2^-23 for the copies
+// rounded toward zero), of g, h and s (a few per term), of log1p/expm1 (an
+// ulp each, amplified by 2.4 (1 + q)) and of the combining operations, plus
+// 1e-15 (|rho E| + |m|^2/2 + phi_min rho^(gamma+1)) at t and at 0 for the
+// FP64 evaluations.  The FP64 test accepts when its Psi(t) >= -1e-13 (|rho
+// eps| + phi_min rho^(gamma+1)); the pre-check answers "accepts" only when
+// that holds for every value within the bounds (0.9 of the slack), so a
+// limiter that takes its answer returns exactly what the FP64 test returns.
+struct PsiCheck32 {
+  float u[5];    // U in FP32
+  float psi0;    // Psi(0), rounded from FP64
+  float pp;      // phi_min rho^(gamma+1), rounded from FP64
+  float inv_rho; // 1/rho in FP32
+  float k0;      // |rho E| + |m|^2/2 + pp in FP32
+};
+
+__device__ __forceinline__ PsiCheck32 make_psi_check(const double* U, double phi_min) {
+  PsiCheck32 a;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) a.u[f] = to_float_rz(U[f]);
+  const double re = U[0] * U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+  const double pp = U[0] > 0.0 ? phi_min * pow_12_5(U[0]) : 0.0;
+  a.psi0 = to_float_rz(re - pp);
+  a.pp = to_float_rz(pp);
+  a.inv_rho = 1.0f / a.u[0];
+  a.k0 = fabsf(a.u[0] * a.u[4]) + 0.5f * (a.u[1] * a.u[1] + a.u[2] * a.u[2] + a.u[3] * a.u[3]) + a.pp;
+  return a;
+}
+
+__device__ __forceinline__ bool psi_accepts_fp32(const PsiCheck32& a, const double* P, double t) {
+  float p[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) p[f] = to_float_rz(P[f]);
+  const float tf = to_float_rz(t);
+  const float s = tf * p[0] * a.inv_rho;
+  if (!(s > -0.5f) || !(a.u[0] > 0.0f)) return false;  // leave strong expansions to FP64
+  const float g = p[0] * a.u[4] + a.u[0] * p[4] - (a.u[1] * p[1] + a.u[2] * p[2] + a.u[3] * p[3]);
+  const float gabs = fabsf(p[0] * a.u[4]) + fabsf(a.u[0] * p[4]) + fabsf(a.u[1] * p[1]) + fabsf(a.u[2] * p[2]) +
+                     fabsf(a.u[3] * p[3]);
+  const float h = p[0] * p[4] - 0.5f * (p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const float habs = fabsf(p[0] * p[4]) + 0.5f * (p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const float lg = log1pf(s);
+  const float q = expm1f(2.4f * lg);
+  const float qa = fabsf(q);
+  const float qe = (1.0f + q) * (7.2f * fabsf(lg) + 24.0f * fabsf(s) / (1.0f + s)) + 3.0f * qa;
+  const float tg = tf * gabs, th = tf * tf * habs;
+  const float psi = a.psi0 + tf * (g + tf * h) - a.pp * q;
+  const float err = 5.9604645e-8f * (8.0f * fabsf(a.psi0) + 18.0f * (tg + th) + a.pp * (8.0f * qa + qe));
+  const float re_t = a.psi0 + a.pp + tf * (g + tf * h);
+  const float r = a.u[0] + tf * p[0], E = a.u[4] + tf * p[4];
+  const float m1 = a.u[1] + tf * p[1], m2 = a.u[2] + tf * p[2], m3 = a.u[3] + tf * p[3];
+  const float ppt = a.pp * (1.0f + q);
+  const float kt = fabsf(r * E) + 0.5f * (m1 * m1 + m2 * m2 + m3 * m3) + ppt;
+  return psi - err >= 1e-15f * (kt + a.k0) - 0.9e-13f * (fabsf(re_t) + ppt);
 }
 
 // limiter.compute(U, P, bounds) of Alg. 2: density interval, then the
@@ -139,13 +230,18 @@ __device__ __forceinline__ double psi_slack(double rho_eps, double phi_term) {
 // safeguards: non-negative discriminants, t_L kept admissible, bracket
 // ordered; Psi >= -psi_slack counts as admissible (for t_R and the new
 // t_L alike).  Returns t_L.
+// With pre (the row's PsiCheck32), an FP32 evaluation settles the first
+// acceptance test where it can (see psi_accepts_fp32); the result is the
+// same.
 __device__ __forceinline__ double limiter(const double* U, const double* P, double rho_min, double rho_max,
-                                          double phi_min, const LimiterParams& prm) {
+                                          double phi_min, const LimiterParams& prm,
+                                          const PsiCheck32* pre = nullptr) {
   double tL = 0.0, tR = 1.0;
   const double rhoU = U[0], rhoP = P[0];
   if (rhoU + tR * rhoP > rho_max && rhoP != 0.0) tR = fabs(rho_max - rhoU) / fabs(rhoP);
   if (rhoU + tR * rhoP < rho_min && rhoP != 0.0) tR = fabs(rho_min - rhoU) / fabs(rhoP);
   tR = fmin(fmax(tR, 0.0), 1.0);
+  if (pre && prm.newton_max > 0 && psi_accepts_fp32(*pre, P, tR)) return tR;
   // Psi and rho^(gamma+1) at the current t_L (t_L = 0 at the start)
   double psiL = 0.0, powL = 0.0;
   bool haveL = false;

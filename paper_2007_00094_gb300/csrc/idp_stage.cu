@@ -276,6 +276,7 @@ __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const Stage
   load5(R, n, r, ri);
   load5(UL, n, r, ul);
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const PsiCheck32 pre = make_psi_check(ul, pmin);
   const double a_i = alpha[r];
   const double inv_mi = G.inv_mi[r];
   const double scale = tau * inv_mi * (double)(len - 1);  // tau / (m_i lambda_i)
@@ -301,7 +302,7 @@ __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const Stage
       pij[f] = scale * (b_ij * rj[f] - b_ji * ri[f] + dd * (uj[f] - ui[f]));
       P[f * ns + p] = pij[f];
     }
-    l[p] = limiter(ul, pij, rmin, rmax, pmin, C.lim);
+    l[p] = limiter(ul, pij, rmin, rmax, pmin, C.lim, &pre);
   }
 }
 
@@ -330,7 +331,8 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) continue;
-    const double lk = fmin(lold[p], lold[G.tpos[p]]);
+    // min of two limiter values in [0, 1] on their bit patterns (integer pipe)
+    const double lk = __longlong_as_double(min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]])));
     const double w = lam * lk;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
@@ -338,24 +340,25 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
 #pragma unroll
   for (int f = 0; f < kFields; ++f) Unext[f * n + r] = u[f];
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  const PsiCheck32 pre = make_psi_check(u, pmin);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) {
       lnew[p] = 0.0;
       continue;
     }
-    const double lk = fmin(lold[p], lold[G.tpos[p]]);
+    const double lk = __longlong_as_double(min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]])));
     double pij[kFields];
     bool zero = true;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
       pij[f] = (1.0 - lk) * P[f * ns + p];
       P[f * ns + p] = pij[f];
-      zero &= pij[f] == 0.0;
+      zero &= (__double_as_longlong(pij[f]) << 1) == 0;  // +0 or -0
     }
     // A zero P_ij (the previous pass accepted it in full, so P_ji is zero
     // too) is moved by no value of l_ij: skip the limiter.
-    lnew[p] = zero ? 1.0 : limiter(u, pij, rmin, rmax, pmin, C.lim);
+    lnew[p] = zero ? 1.0 : limiter(u, pij, rmin, rmax, pmin, C.lim, &pre);
   }
 }
 

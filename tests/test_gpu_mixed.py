@@ -103,3 +103,29 @@ def test_mixed_conservation_and_determinism():
 def W_box():
     from paper_2007_00094_gb300 import workloads as W
     return W.box_mesh((12, 11, 5), periodic=(True, True, True), jitter=0.2, seed=7)
+
+
+def test_mixed_keeps_the_discretization_error_on_sod():
+    """3D Sod tube (129 nodes along x, slip walls, periodic across) advanced to
+    t >= 0.2 in both precisions: the L1 density error against the exact
+    Riemann solution (a textbook solver pinned to published star states,
+    tests/golden/sod_star_state.json) is the discretisation error of the
+    scheme (< 0.015, as for the oracle), and the FP32-mixed path changes it
+    by less than 1 %."""
+    from exact_riemann import sample
+    from paper_2007_00094_gb300 import workloads as W
+    mesh = W.sod_mesh(129, ny=4, nz=4)
+    U0 = W.sod_state(mesh)
+    err = {}
+    for prec in (0, 1):
+        s = _solver(mesh, precision=prec)
+        s.init_state(U0)
+        while s.time()[0] < 0.2:
+            s.step(1)
+        t = s.time()[0]
+        U = s.get_state()
+        exact = sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (mesh.x[:, 0] - 0.5) / t)
+        err[prec] = np.abs(U[0] - exact[0]).mean()
+        assert s.check_bounds()[0] == 0
+    assert err[0] < 0.015 and err[1] < 0.015
+    assert abs(err[1] - err[0]) <= 0.01 * err[0], err
