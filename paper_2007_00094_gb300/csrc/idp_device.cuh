@@ -61,7 +61,10 @@ enum NodeQ : int {
   kQS = 5,       // eta/rho, eta = (rho epsilon)^(1/(gamma+1)) (Harten entropy)
   kQH = 6,       // (E + p)/rho, energy flux factor
   kQPhi = 7,     // phi = epsilon rho^(-gamma) (specific entropy)
-  kNodeQ = 8
+  kQVx = 8,      // velocity m/rho (FP64 stage only)
+  kQVy = 9,
+  kQVz = 10,
+  kNodeQ = 11
 };
 
 struct Side {
@@ -82,6 +85,18 @@ __device__ __forceinline__ void flux_dot(double m1, double m2, double m3, double
   f[4] = __dmul_rn(h, mc);
 }
 
+
+// flux_dot with the velocity v = m/rho given (rounded as __dmul_rn(m, 1/rho),
+// so that the result is bitwise that of flux_dot)
+__device__ __forceinline__ void flux_dot_v(double m1, double m2, double m3, double v1, double v2, double v3, double p,
+                                           double h, double cx, double cy, double cz, double* f) {
+  const double mc = __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
+  f[0] = mc;
+  f[1] = __fma_rn(p, cx, __dmul_rn(v1, mc));
+  f[2] = __fma_rn(p, cy, __dmul_rn(v2, mc));
+  f[3] = __fma_rn(p, cz, __dmul_rn(v3, mc));
+  f[4] = __dmul_rn(h, mc);
+}
 
 // lambda~_max(n, U_L, U_R) of Sec. 3.7.  For gamma = 7/5 the two-rarefaction
 // pressure is p~* = ((c_L + c_R - (u_R - u_L)/5) / (c_L p_L^(-1/7) +
@@ -110,8 +125,10 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   const bool psi_negative = du < 0.0 && 2.0 * dp * dp < du * du * (rho_low * (2.4 * p_max + 0.4 * p_low));
   const double p_star = psi_negative ? p_tr : fmin(p_max, p_tr);
   const double k = 6.0 / 7.0;  // (gamma+1)/(2 gamma)
-  const double lam1 = uL - L.c * sqrt(1.0 + k * fmax((p_star - L.p) * L.inv_p, 0.0));
-  const double lam3 = uR + R.c * sqrt(1.0 + k * fmax((p_star - R.p) * R.inv_p, 0.0));
+  // sqrt(1 + k [z]_+) is exactly 1 where z <= 0 (no shock on that side)
+  const double zL = (p_star - L.p) * L.inv_p, zR = (p_star - R.p) * R.inv_p;
+  const double lam1 = uL - L.c * (zL > 0.0 ? sqrt(1.0 + k * zL) : 1.0);
+  const double lam3 = uR + R.c * (zR > 0.0 ? sqrt(1.0 + k * zR) : 1.0);
   return fmax(fmax(-lam1, 0.0), fmax(lam3, 0.0));
 }
 

@@ -63,6 +63,9 @@ __device__ __forceinline__ void row_node(int64_t n, const double* U, double* Q,
   Q[kQS * n + i] = eta * inv_rho;
   Q[kQH * n + i] = (u[4] + p) * inv_rho;
   Q[kQPhi * n + i] = eps * r7;
+  Q[kQVx * n + i] = __dmul_rn(u[1], inv_rho);
+  Q[kQVy * n + i] = __dmul_rn(u[2], inv_rho);
+  Q[kQVz * n + i] = __dmul_rn(u[3], inv_rho);
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __restrict__ U, double* __restrict__ Q,
@@ -85,6 +88,7 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
   const Side si = load_side(U, Q, n, r);
   const double Ei = U[4 * n + r];
   const double s_i = Q[kQS * n + r], h_i = Q[kQH * n + r];
+  const double vxi = Q[kQVx * n + r], vyi = Q[kQVy * n + r], vzi = Q[kQVz * n + r];
   double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0, b4 = 0.0;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
@@ -94,8 +98,8 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
     const Side sj = load_side(U, Q, n, j);
     const double s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
     double fj[kFields], fi[kFields];
-    flux_dot(sj.mx, sj.my, sj.mz, sj.inv_rho, sj.p, h_j, cx, cy, cz, fj);
-    flux_dot(si.mx, si.my, si.mz, si.inv_rho, si.p, h_i, cx, cy, cz, fi);
+    flux_dot_v(sj.mx, sj.my, sj.mz, Q[kQVx * n + j], Q[kQVy * n + j], Q[kQVz * n + j], sj.p, h_j, cx, cy, cz, fj);
+    flux_dot_v(si.mx, si.my, si.mz, vxi, vyi, vzi, si.p, h_i, cx, cy, cz, fi);
     a += (s_j - s_i) * fj[0];
     double df[kFields];
 #pragma unroll
