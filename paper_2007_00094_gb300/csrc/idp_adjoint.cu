@@ -232,21 +232,22 @@ __global__ void __launch_bounds__(kB) ka_final(DeviceGraph G, const double* __re
   }
 }
 
-// Step 5 reverse: l5_ij = limiter(U5, P'_ij, bounds), P'_ij = (1 - m_ij) P_ij
-// and U5 = U^L + sum_j lambda_i m_ij P_ij with m_ij = min(l4_ij, l4_ji).
-__global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, StageConfig C, const double* __restrict__ U5,
-                                              const double* __restrict__ P, const double* __restrict__ Pp,
-                                              const double* __restrict__ l4, const double* __restrict__ l5,
-                                              const double* __restrict__ bnd, AdjointBuffers A) {
+// The limiter's derivative (a Dual<8> pass, ~255 registers) runs in kernels of
+// its own, over the entries whose limiter value lies strictly inside (0, 1);
+// the rest of each reversed step then runs at a higher occupancy.
+
+// Step 5 reverse, limiter part: l5_ij = limiter(U5, P'_ij, bounds); adds to
+// the adjoints of U5 (row), P'_ij (entry) and the bounds (row, first writer).
+__global__ void __launch_bounds__(kB) ka_pass_lim(DeviceGraph G, StageConfig C, const double* __restrict__ U5,
+                                                  const double* __restrict__ Pp, const double* __restrict__ l5,
+                                                  const double* __restrict__ bnd, AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
-  const double lam = G.lam[r];
   double u5[kFields], gU5[kFields], gb[3] = {0.0, 0.0, 0.0};
-  load5(U5, n, r, u5);
-  load5(A.gU5, n, r, gU5);
+  bool touched = false;
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
@@ -255,6 +256,11 @@ __global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, StageConfig C, cons
     const double l = l5[p];
     // l = 0 and l = 1 are clamped (or skipped) values: locally constant
     if (gl == 0.0 || !(l > 0.0 && l < 1.0)) continue;
+    if (!touched) {
+      load5(U5, n, r, u5);
+      load5(A.gU5, n, r, gU5);
+      touched = true;
+    }
     double pij[kFields], gP[kFields];
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
@@ -265,6 +271,27 @@ __global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, StageConfig C, cons
 #pragma unroll
     for (int f = 0; f < kFields; ++f) A.gPp[f * ns + p] += gP[f];
   }
+  if (touched) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gU5[f * n + r] = gU5[f];
+  }
+  A.gbnd[r] = gb[0];
+  A.gbnd[n + r] = gb[1];
+  A.gbnd[2 * n + r] = gb[2];
+}
+
+// Step 5 reverse, the rest: P'_ij = (1 - m_ij) P_ij and
+// U5 = U^L + sum_j lambda_i m_ij P_ij with m_ij = min(l4_ij, l4_ji).
+__global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, const double* __restrict__ P,
+                                              const double* __restrict__ l4, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  const double lam = G.lam[r];
+  double gU5[kFields];
+  load5(A.gU5, n, r, gU5);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) continue;
@@ -283,31 +310,65 @@ __global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, StageConfig C, cons
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) A.gUL[f * n + r] = gU5[f];
-  A.gbnd[r] = gb[0];
-  A.gbnd[n + r] = gb[1];
-  A.gbnd[2 * n + r] = gb[2];
 }
 
-// Step 4 reverse: l4_ij = limiter(U^L, P_ij, bounds) and
+// Step 4 reverse, limiter part: l4_ij = limiter(U^L, P_ij, bounds); adds to
+// the adjoints of U^L (row), P_ij (entry) and the bounds (row).
+__global__ void __launch_bounds__(kB) ka_flux_lim(DeviceGraph G, StageConfig C, const double* __restrict__ UL,
+                                                  const double* __restrict__ P, const double* __restrict__ l4,
+                                                  const double* __restrict__ bnd, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= G.n) return;
+  const int64_t n = G.n, ns = G.n_slots;
+  const int64_t base = slot_base(G, r);
+  const int len = G.row_len[r];
+  double ul[kFields], gUL[kFields], gb[3] = {0.0, 0.0, 0.0};
+  bool touched = false;
+  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (G.col[p] == r) continue;
+    const double gl = A.gl4_own[p] + A.gl4_tr[G.tpos[p]];
+    const double l = l4[p];
+    if (gl == 0.0 || !(l > 0.0 && l < 1.0)) continue;
+    if (!touched) {
+      load5(UL, n, r, ul);
+      load5(A.gUL, n, r, gUL);
+      touched = true;
+    }
+    double pij[kFields], gP[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      pij[f] = P[f * ns + p];
+      gP[f] = 0.0;
+    }
+    limiter_vjp(ul, pij, rmin, rmax, pmin, gl, C.lim, gUL, gP, gb);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gP[f * ns + p] += gP[f];
+  }
+  if (touched) {
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) A.gUL[f * n + r] = gUL[f];
+    A.gbnd[r] += gb[0];
+    A.gbnd[n + r] += gb[1];
+    A.gbnd[2 * n + r] += gb[2];
+  }
+}
+
+// Step 4 reverse, the rest:
 // P_ij = tau/(m_i lambda_i) (b_ij R_j - b_ji R_i + (d^H_ij - d_ij)(U_j - U_i)).
-__global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, StageConfig C, const double* __restrict__ U,
-                                              const double* __restrict__ UL, const double* __restrict__ P,
-                                              const double* __restrict__ l4, const double* __restrict__ d,
-                                              const double* __restrict__ alpha, const double* __restrict__ bnd,
-                                              AdjointBuffers A) {
+__global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, const double* __restrict__ U,
+                                              const double* __restrict__ P, const double* __restrict__ d,
+                                              const double* __restrict__ alpha, AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
   const double tau = G.tau[instance_of(G, r)];
-  double ul[kFields], gUL[kFields], ui[kFields];
+  double ui[kFields];
   double gRi[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gUi[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  double gb[3] = {0.0, 0.0, 0.0};
-  load5(UL, n, r, ul);
-  load5(A.gUL, n, r, gUL);
   load5(U, n, r, ui);
-  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
   const double a_i = alpha[r];
   const double inv_mi = G.inv_mi[r];
   const double scale = tau * inv_mi * (double)(len - 1);
@@ -326,9 +387,6 @@ __global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, StageConfig C, cons
       pij[f] = P[f * ns + p];
       gP[f] = A.gP[f * ns + p];
     }
-    const double gl = A.gl4_own[p] + A.gl4_tr[G.tpos[p]];
-    const double l = l4[p];
-    if (gl != 0.0 && l > 0.0 && l < 1.0) limiter_vjp(ul, pij, rmin, rmax, pmin, gl, C.lim, gUL, gP, gb);
     double uj[kFields];
     load5(U, n, j, uj);
     const double m = G.mij[p];
@@ -354,14 +412,10 @@ __global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, StageConfig C, cons
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) {
-    A.gUL[f * n + r] = gUL[f];
     A.gR_own[f * n + r] = gRi[f];
     A.gU_own[f * n + r] += gUi[f];
   }
   A.ga_own[r] = galpha_i;
-  A.gbnd[r] += gb[0];
-  A.gbnd[n + r] += gb[1];
-  A.gbnd[2 * n + r] += gb[2];
   A.gtau_part[r] = gtau;
 }
 
@@ -756,10 +810,16 @@ int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const Adjo
   // traced intermediates: P and l of Step 4 (tP, tl4), the state and l
   // after the first pass (tU5, tl5), P' of the first pass (left in B.P)
   run(kKAdjFinal, [&] { ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A); });
-  run(kKAdjPass, [&] { ka_pass<<<grid, kB, 0, s>>>(G, C, B.tU5, B.tP, B.P, B.tl4, B.tl5, B.bnd, A); });
-  run(kKAdjFlux, [&] { ka_flux<<<grid, kB, 0, s>>>(G, C, Uin, B.UL, B.tP, B.tl4, B.d, B.alpha, B.bnd, A); });
+  run(kKAdjPass, [&] {
+    ka_pass_lim<<<grid, kB, 0, s>>>(G, C, B.tU5, B.P, B.tl5, B.bnd, A);
+    ka_pass<<<grid, kB, 0, s>>>(G, B.tP, B.tl4, A);
+  });
+  run(kKAdjFlux, [&] {
+    ka_flux_lim<<<grid, kB, 0, s>>>(G, C, B.UL, B.tP, B.tl4, B.bnd, A);
+    ka_flux<<<grid, kB, 0, s>>>(G, Uin, B.tP, B.d, B.alpha, A);
+  });
   run(kKAdjLow, [&] { ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.alpha, A); });
-  launches += 4;
+  launches += 6;
   run(kKAdjTau, [&] {
     ka_tau<<<1, kB, 0, s>>>(G, A, tau_computed ? 1 : 0);
     if (tau_computed) {
