@@ -255,9 +255,18 @@ __device__ __forceinline__ double limiter(const double* U, const double* P, doub
                                           const PsiCheck32* pre = nullptr) {
   double tL = 0.0, tR = 1.0;
   const double rhoU = U[0], rhoP = P[0];
-  if (rhoU + tR * rhoP > rho_max && rhoP != 0.0) tR = fabs(rho_max - rhoU) / fabs(rhoP);
-  if (rhoU + tR * rhoP < rho_min && rhoP != 0.0) tR = fabs(rho_min - rhoU) / fabs(rhoP);
-  tR = fmin(fmax(tR, 0.0), 1.0);
+  if ((__double_as_longlong(rhoP) << 1) != 0) {  // rho(P) != 0
+    bool cut = false;
+    if (rhoU + tR * rhoP > rho_max) {
+      tR = fabs(rho_max - rhoU) / fabs(rhoP);
+      cut = true;
+    }
+    if (rhoU + tR * rhoP < rho_min) {
+      tR = fabs(rho_min - rhoU) / fabs(rhoP);
+      cut = true;
+    }
+    if (cut) tR = fmin(fmax(tR, 0.0), 1.0);  // t_R = 1 needs no clamp
+  }
   if (pre && prm.newton_max > 0 && psi_accepts_fp32(*pre, P, tR)) return tR;
   // Psi and rho^(gamma+1) at the current t_L (t_L = 0 at the start)
   double psiL = 0.0, powL = 0.0;

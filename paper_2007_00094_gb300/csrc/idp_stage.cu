@@ -351,14 +351,25 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
       lnew[p] = 0.0;
       continue;
     }
-    const double lk = __longlong_as_double(min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]])));
+    const long long lkb = min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]]));
     double pij[kFields];
     bool zero = true;
+    if (lkb == 0x3ff0000000000000LL) {
+      // l = 1: (1 - l) P_ij is a zero with the sign of P_ij
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      pij[f] = (1.0 - lk) * P[f * ns + p];
-      P[f * ns + p] = pij[f];
-      zero &= (__double_as_longlong(pij[f]) << 1) == 0;  // +0 or -0
+      for (int f = 0; f < kFields; ++f) {
+        pij[f] = __longlong_as_double(__double_as_longlong(P[f * ns + p]) & (long long)0x8000000000000000ULL);
+        P[f * ns + p] = pij[f];
+      }
+    } else {
+      const double lk = __longlong_as_double(lkb);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        // l = 0 leaves P_ij as it is
+        pij[f] = lkb == 0 ? P[f * ns + p] : (1.0 - lk) * P[f * ns + p];
+        if (lkb != 0) P[f * ns + p] = pij[f];
+        zero &= (__double_as_longlong(pij[f]) << 1) == 0;  // +0 or -0
+      }
     }
     // A zero P_ij (the previous pass accepted it in full, so P_ji is zero
     // too) is moved by no value of l_ij: skip the limiter.
