@@ -71,6 +71,23 @@ struct Side {
   double rho, inv_rho, mx, my, mz, p, c, pm, inv_p;
 };
 
+// Comparisons of doubles on the integer pipe (the FP64 pipe, which also
+// executes FP64 compares and min/max, is the bottleneck of the FP64 stage).
+// dkey maps a double to a signed 64-bit key with the same order (the
+// magnitude bits of negative values reflected); ties keep the first operand.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double min_k(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
+__device__ __forceinline__ double max_k(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+// x > 0 and x < 0 from the bit pattern (+0 and -0 are neither)
+__device__ __forceinline__ bool positive_k(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool negative_k(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && (b << 1) != 0;
+}
+
 // f(U) . c of eq. (flux): (m.c, v (m.c) + p c, (E+p)/rho (m.c)), with an
 // operation sequence pinned by rounding intrinsics so that equal states give
 // bitwise equal fluxes (differences f_j - f_i then vanish exactly, as in the
@@ -108,11 +125,11 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
   const double uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
   double num = L.c + R.c - 0.2 * (uR - uL);
-  num = num > 0.0 ? num : 0.0;  // vacuum: p~* = 0
+  num = positive_k(num) ? num : 0.0;  // vacuum: p~* = 0
   const double x = num / (L.c * L.pm + R.c * R.pm);
   const double x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
   const double p_tr = x6 * x;
-  const bool left_high = L.p >= R.p;
+  const bool left_high = dkey(L.p) >= dkey(R.p);
   const double p_max = left_high ? L.p : R.p;
   const double p_low = left_high ? R.p : L.p;
   const double rho_low = left_high ? R.rho : L.rho;
@@ -122,14 +139,15 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   // division
   const double du = uR - uL;
   const double dp = p_max - p_low;
-  const bool psi_negative = du < 0.0 && 2.0 * dp * dp < du * du * (rho_low * (2.4 * p_max + 0.4 * p_low));
-  const double p_star = psi_negative ? p_tr : fmin(p_max, p_tr);
+  const bool psi_negative = negative_k(du) && 2.0 * dp * dp < du * du * (rho_low * (2.4 * p_max + 0.4 * p_low));
+  const double p_star = psi_negative ? p_tr : min_k(p_max, p_tr);
   const double k = 6.0 / 7.0;  // (gamma+1)/(2 gamma)
   // sqrt(1 + k [z]_+) is exactly 1 where z <= 0 (no shock on that side)
   const double zL = (p_star - L.p) * L.inv_p, zR = (p_star - R.p) * R.inv_p;
-  const double lam1 = uL - L.c * (zL > 0.0 ? sqrt(1.0 + k * zL) : 1.0);
-  const double lam3 = uR + R.c * (zR > 0.0 ? sqrt(1.0 + k * zR) : 1.0);
-  return fmax(fmax(-lam1, 0.0), fmax(lam3, 0.0));
+  const double lam1 = uL - L.c * (positive_k(zL) ? sqrt(1.0 + k * zL) : 1.0);
+  const double lam3 = uR + R.c * (positive_k(zR) ? sqrt(1.0 + k * zR) : 1.0);
+  const double a = negative_k(-lam1) ? 0.0 : -lam1, b = negative_k(lam3) ? 0.0 : lam3;
+  return max_k(a, b);
 }
 
 struct LimiterParams {

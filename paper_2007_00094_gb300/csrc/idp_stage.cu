@@ -237,10 +237,10 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
         ub[f] = 0.5 * (ui[f] + uj[f]) - df[f] * inv2d;
         ul[f] += coef * ub[f];
       }
-      rho_min = fmin(rho_min, ub[0]);
-      rho_max = fmax(rho_max, ub[0]);
+      rho_min = min_k(rho_min, ub[0]);
+      rho_max = max_k(rho_max, ub[0]);
     }
-    phi_min = fmin(phi_min, Q[kQPhi * n + j]);
+    phi_min = min_k(phi_min, Q[kQPhi * n + j]);
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) {
