@@ -275,11 +275,11 @@ __device__ __forceinline__ double limiter(const double* U, const double* P, doub
   const double rhoU = U[0], rhoP = P[0];
   if ((__double_as_longlong(rhoP) << 1) != 0) {  // rho(P) != 0
     bool cut = false;
-    if (rhoU + tR * rhoP > rho_max) {
+    if (dkey(rhoU + tR * rhoP) > dkey(rho_max)) {
       tR = fabs(rho_max - rhoU) / fabs(rhoP);
       cut = true;
     }
-    if (rhoU + tR * rhoP < rho_min) {
+    if (dkey(rhoU + tR * rhoP) < dkey(rho_min)) {
       tR = fabs(rho_min - rhoU) / fabs(rhoP);
       cut = true;
     }

@@ -228,7 +228,7 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
     const double dH = dij * (a_i + alpha[j]) * 0.5;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * (uj[f] - ui[f]);
-    if (dij != 0.0) {
+    if ((__double_as_longlong(dij) << 1) != 0) {  // d_ij != 0
       const double inv2d = dinv[p];
       const double coef = two_tau_m * dij;
       double ub[kFields];
@@ -402,7 +402,7 @@ __device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfi
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) continue;
-    const double lk = fmin(l[p], l[G.tpos[p]]);
+    const double lk = __longlong_as_double(min(__double_as_longlong(l[p]), __double_as_longlong(l[G.tpos[p]])));
     const double w = lam * lk;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
@@ -428,7 +428,7 @@ __device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfi
     if (blend == kBlendStage2) v = 0.75 * Un[f * n + r] + 0.25 * u[f];
     if (blend == kBlendStage3) v = (1.0 / 3.0) * Un[f * n + r] + (2.0 / 3.0) * u[f];
     out[f] = v;
-    finite &= isfinite(v);
+    finite &= (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;  // not inf/nan
   }
   if (!finite) atomicOr(&scal->status, kStatusNonFinite);
   if (skip_write_on_error && *(volatile int*)&scal->status != 0) return;
