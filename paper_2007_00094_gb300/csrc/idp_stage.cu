@@ -115,20 +115,20 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
     if (fl & kEntryUpper) {
       const double nc = G.cn[p];
       double dij = 0.0;
-      if (nc > 0.0) {
+      if (positive_k(nc)) {
         const double inv = G.inv_cn[p];
         dij = lambda_max(cx * inv, cy * inv, cz * inv, si, sj) * nc;
       }
       if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
         const int64_t pt = G.tpos[p];
         const double nt = G.cn[pt];
-        if (nt > 0.0) {
+        if (positive_k(nt)) {
           const double inv = G.inv_cn[pt];
           dij = fmax(dij, lambda_max(G.cx[pt] * inv, G.cy[pt] * inv, G.cz[pt] * inv, sj, si) * nt);
         }
       }
       d[p] = dij;
-      dinv[p] = dij != 0.0 ? 0.5 / dij : 0.0;
+      dinv[p] = (__double_as_longlong(dij) << 1) != 0 ? 0.5 / dij : 0.0;
     }
   }
   // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
@@ -137,7 +137,7 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
   const double num = a - (e0 * b0 + e1 * b1 + e2 * b2 + e3 * b3 + e4 * b4) + s_i * b0;
   const double D = fabs(a) + fabs(e0 - s_i) * fabs(b0) + fabs(e1) * fabs(b1) + fabs(e2) * fabs(b2) +
                    fabs(e3) * fabs(b3) + fabs(e4) * fabs(b4);
-  alpha[r] = D > 0.0 ? fabs(num) / D : 0.0;
+  alpha[r] = positive_k(D) ? fabs(num) / D : 0.0;
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
