@@ -29,13 +29,13 @@ template <int K>
 __device__ __forceinline__ double inv_root(double x) {
   double w0;
   {
-    const long long b = __double_as_longlong(x);
-    const int e = (int)(b >> 52) - 1023 + 127;
+    const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+    const int e = (int)(hi >> 20) - 1023 + 127;
     if (e > 0 && e < 255) {
-      const float xf = __int_as_float((e << 23) | (int)((b >> 29) & 0x7fffff));
-      const int wb = __float_as_int(powf(xf, -1.0f / (float)K));
-      w0 = __longlong_as_double(((long long)(((wb >> 23) & 0xff) - 127 + 1023) << 52) |
-                                ((long long)(wb & 0x7fffff) << 29));
+      const float xf = __uint_as_float(((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+      const unsigned int wb = __float_as_uint(powf(xf, -1.0f / (float)K));
+      const unsigned int we = ((wb >> 23) & 0xffu) - 127u + 1023u;
+      w0 = __hiloint2double((int)((we << 20) | ((wb & 0x7fffffu) >> 3)), (int)((wb & 7u) << 29));
     } else {
       w0 = (double)powf((float)x, -1.0f / (float)K);
     }
@@ -71,22 +71,33 @@ struct Side {
   double rho, inv_rho, mx, my, mz, p, c, pm, inv_p;
 };
 
-// Comparisons of doubles on the integer pipe (the FP64 pipe, which also
-// executes FP64 compares and min/max, is the bottleneck of the FP64 stage).
-// dkey maps a double to a signed 64-bit key with the same order (the
-// magnitude bits of negative values reflected); ties keep the first operand.
-__device__ __forceinline__ long long dkey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+// Comparisons of doubles on the integer pipe, from the two 32-bit words of
+// each value (the FP64 pipe, which executes FP64 compares and min/max and is
+// slow for 64-bit integer operations too, is the bottleneck of the FP64
+// stage).  dle(a, b) is a <= b in IEEE order without NaNs: the words of a
+// negative value are reflected so that the (signed high, unsigned low) pair
+// orders like the value; ties keep the first operand in min_k / max_k.
+__device__ __forceinline__ bool dzero(double x) {
+  return ((((unsigned int)__double2hiint(x)) << 1) | (unsigned int)__double2loint(x)) == 0u;
 }
-__device__ __forceinline__ double min_k(double a, double b) { return dkey(a) <= dkey(b) ? a : b; }
-__device__ __forceinline__ double max_k(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
-// x > 0 and x < 0 from the bit pattern (+0 and -0 are neither)
-__device__ __forceinline__ bool positive_k(double x) { return __double_as_longlong(x) > 0; }
-__device__ __forceinline__ bool negative_k(double x) {
-  const long long b = __double_as_longlong(x);
-  return b < 0 && (b << 1) != 0;
+__device__ __forceinline__ bool dle(double a, double b) {
+  int ha = __double2hiint(a), hb = __double2hiint(b);
+  unsigned int la = (unsigned int)__double2loint(a), lb = (unsigned int)__double2loint(b);
+  const int ma = ha >> 31, mb = hb >> 31;
+  ha ^= ma & 0x7fffffff;
+  la ^= (unsigned int)ma;
+  hb ^= mb & 0x7fffffff;
+  lb ^= (unsigned int)mb;
+  return ha < hb || (ha == hb && la <= lb);
 }
+__device__ __forceinline__ double min_k(double a, double b) { return dle(a, b) ? a : b; }
+__device__ __forceinline__ double max_k(double a, double b) { return dle(b, a) ? a : b; }
+// x > 0 and x < 0 (+0 and -0 are neither)
+__device__ __forceinline__ bool positive_k(double x) { return __double2hiint(x) >= 0 && !dzero(x); }
+__device__ __forceinline__ bool negative_k(double x) { return __double2hiint(x) < 0 && !dzero(x); }
+// exactly 1.0 and exactly +0
+__device__ __forceinline__ bool is_one(double x) { return __double2hiint(x) == 0x3ff00000 && __double2loint(x) == 0; }
+__device__ __forceinline__ bool is_pos_zero(double x) { return __double2hiint(x) == 0 && __double2loint(x) == 0; }
 
 // f(U) . c of eq. (flux): (m.c, v (m.c) + p c, (E+p)/rho (m.c)), with an
 // operation sequence pinned by rounding intrinsics so that equal states give
@@ -129,7 +140,7 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   const double x = num / (L.c * L.pm + R.c * R.pm);
   const double x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
   const double p_tr = x6 * x;
-  const bool left_high = dkey(L.p) >= dkey(R.p);
+  const bool left_high = dle(R.p, L.p);
   const double p_max = left_high ? L.p : R.p;
   const double p_low = left_high ? R.p : L.p;
   const double rho_low = left_high ? R.rho : L.rho;
@@ -179,9 +190,11 @@ __device__ __forceinline__ double drho_eps_at(const double* U, const double* P, 
 // |phi_min rho^(gamma+1)|) counts as admissible, a margin far above rounding
 // and far below the tolerance of the invariant checks.
 // (|x| by clearing the sign bit, on the integer pipe)
+__device__ __forceinline__ double dabs_k(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
 __device__ __forceinline__ double psi_slack(double rho_eps, double phi_term) {
-  return 1e-13 * (__longlong_as_double(__double_as_longlong(rho_eps) & 0x7fffffffffffffffLL) +
-                  __longlong_as_double(__double_as_longlong(phi_term) & 0x7fffffffffffffffLL));
+  return 1e-13 * (dabs_k(rho_eps) + dabs_k(phi_term));
 }
 
 // Double to float rounded toward zero by bit arithmetic (integer pipe): the
@@ -189,12 +202,11 @@ __device__ __forceinline__ double psi_slack(double rho_eps, double phi_term) {
 // below 2^-23.  Zero maps to zero; doubles outside the normal float range
 // take the conversion instruction.
 __device__ __forceinline__ float to_float_rz(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hi = (unsigned int)(b >> 32);
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
   if (e > 0 && e < 255)
-    return __uint_as_float((hi & 0x80000000u) | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7fffffu));
-  if ((b << 1) == 0ull) return 0.0f;
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  if (((hi << 1) | lo) == 0u) return 0.0f;
   return __double2float_rz(x);
 }
 
@@ -273,13 +285,13 @@ __device__ __forceinline__ double limiter(const double* U, const double* P, doub
                                           const PsiCheck32* pre = nullptr) {
   double tL = 0.0, tR = 1.0;
   const double rhoU = U[0], rhoP = P[0];
-  if ((__double_as_longlong(rhoP) << 1) != 0) {  // rho(P) != 0
+  if (!dzero(rhoP)) {  // rho(P) != 0
     bool cut = false;
-    if (dkey(rhoU + tR * rhoP) > dkey(rho_max)) {
+    if (!dle(rhoU + tR * rhoP, rho_max)) {
       tR = fabs(rho_max - rhoU) / fabs(rhoP);
       cut = true;
     }
-    if (dkey(rhoU + tR * rhoP) < dkey(rho_min)) {
+    if (!dle(rho_min, rhoU + tR * rhoP)) {
       tR = fabs(rho_min - rhoU) / fabs(rhoP);
       cut = true;
     }

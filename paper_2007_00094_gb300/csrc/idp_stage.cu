@@ -128,7 +128,7 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
         }
       }
       d[p] = dij;
-      dinv[p] = (__double_as_longlong(dij) << 1) != 0 ? 0.5 / dij : 0.0;
+      dinv[p] = !dzero(dij) ? 0.5 / dij : 0.0;
     }
   }
   // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
@@ -228,7 +228,7 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
     const double dH = dij * (a_i + alpha[j]) * 0.5;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * (uj[f] - ui[f]);
-    if ((__double_as_longlong(dij) << 1) != 0) {  // d_ij != 0
+    if (!dzero(dij)) {
       const double inv2d = dinv[p];
       const double coef = two_tau_m * dij;
       double ub[kFields];
@@ -336,7 +336,8 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) continue;
     // min of two limiter values in [0, 1] on their bit patterns (integer pipe)
-    const double lk = __longlong_as_double(min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]])));
+    const double la = lold[p], lb = lold[G.tpos[p]];
+    const double lk = min_k(la, lb);
     const double w = lam * lk;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
@@ -351,24 +352,24 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
       lnew[p] = 0.0;
       continue;
     }
-    const long long lkb = min(__double_as_longlong(lold[p]), __double_as_longlong(lold[G.tpos[p]]));
+    const double lk = min_k(lold[p], lold[G.tpos[p]]);
     double pij[kFields];
     bool zero = true;
-    if (lkb == 0x3ff0000000000000LL) {
+    if (is_one(lk)) {
       // l = 1: (1 - l) P_ij is a zero with the sign of P_ij
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        pij[f] = __longlong_as_double(__double_as_longlong(P[f * ns + p]) & (long long)0x8000000000000000ULL);
+        pij[f] = __hiloint2double(__double2hiint(P[f * ns + p]) & (int)0x80000000, 0);
         P[f * ns + p] = pij[f];
       }
     } else {
-      const double lk = __longlong_as_double(lkb);
+      const bool keep = is_pos_zero(lk);
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
         // l = 0 leaves P_ij as it is
-        pij[f] = lkb == 0 ? P[f * ns + p] : (1.0 - lk) * P[f * ns + p];
-        if (lkb != 0) P[f * ns + p] = pij[f];
-        zero &= (__double_as_longlong(pij[f]) << 1) == 0;  // +0 or -0
+        pij[f] = keep ? P[f * ns + p] : (1.0 - lk) * P[f * ns + p];
+        if (!keep) P[f * ns + p] = pij[f];
+        zero &= ((((unsigned int)__double2hiint(pij[f])) << 1) | (unsigned int)__double2loint(pij[f])) == 0u;
       }
     }
     // A zero P_ij (the previous pass accepted it in full, so P_ji is zero
@@ -402,7 +403,7 @@ __device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfi
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] == r) continue;
-    const double lk = __longlong_as_double(min(__double_as_longlong(l[p]), __double_as_longlong(l[G.tpos[p]])));
+    const double lk = min_k(l[p], l[G.tpos[p]]);
     const double w = lam * lk;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
@@ -428,7 +429,7 @@ __device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfi
     if (blend == kBlendStage2) v = 0.75 * Un[f * n + r] + 0.25 * u[f];
     if (blend == kBlendStage3) v = (1.0 / 3.0) * Un[f * n + r] + (2.0 / 3.0) * u[f];
     out[f] = v;
-    finite &= (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;  // not inf/nan
+    finite &= (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;  // not inf/nan
   }
   if (!finite) atomicOr(&scal->status, kStatusNonFinite);
   if (skip_write_on_error && *(volatile int*)&scal->status != 0) return;
