@@ -59,6 +59,10 @@ typedef struct {
                                accumulation, mass division, tau and the final limiter check in FP64 */
   int schedule;             /* kernel schedule id; 0 = default */
   int64_t barrier_spin_limit; /* iteration limit of any device-side wait */
+  int relax;                /* != 0: relax the local bounds, rho_min (1 - r_i), rho_max (1 + r_i),
+                               phi_min (1 - r_i) with r_i = (m_i / |Omega|)^(1/2), |Omega| the volume of
+                               the node's instance (Sec. 3.9 remark; the formula is project-defined);
+                               0 (default): the bounds as Alg. 1 states them */
 } idp_config;
 
 /* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,

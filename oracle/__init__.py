@@ -31,7 +31,7 @@ _i32p = C.POINTER(C.c_int32)
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter_passes", C.c_int),
                 ("newton_max", C.c_int), ("newton_tol", C.c_double), ("newton_eps", C.c_double),
-                ("n_threads", C.c_int)]
+                ("n_threads", C.c_int), ("relax", C.c_int)]
 
 
 def default_params(**kw) -> Params:
@@ -39,7 +39,7 @@ def default_params(**kw) -> Params:
     two Newton steps and tolerance 1e-10 (Reading A11), eps = DBL_EPSILON
     (Reading A5)."""
     p = Params(gamma=1.4, cfl=0.5, limiter_passes=2, newton_max=2, newton_tol=1e-10,
-               newton_eps=float(np.finfo(np.float64).eps), n_threads=1)
+               newton_eps=float(np.finfo(np.float64).eps), n_threads=1, relax=0)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

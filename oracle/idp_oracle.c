@@ -514,6 +514,12 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
   }
   const double dt = *tau;
 
+  /* Bound relaxation (Reading A14, project-defined; the paper leaves the
+   * formula to the literature): r_i = (m_i / |Omega|)^(1/2), |Omega| = sum_i m_i. */
+  double volume = 0.0;
+  if (prm->relax)
+    for (int64_t i = 0; i < n; ++i) volume += M->mi[i];
+
   /* Step 3: low-order update via bar states (Sec. 3.3 eq. def-ubar, Reading
    * A1), R_i (eq. high-order-final) and the local bounds (Sec. 3.9). */
 #pragma omp parallel for num_threads(nt) schedule(static)
@@ -545,6 +551,12 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
       }
       const double phj = specific_entropy(uj, gamma); /* j ranges over I(i), i included (Reading A13) */
       if (phj < phi_min) phi_min = phj;
+    }
+    if (prm->relax) {
+      const double ri = sqrt(M->mi[i] / volume);
+      rho_min *= 1.0 - ri;
+      rho_max *= 1.0 + ri;
+      phi_min *= 1.0 - ri;
     }
     store(UL, n, i, ul);
     store(R, n, i, r);

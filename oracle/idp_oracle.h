@@ -28,6 +28,7 @@ typedef struct {
   double newton_tol;  /* Alg. 2 stops once Psi(t_L) <= newton_tol * rho*eps(U) */
   double newton_eps;  /* eps of Alg. 3 */
   int n_threads;      /* OpenMP threads over rows (results do not depend on it) */
+  int relax;          /* != 0: relax the local bounds (Sec. 3.9 remark; Reading A14) */
 } orc_params;
 
 typedef struct {

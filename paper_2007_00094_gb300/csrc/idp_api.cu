@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -162,6 +163,26 @@ idp_status device_status(idp_ctx* ctx, bool clear) {
   return IDP_OK;
 }
 
+// Per-row bound relaxation r_i = (m_i / |Omega_k|)^(1/2), |Omega_k| the sum of
+// m_i over the row's instance k (inst: instance per row, empty for one).
+idp_status upload_relax(idp_ctx* ctx, const std::vector<int32_t>& inst) {
+  const idp::SellLayout& L = ctx->L;
+  const int64_t n = L.n;
+  int64_t n_inst = 1;
+  for (int32_t k : inst) n_inst = k + 1 > n_inst ? k + 1 : n_inst;
+  std::vector<double> vol((size_t)n_inst, 0.0), r((size_t)n);
+  for (int64_t i = 0; i < n; ++i) vol[inst.empty() ? 0 : inst[i]] += L.mi[i];
+  for (int64_t i = 0; i < n; ++i) r[i] = std::sqrt(L.mi[i] / vol[inst.empty() ? 0 : inst[i]]);
+  if (!ctx->G.relax) {
+    double* p = nullptr;
+    idp_status st = dalloc(ctx, &p, (size_t)n);
+    if (st != IDP_OK) return st;
+    ctx->G.relax = p;
+  }
+  IDP_CUDA(ctx, cudaMemcpy(const_cast<double*>(ctx->G.relax), r.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  return IDP_OK;
+}
+
 // Trace copies of the stage intermediates (allocated on first traced stage).
 idp_status ensure_trace(idp_ctx* ctx) {
   if (ctx->has_trace) return IDP_OK;
@@ -181,6 +202,7 @@ idp_status adjoint_supported(idp_ctx* ctx) {
   if (ctx->mixed) return fail(ctx, IDP_ERR_ARG, "the adjoint needs the FP64 precision mode");
   if (ctx->C.limiter_passes != 2) return fail(ctx, IDP_ERR_ARG, "the adjoint needs limiter_passes = 2");
   if (ctx->G.n_inst != 1) return fail(ctx, IDP_ERR_ARG, "the adjoint needs a single instance");
+  if (ctx->cfg.relax) return fail(ctx, IDP_ERR_ARG, "the adjoint does not cover the bound relaxation");
   return IDP_OK;
 }
 
@@ -376,6 +398,8 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   G.inv_mi = inv_mi;
   G.lam = lam;
   G.bc = bc;
+  G.relax = nullptr;
+  if (ctx->cfg.relax && (st = upload_relax(ctx, std::vector<int32_t>()))) return st;
 
   idp::StageBuffers& B = ctx->B;
   const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
@@ -574,6 +598,10 @@ idp_status idp_set_instances(idp_ctx* ctx, int64_t n_instances, const int64_t* n
   std::vector<int32_t> of_row(n);
   for (int64_t i = 0; i < n; ++i) of_row[ctx->L.perm[i]] = of_node[i];
   IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->cfg.relax) {
+    idp_status st = upload_relax(ctx, of_row);
+    if (st != IDP_OK) return st;
+  }
   return alloc_instances(ctx, n_instances, of_row);
 }
 

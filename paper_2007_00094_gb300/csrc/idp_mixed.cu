@@ -450,9 +450,16 @@ __device__ __forceinline__ void row_low_order_m(const DeviceGraph& G, const Stag
     UL[f * n + r] = U[f * n + r] + (double)inc[f];
     R[f * n + r] = rr[f];
   }
-  bnd[r] = rho_i + (double)dmin;
-  bnd[n + r] = rho_i + (double)dmax;
-  bnd[2 * n + r] = (double)phi_min;
+  double bmin = rho_i + (double)dmin, bmax = rho_i + (double)dmax, pmin = (double)phi_min;
+  if (G.relax) {  // bound relaxation (off unless configured)
+    const double q = G.relax[r];
+    bmin *= 1.0 - q;
+    bmax *= 1.0 + q;
+    pmin *= 1.0 - q;
+  }
+  bnd[r] = bmin;
+  bnd[n + r] = bmax;
+  bnd[2 * n + r] = pmin;
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageConfig C, const double* __restrict__ U,

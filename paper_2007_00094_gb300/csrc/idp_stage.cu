@@ -247,6 +247,12 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
     UL[f * n + r] = ul[f];
     R[f * n + r] = rr[f];
   }
+  if (G.relax) {  // bound relaxation (off unless configured)
+    const double q = G.relax[r];
+    rho_min *= 1.0 - q;
+    rho_max *= 1.0 + q;
+    phi_min *= 1.0 - q;
+  }
   bnd[r] = rho_min;
   bnd[n + r] = rho_max;
   bnd[2 * n + r] = phi_min;

@@ -32,6 +32,7 @@ struct DeviceGraph {
   const double* inv_mi;
   const double* lam;
   const int32_t* bc;
+  const double* relax;  // per-row bound relaxation r_i, or nullptr (off)
   // Independent instances (node ranges without entries between them): each
   // has its own tau_n and time.  inst[r] is the instance of row r (nullptr:
   // one instance).  The per-instance arrays below are device state written

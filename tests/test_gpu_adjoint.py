@@ -226,6 +226,9 @@ def test_adjoint_rejects_unsupported_configurations():
         _solver(mesh, limiter_passes=3).adjoint_euler_step(U, w)
     assert e.value.status == 1
     with pytest.raises(IdpError) as e:
+        _solver(mesh, relax=1).adjoint_euler_step(U, w)
+    assert e.value.status == 1
+    with pytest.raises(IdpError) as e:
         s.adjoint_record(0)
     assert e.value.status == 1
 

@@ -137,3 +137,22 @@ def test_instances_must_not_share_entries(batch):
     with pytest.raises(IdpError) as e:
         s.set_instances(bad)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_with_relaxed_bounds_equals_instances_alone(batch, precision):
+    """With bound relaxation r_i = (m_i / |Omega_k|)^(1/2) each instance uses
+    its own volume |Omega_k|: the batch equals each instance alone, bitwise."""
+    parts, mesh, off, U = batch
+    s = _solver(mesh, precision=precision, relax=1)
+    s.set_instances(off)
+    s.init_state(U)
+    s.step(2)
+    s.synchronize()
+    out = s.get_state()
+    for k, (m, u) in enumerate(parts):
+        a = _solver(m, precision=precision, relax=1)
+        a.init_state(u)
+        a.step(2)
+        a.synchronize()
+        np.testing.assert_array_equal(out[:, off[k]:off[k + 1]], a.get_state())

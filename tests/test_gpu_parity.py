@@ -234,3 +234,27 @@ def test_torch_device_buffers():
     s2.init_state(U)
     s2.step(2)
     np.testing.assert_array_equal(out.cpu().numpy(), s2.get_state())
+
+
+@pytest.mark.parametrize("name", ["wallbox_jitter", "sod_jitter", "vortex17"])
+def test_relaxed_bounds_parity(name, n_threads):
+    """Bound relaxation (idp_config.relax, Reading A14) against the oracle with
+    the same option: the relaxed bounds, one euler_step and one SSP-RK3 step."""
+    mesh, U = _mesh(name)
+    om = O.assemble(mesh)
+    prm = O.default_params(n_threads=n_threads, relax=1)
+    ref, tau_ref, st, tr = O.euler_step(om, U, params=prm, trace=True)
+    assert st == 0
+    s = _solver(mesh, relax=1)
+    s.init_state(U)
+    tau = s.euler_step(trace=True)
+    assert abs(tau - tau_ref) <= 1e-14 * tau_ref
+    b = s.field("bounds")
+    assert np.abs(b - tr["bounds"]).max() <= 1e-13 * np.abs(tr["bounds"]).max()
+    out = s.get_state()
+    assert rel_field_err_l2(out, ref).max() <= 1e-12
+    ref3, _, st = O.ssprk3_step(om, U, prm)
+    s.init_state(U)
+    s.step(1)
+    s.synchronize()
+    assert rel_field_err_l2(s.get_state(), ref3).max() <= 1e-12
