@@ -247,6 +247,33 @@ def pattern_adjoint(stream, args):
                          "max_rel_err": {f"{e:.0e}": (max(v) if v else None) for e, v in fd_err.items()}}}
 
 
+def pattern_relaxation(stream, args):
+    """Accuracy of the bound relaxation (idp_config.relax): L1 density error
+    of the isentropic vortex against its exact translation at t >= 0.05 on
+    periodic n x n x 3 meshes, FP64, with and without relaxation, and the
+    observed orders."""
+    import numpy as np
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+
+    out = {"config": {"workload": "isentropic_vortex_periodic_n_x_n_x_3_t0.05", "n": [40, 80, 160]}}
+    for relax in (0, 1):
+        errs = []
+        for n in out["config"]["n"]:
+            mesh = W.box_mesh((n, n, 3), periodic=(True, True, True))
+            s = Solver(mesh, stream=stream, relax=relax)
+            s.init_state(W.vortex_state(mesh))
+            while s.time()[0] < 0.05:
+                s.step(1)
+            t = s.time()[0]
+            errs.append(float(np.abs(s.get_state()[0] - W.vortex_state(mesh, t=t)[0]).mean()))
+            s.close()
+        out["relaxed" if relax else "plain"] = {
+            "l1_density_error": errs, "orders": [float(np.log2(errs[k] / errs[k + 1])) for k in range(len(errs) - 1)]}
+    return out
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -404,7 +431,7 @@ def main():
     ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
     ap.add_argument("--adj-steps", type=int, default=100)
     ap.add_argument("--adj-fd-directions", type=int, default=2)
-    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint"],
+    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -427,7 +454,8 @@ def main():
     torch.cuda.set_device(local)
     if args.only:
         build.build()
-        run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint}[args.only]
+        run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
+               "relaxation": pattern_relaxation}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return
     dist = None
@@ -529,7 +557,8 @@ def main():
         }
         if not args.no_patterns:
             line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
-                                "adjoint": pattern_adjoint(stream, args)}
+                                "adjoint": pattern_adjoint(stream, args),
+                                "relaxation": pattern_relaxation(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)
