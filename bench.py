@@ -274,6 +274,19 @@ def pattern_relaxation(stream, args):
     return out
 
 
+def job_rate(local_ms, units_per_rank, dist=None, device="cpu"):
+    """Whole-job rate of a weak-scaling run: the slowest rank's time (max over
+    ranks) and all ranks' units divided by it.  Returns (ms_max, units/s)."""
+    import torch
+
+    ws = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, ws * units_per_rank / (ms_max * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -503,11 +516,7 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = s.profile_read()
     s.profile(False)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = ws * N * 3 * args.steps / (ms_max * 1e-3)
+    ms_max, value = job_rate(ms, N * 3 * args.steps, dist, device="cuda")
     launches = sum(c for _, c in prof.values())
 
     # end-to-end through the public API with host buffers: every step copies
@@ -527,10 +536,7 @@ def main():
         host_in, host_out = host_out, host_in
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * N * 3 * args.e2e_steps / float(e2e_t.item())
+    _, e2e_value = job_rate(e2e_s * 1e3, N * 3 * args.e2e_steps, dist, device="cuda")
     state_bytes = 5 * N * 8
 
     if rank == 0:
