@@ -274,6 +274,50 @@ def pattern_relaxation(stream, args):
     return out
 
 
+def pattern_q1_2d(stream, args):
+    """2D Q1 variant (quadrilaterals, 9-point stencil): the Mach 3 forward-facing
+    step [0,3]x[0,1] with h = 1/m2d, jittered interior, FP64 and FP32-mixed."""
+    import numpy as np
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+
+    mesh = W.forward_step_mesh_2d(m=args.m2d, jitter=0.2, seed=2007)
+    U0 = W.forward_step_state(mesh)
+    out = {"config": {"workload": f"mach3_forward_facing_step_2d_h1/{args.m2d}_jitter0.2_seed2007",
+                      "nodes": mesh.n_nodes, "stencil": "Q1 9-point", "steps_timed": args.pattern_steps,
+                      "warmup": args.warmup}}
+    peak_hbm, src = _hbm_peak()
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+        s = Solver(mesh, stream=stream, precision=prec)
+        s.init_state(U0)
+        ms, prof = _time_steps(s, stream, args.pattern_steps, args.warmup)
+        out["config"]["nnz"] = s.nnz
+        dom = max(prof, key=lambda k: prof[k][0])
+        dom_ms, dom_n = prof[dom]
+        per_launch_s = dom_ms / dom_n * 1e-3
+        if prec == 0:
+            achieved = FLOP_PER_NNZ[dom] * s.nnz / per_launch_s / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "work": f"{FLOP_PER_NNZ[dom]:.0f} flop/nnz x {s.nnz} nnz per launch"}
+        else:
+            per_slot, per_node = MIXED_BYTES[dom]
+            achieved = (per_slot * s.nnz + per_node * mesh.n_nodes) / per_launch_s / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": achieved / peak_hbm, "traffic": None, "peak_source": src,
+                    "work": f"{per_slot} B/entry x {s.nnz} + {per_node} B/node x {mesh.n_nodes}"}
+        U = s.get_state()
+        st, rep = s.check_bounds()
+        out[name] = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
+                     "roofline": roof, "m_z_max_abs": float(np.abs(U[3]).max()),
+                     "invariants": {"status": st, "rho_min": rep.rho_min, "eps_min": rep.eps_min}}
+        s.close()
+    out["fp32_mixed"]["speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32_mixed"]["ms_per_step"]
+    return out
+
+
 def job_rate(local_ms, units_per_rank, dist=None, device="cpu"):
     """Whole-job rate of a weak-scaling run: the slowest rank's time (max over
     ranks) and all ranks' units divided by it.  Returns (ms_max, units/s)."""
@@ -444,7 +488,8 @@ def main():
     ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
     ap.add_argument("--adj-steps", type=int, default=100)
     ap.add_argument("--adj-fd-directions", type=int, default=2)
-    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation"],
+    ap.add_argument("--m2d", type=int, default=1000, help="cells per unit length of the 2D channel mesh")
+    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation", "q1_2d"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -468,7 +513,7 @@ def main():
     if args.only:
         build.build()
         run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
-               "relaxation": pattern_relaxation}[args.only]
+               "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return
     dist = None
@@ -564,7 +609,7 @@ def main():
         if not args.no_patterns:
             line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
                                 "adjoint": pattern_adjoint(stream, args),
-                                "relaxation": pattern_relaxation(stream, args)}
+                                "relaxation": pattern_relaxation(stream, args), "q1_2d": pattern_q1_2d(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)

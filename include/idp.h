@@ -93,6 +93,14 @@ const char* idp_status_string(idp_status s);
  * Set-up work runs on the host and is not part of a stage. */
 idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
                                const double* cell_xyz, const int32_t* node_bc, const double* inflow_state);
+/* The same for a 2D mesh of Q1 quadrilaterals (Sec. 3.1 with d = 2, 9-point
+ * stencil): cells holds 4 node ids per cell (local vertex v = a + 2b for the
+ * reference corner (a, b)), cell_xy 2 coordinates per vertex (unwrapped on
+ * periodic axes), node_bc as for hexahedra (IDP_BC_SLIP_Z unused).  The state
+ * keeps 5 fields (rho, m_x, m_y, m_z, E): c_ij has no z component, so an
+ * initial m_z = 0 stays exactly 0 and the update is the 2D one. */
+idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                                const double* cell_xy, const int32_t* node_bc, const double* inflow_state);
 
 /* Number of nodes and of stored matrix entries (the stencil sizes I(i) of
  * Sec. 3.1 summed over i). */

@@ -76,6 +76,10 @@ def lib():
         L.orc_sparsity.argtypes = [C.c_int64, C.c_int64, _i64p, _i64p, _i64p]
         L.orc_assemble.restype = C.c_int
         L.orc_assemble.argtypes = [C.c_int64, C.c_int64, _i64p, _dp, _i64p, _i64p, _dp, _dp, _dp]
+        L.orc_sparsity_nv.restype = C.c_int64
+        L.orc_sparsity_nv.argtypes = [C.c_int64, C.c_int64, C.c_int, _i64p, _i64p, _i64p]
+        L.orc_assemble_quad.restype = C.c_int
+        L.orc_assemble_quad.argtypes = [C.c_int64, C.c_int64, _i64p, _dp, _i64p, _i64p, _dp, _dp, _dp]
         L.orc_node_quantities.restype = None
         L.orc_node_quantities.argtypes = [_dp, C.c_double, _dp]
         L.orc_lambda_max.restype = C.c_double
@@ -122,20 +126,27 @@ class OracleMesh:
 
 
 def assemble(mesh) -> OracleMesh:
-    """Q1 matrices of Sec. 3.1 eq. (matrices) for ``mesh`` (a workloads.HexMesh)."""
+    """Q1 matrices of Sec. 3.1 eq. (matrices) for ``mesh`` (a workloads.HexMesh of
+    hexahedra, or of quadrilaterals when its cells have 4 vertices)."""
     L = lib()
     cells = np.ascontiguousarray(mesh.cells, dtype=np.int64)
-    xyz = np.ascontiguousarray(mesh.cell_xyz, dtype=np.float64)
+    nv = cells.shape[1]
+    if nv == 4:
+        xyz = np.ascontiguousarray(mesh.cell_xyz[:, :, :2], dtype=np.float64)
+        assemble_fn = L.orc_assemble_quad
+    else:
+        xyz = np.ascontiguousarray(mesh.cell_xyz, dtype=np.float64)
+        assemble_fn = L.orc_assemble
     n = mesh.n_nodes
     rowptr = np.zeros(n + 1, dtype=np.int64)
-    nnz = L.orc_sparsity(n, cells.shape[0], _p(cells, _i64p), _p(rowptr, _i64p), None)
+    nnz = L.orc_sparsity_nv(n, cells.shape[0], nv, _p(cells, _i64p), _p(rowptr, _i64p), None)
     col = np.zeros(nnz, dtype=np.int64)
-    L.orc_sparsity(n, cells.shape[0], _p(cells, _i64p), _p(rowptr, _i64p), _p(col, _i64p))
+    L.orc_sparsity_nv(n, cells.shape[0], nv, _p(cells, _i64p), _p(rowptr, _i64p), _p(col, _i64p))
     mij = np.zeros(nnz)
     cij = np.zeros((3, nnz))
     mi = np.zeros(n)
-    st = L.orc_assemble(n, cells.shape[0], _p(cells, _i64p), _p(xyz), _p(rowptr, _i64p), _p(col, _i64p),
-                        _p(mij), _p(cij), _p(mi))
+    st = assemble_fn(n, cells.shape[0], _p(cells, _i64p), _p(xyz), _p(rowptr, _i64p), _p(col, _i64p),
+                     _p(mij), _p(cij), _p(mi))
     if st != 0:
         raise ValueError("oracle assembly failed (inverted cell?)")
     inflow = np.zeros(5) if mesh.inflow is None else np.ascontiguousarray(mesh.inflow, dtype=np.float64)

@@ -38,18 +38,20 @@ static int cmp_i64(const void* a, const void* b) {
 }
 
 /* Stencil I(i) = { j : supp(phi_i) and supp(phi_j) overlap } (Sec. 3.1): all
- * nodes of all cells that contain node i.  With col == NULL only the row
- * pointer is filled; returns nnz. */
-int64_t orc_sparsity(int64_t n_nodes, int64_t n_cells, const int64_t* cells, int64_t* rowptr, int64_t* col) {
+ * nodes of all cells that contain node i, for cells of nv vertices (8 for
+ * hexahedra, 4 for quadrilaterals).  With col == NULL only the row pointer is
+ * filled; returns nnz. */
+int64_t orc_sparsity_nv(int64_t n_nodes, int64_t n_cells, int nv, const int64_t* cells, int64_t* rowptr,
+                        int64_t* col) {
   int64_t* cnt = (int64_t*)calloc((size_t)n_nodes + 1, sizeof(int64_t));
   for (int64_t c = 0; c < n_cells; ++c)
-    for (int v = 0; v < 8; ++v) cnt[cells[8 * c + v] + 1]++;
+    for (int v = 0; v < nv; ++v) cnt[cells[nv * c + v] + 1]++;
   for (int64_t i = 0; i < n_nodes; ++i) cnt[i + 1] += cnt[i];
   int64_t* inc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cnt[n_nodes] + 1));
   int64_t* fill = (int64_t*)calloc((size_t)n_nodes, sizeof(int64_t));
   for (int64_t c = 0; c < n_cells; ++c)
-    for (int v = 0; v < 8; ++v) {
-      int64_t i = cells[8 * c + v];
+    for (int v = 0; v < nv; ++v) {
+      int64_t i = cells[nv * c + v];
       inc[cnt[i] + fill[i]++] = c;
     }
   int64_t nnz = 0;
@@ -57,8 +59,8 @@ int64_t orc_sparsity(int64_t n_nodes, int64_t n_cells, const int64_t* cells, int
   rowptr[0] = 0;
   for (int64_t i = 0; i < n_nodes; ++i) {
     int64_t m = 0;
-    for (int64_t q = cnt[i]; q < cnt[i + 1] && m + 8 <= 8 * 64; ++q)
-      for (int v = 0; v < 8; ++v) buf[m++] = cells[8 * inc[q] + v];
+    for (int64_t q = cnt[i]; q < cnt[i + 1] && m + nv <= 8 * 64; ++q)
+      for (int v = 0; v < nv; ++v) buf[m++] = cells[nv * inc[q] + v];
     qsort(buf, (size_t)m, sizeof(int64_t), cmp_i64);
     int64_t u = 0;
     for (int64_t q = 0; q < m; ++q)
@@ -73,6 +75,10 @@ int64_t orc_sparsity(int64_t n_nodes, int64_t n_cells, const int64_t* cells, int
   free(inc);
   free(fill);
   return nnz;
+}
+
+int64_t orc_sparsity(int64_t n_nodes, int64_t n_cells, const int64_t* cells, int64_t* rowptr, int64_t* col) {
+  return orc_sparsity_nv(n_nodes, n_cells, 8, cells, rowptr, col);
 }
 
 static int64_t find_col(const int64_t* rowptr, const int64_t* col, int64_t i, int64_t j) {
@@ -162,6 +168,73 @@ int orc_assemble(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const d
         if (k < 0) return ORC_ERR_ARG;
         mij[k] += Mloc[a][b];
         for (int r = 0; r < 3; ++r) cij[r * nnz + k] += Cloc[a][b][r];
+      }
+    }
+  }
+  return ORC_OK;
+}
+
+/* The same matrices for d = 2 (Sec. 3.1 with Q1 quadrilaterals): 3x3 Gauss
+ * points on the bilinear map of each quadrilateral, local vertex v = a + 2b at
+ * reference corner (a,b), two coordinates per vertex in cell_xy.  c_ij keeps
+ * three rows with the z row zero, so the stage is the 3D one with m_z = 0. */
+int orc_assemble_quad(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const double* cell_xy,
+                      const int64_t* rowptr, const int64_t* col, double* mij, double* cij, double* mi) {
+  const int64_t nnz = rowptr[n_nodes];
+  memset(mij, 0, sizeof(double) * (size_t)nnz);
+  memset(cij, 0, sizeof(double) * 3 * (size_t)nnz);
+  memset(mi, 0, sizeof(double) * (size_t)n_nodes);
+  const double g[3] = {0.5 - 0.5 * sqrt(0.6), 0.5, 0.5 + 0.5 * sqrt(0.6)};
+  const double w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  for (int64_t c = 0; c < n_cells; ++c) {
+    const double* X = cell_xy + 8 * c;
+    double Mloc[4][4], Cloc[4][4][2], mloc[4];
+    memset(Mloc, 0, sizeof Mloc);
+    memset(Cloc, 0, sizeof Cloc);
+    memset(mloc, 0, sizeof mloc);
+    for (int qx = 0; qx < 3; ++qx)
+      for (int qy = 0; qy < 3; ++qy) {
+        const double xi[2] = {g[qx], g[qy]};
+        const double wq = w[qx] * w[qy];
+        double phi[4], dphi[4][2];
+        for (int v = 0; v < 4; ++v) {
+          const double fx = (v & 1) ? xi[0] : 1.0 - xi[0];
+          const double fy = (v & 2) ? xi[1] : 1.0 - xi[1];
+          const double dfx = (v & 1) ? 1.0 : -1.0;
+          const double dfy = (v & 2) ? 1.0 : -1.0;
+          phi[v] = fx * fy;
+          dphi[v][0] = dfx * fy;
+          dphi[v][1] = fx * dfy;
+        }
+        /* J[r][s] = d x_r / d xi_s */
+        double J[2][2] = {{0}};
+        for (int v = 0; v < 4; ++v)
+          for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s) J[r][s] += X[2 * v + r] * dphi[v][s];
+        const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        if (!(det > 0.0)) return ORC_ERR_ARG;
+        /* Jinv[s][r] = d xi_s / d x_r */
+        const double Jinv[2][2] = {{J[1][1] / det, -J[0][1] / det}, {-J[1][0] / det, J[0][0] / det}};
+        double grad[4][2];
+        for (int v = 0; v < 4; ++v)
+          for (int r = 0; r < 2; ++r) grad[v][r] = dphi[v][0] * Jinv[0][r] + dphi[v][1] * Jinv[1][r];
+        const double dx = wq * det;
+        for (int a = 0; a < 4; ++a) {
+          mloc[a] += phi[a] * dx;
+          for (int b = 0; b < 4; ++b) {
+            Mloc[a][b] += phi[a] * phi[b] * dx;
+            for (int r = 0; r < 2; ++r) Cloc[a][b][r] += phi[a] * grad[b][r] * dx;
+          }
+        }
+      }
+    for (int a = 0; a < 4; ++a) {
+      int64_t i = cells[4 * c + a];
+      mi[i] += mloc[a];
+      for (int b = 0; b < 4; ++b) {
+        int64_t k = find_col(rowptr, col, i, cells[4 * c + b]);
+        if (k < 0) return ORC_ERR_ARG;
+        mij[k] += Mloc[a][b];
+        for (int r = 0; r < 2; ++r) cij[r * nnz + k] += Cloc[a][b][r];
       }
     }
   }

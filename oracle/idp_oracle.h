@@ -63,6 +63,11 @@ enum { ORC_OK = 0, ORC_ERR_CFL = 1, ORC_ERR_STATE = 2, ORC_ERR_ARG = 3 };
 int64_t orc_sparsity(int64_t n_nodes, int64_t n_cells, const int64_t* cells, int64_t* rowptr, int64_t* col);
 int orc_assemble(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const double* cell_xyz,
                  const int64_t* rowptr, const int64_t* col, double* mij, double* cij, double* mi);
+/* d = 2: Q1 quadrilaterals, 4 vertices and 2 coordinates per vertex; c_ij z row zero */
+int64_t orc_sparsity_nv(int64_t n_nodes, int64_t n_cells, int nv, const int64_t* cells, int64_t* rowptr,
+                        int64_t* col);
+int orc_assemble_quad(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const double* cell_xy,
+                      const int64_t* rowptr, const int64_t* col, double* mij, double* cij, double* mi);
 
 /* ---- pointwise building blocks ---- */
 void orc_node_quantities(const double* U, double gamma, double* out /* p, c, phi, eta, eta'(5) */);

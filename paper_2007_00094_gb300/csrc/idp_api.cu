@@ -348,15 +348,34 @@ void idp_destroy(idp_ctx* ctx) {
 
 const char* idp_last_error(const idp_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
-idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
-                               const double* cell_xyz, const int32_t* node_bc, const double* inflow_state) {
-  if (!ctx || !cells || !cell_xyz || n_nodes <= 0 || n_cells <= 0) return fail(ctx, IDP_ERR_ARG, "bad mesh arguments");
+namespace {
+idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                       const double* cell_x, const int32_t* node_bc, const double* inflow_state);
+}
+
+extern "C" idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                                          const double* cell_xyz, const int32_t* node_bc,
+                                          const double* inflow_state) {
+  return upload_mesh(ctx, 3, n_nodes, n_cells, cells, cell_xyz, node_bc, inflow_state);
+}
+
+extern "C" idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                                           const double* cell_xy, const int32_t* node_bc,
+                                           const double* inflow_state) {
+  return upload_mesh(ctx, 2, n_nodes, n_cells, cells, cell_xy, node_bc, inflow_state);
+}
+
+namespace {
+idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
+                       const double* cell_x, const int32_t* node_bc, const double* inflow_state) {
+  if (!ctx || !cells || !cell_x || n_nodes <= 0 || n_cells <= 0) return fail(ctx, IDP_ERR_ARG, "bad mesh arguments");
   if (ctx->has_mesh) {
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
     ctx->has_mesh = ctx->has_state = ctx->has_trace = false;
   }
-  std::string msg = idp::assemble_q1(n_nodes, n_cells, cells, cell_xyz, ctx->M);
+  std::string msg = dim == 3 ? idp::assemble_q1(n_nodes, n_cells, cells, cell_x, ctx->M)
+                             : idp::assemble_q1_2d(n_nodes, n_cells, cells, cell_x, ctx->M);
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
   ctx->M.bc.assign(node_bc ? node_bc : nullptr, node_bc ? node_bc + n_nodes : nullptr);
   if (!node_bc) ctx->M.bc.assign(n_nodes, 0);
@@ -441,6 +460,7 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
   ctx->has_mesh = true;
   return IDP_OK;
 }
+}  // namespace
 
 idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz) {
   if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");

@@ -32,6 +32,10 @@ struct HostMatrices {
 // an empty string on success or a message describing the bad input.
 std::string assemble_q1(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const double* cell_xyz,
                         HostMatrices& out);
+// The same for Q1 quadrilaterals in 2D (4 vertices per cell, v = a + 2b,
+// 2 coordinates per vertex); the z components of c_ij are zero.
+std::string assemble_q1_2d(int64_t n_nodes, int64_t n_cells, const int64_t* cells, const double* cell_xy,
+                           HostMatrices& out);
 
 // Sliced-ELL (C = 32) layout of the matrices in the library's row order.
 struct SellLayout {

@@ -14,96 +14,125 @@ namespace idp {
 
 namespace {
 
-// 3-point Gauss-Legendre rule on [0,1]: exact for polynomials of degree 5,
-// enough for phi_i phi_j det J and phi_i cof(J) grad^ phi_j of a trilinear
-// map (degree <= 4 per direction).
+// 3-point Gauss-Legendre rule per direction on [0,1]^D: exact for
+// polynomials of degree 5 per direction, enough for phi_i phi_j det J and
+// phi_i cof(J) grad^ phi_j of a multilinear map (degree <= 4 per direction).
+template <int D>
 struct Quadrature {
-  double w[27];
-  double phi[27][8];
-  double dphi[27][8][3];
+  static constexpr int NQ = D == 3 ? 27 : 9, NV = 1 << D;
+  double w[NQ];
+  double phi[NQ][NV];
+  double dphi[NQ][NV][D];
   Quadrature() {
     const double r = std::sqrt(15.0) / 10.0;
     const double x1[3] = {0.5 - r, 0.5, 0.5 + r};
     const double w1[3] = {5.0 / 18.0, 4.0 / 9.0, 5.0 / 18.0};
-    for (int q = 0; q < 27; ++q) {
-      const int qi[3] = {q % 3, (q / 3) % 3, q / 9};
-      w[q] = w1[qi[0]] * w1[qi[1]] * w1[qi[2]];
-      for (int v = 0; v < 8; ++v) {
-        double s[3], ds[3];
-        for (int d = 0; d < 3; ++d) {
+    for (int q = 0; q < NQ; ++q) {
+      int qi[3] = {q % 3, (q / 3) % 3, q / 9};
+      w[q] = 1.0;
+      for (int d = 0; d < D; ++d) w[q] *= w1[qi[d]];
+      for (int v = 0; v < NV; ++v) {
+        double sh[3], ds[3];
+        for (int d = 0; d < D; ++d) {
           const double x = x1[qi[d]];
           const bool hi = (v >> d) & 1;
-          s[d] = hi ? x : 1.0 - x;
+          sh[d] = hi ? x : 1.0 - x;
           ds[d] = hi ? 1.0 : -1.0;
         }
-        phi[q][v] = s[0] * s[1] * s[2];
-        dphi[q][v][0] = ds[0] * s[1] * s[2];
-        dphi[q][v][1] = s[0] * ds[1] * s[2];
-        dphi[q][v][2] = s[0] * s[1] * ds[2];
+        phi[q][v] = 1.0;
+        for (int d = 0; d < D; ++d) phi[q][v] *= sh[d];
+        for (int e = 0; e < D; ++e) {
+          double g = ds[e];
+          for (int d = 0; d < D; ++d)
+            if (d != e) g *= sh[d];
+          dphi[q][v][e] = g;
+        }
       }
     }
   }
 };
 
-// Local 8x8 matrices of one cell: m_ab, c_ab (3 components) and int phi_a.
-// Uses det(J) grad phi_b = cof(J) grad^ phi_b, with cof(J) the cofactor matrix.
-bool local_matrices(const Quadrature& Q, const double* X, double M[8][8], double Cm[3][8][8], double m[8]) {
-  std::memset(M, 0, sizeof(double) * 64);
-  std::memset(Cm, 0, sizeof(double) * 192);
-  std::memset(m, 0, sizeof(double) * 8);
-  for (int q = 0; q < 27; ++q) {
+// Local matrices of one cell: m_ab, c_ab (3 components; the z component is 0
+// in 2D) and int phi_a.  Uses det(J) grad phi_b = cof(J) grad^ phi_b, with
+// cof(J) the cofactor matrix; X holds D coordinates per vertex.
+template <int D>
+bool local_matrices(const Quadrature<D>& Q, const double* X, double (*M)[1 << D], double (*Cm)[1 << D][1 << D],
+                    double* m) {
+  constexpr int NV = 1 << D, NQ = Quadrature<D>::NQ;
+  for (int a = 0; a < NV; ++a) {
+    m[a] = 0.0;
+    for (int b = 0; b < NV; ++b) {
+      M[a][b] = 0.0;
+      for (int r = 0; r < 3; ++r) Cm[r][a][b] = 0.0;
+    }
+  }
+  for (int q = 0; q < NQ; ++q) {
     double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int v = 0; v < 8; ++v)
-      for (int r = 0; r < 3; ++r)
-        for (int s = 0; s < 3; ++s) J[r][s] += X[3 * v + r] * Q.dphi[q][v][s];
-    double K[3][3];  // cofactors
-    K[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    K[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    K[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    K[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-    K[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-    K[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-    K[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-    K[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-    K[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const double det = J[0][0] * K[0][0] + J[0][1] * K[0][1] + J[0][2] * K[0][2];
+    for (int v = 0; v < NV; ++v)
+      for (int r = 0; r < D; ++r)
+        for (int t = 0; t < D; ++t) J[r][t] += X[D * v + r] * Q.dphi[q][v][t];
+    double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // cofactors
+    double det;
+    if (D == 3) {
+      K[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      K[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      K[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      K[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+      K[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+      K[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+      K[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+      K[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+      K[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      det = J[0][0] * K[0][0] + J[0][1] * K[0][1] + J[0][2] * K[0][2];
+    } else {
+      K[0][0] = J[1][1];
+      K[0][1] = -J[1][0];
+      K[1][0] = -J[0][1];
+      K[1][1] = J[0][0];
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    }
     if (!(det > 0.0)) return false;
-    double G[8][3];
-    for (int b = 0; b < 8; ++b)
-      for (int r = 0; r < 3; ++r)
-        G[b][r] = K[r][0] * Q.dphi[q][b][0] + K[r][1] * Q.dphi[q][b][1] + K[r][2] * Q.dphi[q][b][2];
-    for (int a = 0; a < 8; ++a) {
+    double G[NV][3];
+    for (int b = 0; b < NV; ++b)
+      for (int r = 0; r < 3; ++r) {
+        double g = 0.0;
+        if (r < D)
+          for (int t = 0; t < D; ++t) g += K[r][t] * Q.dphi[q][b][t];
+        G[b][r] = g;
+      }
+    for (int a = 0; a < NV; ++a) {
       const double wa = Q.w[q] * Q.phi[q][a];
       m[a] += wa * det;
-      for (int b = 0; b < 8; ++b) {
+      for (int b = 0; b < NV; ++b) {
         M[a][b] += wa * Q.phi[q][b] * det;
-        Cm[0][a][b] += wa * G[b][0];
-        Cm[1][a][b] += wa * G[b][1];
-        Cm[2][a][b] += wa * G[b][2];
+        for (int r = 0; r < D; ++r) Cm[r][a][b] += wa * G[b][r];
       }
     }
   }
   return true;
 }
 
-// Local vertices of the six faces of a hexahedron (v = a + 2b + 4c).
-const int kFace[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+// Local vertices of the faces of a cell (v = a + 2b + 4c): six quadrilaterals
+// of a hexahedron, four edges of a quadrilateral.
+const int kFace3[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+const int kFace2[4][4] = {{0, 2, -1, -1}, {1, 3, -1, -1}, {0, 1, -1, -1}, {2, 3, -1, -1}};
 
-}  // namespace
-
-std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const double* xyz, HostMatrices& out) {
+template <int D>
+std::string assemble_impl(int64_t n, int64_t nc, const int64_t* cells, const double* xyz, HostMatrices& out) {
+  constexpr int NV = 1 << D, NF = 2 * D, FV = 1 << (D - 1);
+  const int(*kFace)[4] = D == 3 ? kFace3 : kFace2;
   if (n <= 0 || nc <= 0) return "empty mesh";
-  for (int64_t q = 0; q < 8 * nc; ++q)
+  for (int64_t q = 0; q < NV * nc; ++q)
     if (cells[q] < 0 || cells[q] >= n) return "cell references a node id out of range";
   // node -> cell incidence
   std::vector<int64_t> inc_ptr(n + 1, 0), inc;
-  for (int64_t q = 0; q < 8 * nc; ++q) inc_ptr[cells[q] + 1]++;
+  for (int64_t q = 0; q < NV * nc; ++q) inc_ptr[cells[q] + 1]++;
   for (int64_t i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
   inc.resize(inc_ptr[n]);
   {
     std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
     for (int64_t c = 0; c < nc; ++c)
-      for (int v = 0; v < 8; ++v) inc[fill[cells[8 * c + v]]++] = c;
+      for (int v = 0; v < NV; ++v) inc[fill[cells[NV * c + v]]++] = c;
   }
   for (int64_t i = 0; i < n; ++i)
     if (inc_ptr[i + 1] == inc_ptr[i]) return "a node belongs to no cell";
@@ -116,7 +145,7 @@ std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const doubl
   for (int64_t i = 0; i < n; ++i) {
     std::vector<int64_t>& r = rows[i];
     for (int64_t q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q)
-      for (int v = 0; v < 8; ++v) r.push_back(cells[8 * inc[q] + v]);
+      for (int v = 0; v < NV; ++v) r.push_back(cells[NV * inc[q] + v]);
     std::sort(r.begin(), r.end());
     r.erase(std::unique(r.begin(), r.end()), r.end());
   }
@@ -139,10 +168,10 @@ std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const doubl
 
   // cell matrices, computed in parallel chunks and added in cell order so the
   // sums do not depend on the thread count
-  static const Quadrature Q;
+  static const Quadrature<D> Q;
   const int64_t chunk = 1 << 16;
   struct Local {
-    double M[8][8], C[3][8][8], m[8];
+    double M[NV][NV], C[3][NV][NV], m[NV];
   };
   std::vector<Local> loc(std::min<int64_t>(chunk, nc));
   for (int64_t c0 = 0; c0 < nc; c0 += chunk) {
@@ -151,15 +180,15 @@ std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const doubl
 #pragma omp parallel for schedule(static) reduction(| : bad)
     for (int64_t c = c0; c < c1; ++c) {
       Local& L = loc[c - c0];
-      if (!local_matrices(Q, xyz + 24 * c, L.M, L.C, L.m)) bad |= 1;
+      if (!local_matrices<D>(Q, xyz + D * NV * c, L.M, L.C, L.m)) bad |= 1;
     }
     if (bad) return "a cell has a non-positive Jacobian determinant";
     for (int64_t c = c0; c < c1; ++c) {
       const Local& L = loc[c - c0];
-      const int64_t* vn = cells + 8 * c;
-      for (int a = 0; a < 8; ++a) {
+      const int64_t* vn = cells + NV * c;
+      for (int a = 0; a < NV; ++a) {
         out.mi[vn[a]] += L.m[a];
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < NV; ++b) {
           const int64_t k = find(vn[a], vn[b]);
           out.mij[k] += L.M[a][b];
           for (int d = 0; d < 3; ++d) out.cij[d][k] += L.C[d][a][b];
@@ -174,32 +203,34 @@ std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const doubl
   // arithmetic and are made skew bitwise here.
   out.boundary_pair.assign(nnz, 0);
   std::vector<uint8_t> on_boundary(n, 0);
-  std::vector<uint8_t> face_free(6 * nc, 0);
+  std::vector<uint8_t> face_free(NF * nc, 0);
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
-    const int64_t* vn = cells + 8 * c;
-    for (int f = 0; f < 6; ++f) {
-      const int64_t a = vn[kFace[f][0]], b = vn[kFace[f][1]], e = vn[kFace[f][2]], g = vn[kFace[f][3]];
+    const int64_t* vn = cells + NV * c;
+    for (int f = 0; f < NF; ++f) {
+      const int64_t a = vn[kFace[f][0]];
       bool shared = false;
       for (int64_t q = inc_ptr[a]; q < inc_ptr[a + 1] && !shared; ++q) {
         const int64_t o = inc[q];
         if (o == c) continue;
-        const int64_t* on = cells + 8 * o;
+        const int64_t* on = cells + NV * o;
         int hit = 0;
-        for (int v = 0; v < 8; ++v) hit += (on[v] == b) + (on[v] == e) + (on[v] == g);
-        shared = hit >= 3;
+        for (int v = 0; v < NV; ++v)
+          for (int p = 1; p < FV; ++p) hit += on[v] == vn[kFace[f][p]];
+        shared = hit >= FV - 1;
       }
-      face_free[6 * c + f] = shared ? 0 : 1;
+      face_free[NF * c + f] = shared ? 0 : 1;
     }
   }
   for (int64_t c = 0; c < nc; ++c) {
-    const int64_t* vn = cells + 8 * c;
-    for (int f = 0; f < 6; ++f) {
-      if (!face_free[6 * c + f]) continue;
-      const int64_t fn[4] = {vn[kFace[f][0]], vn[kFace[f][1]], vn[kFace[f][2]], vn[kFace[f][3]]};
-      for (int p = 0; p < 4; ++p) {
+    const int64_t* vn = cells + NV * c;
+    for (int f = 0; f < NF; ++f) {
+      if (!face_free[NF * c + f]) continue;
+      int64_t fn[4];
+      for (int p = 0; p < FV; ++p) fn[p] = vn[kFace[f][p]];
+      for (int p = 0; p < FV; ++p) {
         on_boundary[fn[p]] = 1;
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < FV; ++r) {
           const int64_t k = find(fn[p], fn[r]);
           if (k >= 0) out.boundary_pair[k] = 1;
         }
@@ -224,6 +255,16 @@ std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const doubl
     }
   }
   return "";
+}
+
+}  // namespace
+
+std::string assemble_q1(int64_t n, int64_t nc, const int64_t* cells, const double* xyz, HostMatrices& out) {
+  return assemble_impl<3>(n, nc, cells, xyz, out);
+}
+
+std::string assemble_q1_2d(int64_t n, int64_t nc, const int64_t* cells, const double* xy, HostMatrices& out) {
+  return assemble_impl<2>(n, nc, cells, xy, out);
 }
 
 std::string build_sell(const HostMatrices& M, SellLayout& L) {

@@ -32,7 +32,7 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
-            "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest"]
+            "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
     L.idp_status_string.argtypes = [C.c_int]
     L.idp_status_string.restype = C.c_char_p
     L.idp_upload_mesh_hex.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
+    L.idp_upload_mesh_quad.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
     L.idp_mesh_info.argtypes = [_vp, _i64p, _i64p]
     L.idp_get_matrices.argtypes = [_vp, _i64p, _i64p, _dp, _dp, _dp]
     L.idp_init_state.argtypes = [_vp, _vp, C.c_int]
@@ -161,12 +162,16 @@ class Solver:
             raise IdpError(st, "idp_create failed")
         self.n = mesh.n_nodes
         cells = np.ascontiguousarray(mesh.cells, dtype=np.int64)
-        xyz = np.ascontiguousarray(mesh.cell_xyz, dtype=np.float64)
         bc = np.ascontiguousarray(mesh.bc, dtype=np.int32)
         inflow = None if mesh.inflow is None else np.ascontiguousarray(mesh.inflow, dtype=np.float64)
-        _check(self._ctx, L.idp_upload_mesh_hex(self._ctx, mesh.n_nodes, cells.shape[0], _ptr(cells, _i64p),
-                                                _ptr(xyz), _ptr(bc, _i32p),
-                                                None if inflow is None else _ptr(inflow)))
+        if cells.shape[1] == 4:  # Q1 quadrilaterals (2D)
+            xyz = np.ascontiguousarray(mesh.cell_xyz[:, :, :2], dtype=np.float64)
+            upload = L.idp_upload_mesh_quad
+        else:
+            xyz = np.ascontiguousarray(mesh.cell_xyz, dtype=np.float64)
+            upload = L.idp_upload_mesh_hex
+        _check(self._ctx, upload(self._ctx, mesh.n_nodes, cells.shape[0], _ptr(cells, _i64p), _ptr(xyz),
+                                 _ptr(bc, _i32p), None if inflow is None else _ptr(inflow)))
         n, nnz = C.c_int64(), C.c_int64()
         _check(self._ctx, L.idp_mesh_info(self._ctx, C.byref(n), C.byref(nnz)))
         self.nnz = nnz.value

@@ -18,6 +18,9 @@ Conventions (the input format of ``idp_upload_mesh_hex`` in include/idp.h):
   axis-aligned wall normals of the faces node ``i`` lies on (slip walls remove
   those momentum components), ``BC_INFLOW`` fixes the node to the inflow
   state.  Outflow and periodic nodes carry no flag.
+* A 2D mesh (Q1 quadrilaterals, 9-point stencil; ``idp_upload_mesh_quad``)
+  uses the same container with 4 vertices per cell, ``v = a + 2 b``; node and
+  vertex positions keep a zero z coordinate.
 * States are conserved variables ``U = (rho, m_x, m_y, m_z, E)`` stored
   struct-of-arrays as a ``(5, N)`` float64 array (Sec. 2).
 
@@ -63,6 +66,10 @@ class HexMesh:
     @property
     def n_cells(self) -> int:
         return int(self.cells.shape[0])
+
+    @property
+    def dim(self) -> int:
+        return 2 if self.cells.shape[1] == 4 else 3
 
 
 def _axis_nodes(n, lo, hi, periodic):
@@ -205,6 +212,131 @@ def forward_step_mesh(m=120, jitter=0.2, seed=2007) -> HexMesh:
                    inflow=U_in, meta={"m": m, "h": h, "jitter": jitter, "seed": seed})
 
 
+def rect_mesh(shape, lo=(0.0, 0.0), hi=(1.0, 1.0), periodic=(True, True), jitter=0.0, seed=0,
+              walls="slip", name=None) -> HexMesh:
+    """2D tensor-product mesh of Q1 quadrilaterals with ``shape = (nx, ny)`` unique
+    nodes per axis; periodic axes, wall flags and jitter as in ``box_mesh``."""
+    nx, ny = (int(v) for v in shape)
+    lo = tuple(float(v) for v in lo)
+    hi = tuple(float(v) for v in hi)
+    coords, hs, ncell = [], [], []
+    for n, a, b, p in zip((nx, ny), lo, hi, periodic):
+        c, h, nc = _axis_nodes(n, a, b, p)
+        coords.append(c)
+        hs.append(h)
+        ncell.append(nc)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()  # x fastest
+    N = ii.shape[0]
+    x = np.zeros((N, 3))
+    x[:, 0] = coords[0][ii]
+    x[:, 1] = coords[1][jj]
+
+    bc = np.zeros(N, dtype=np.int32)
+    on_wall = np.zeros(N, dtype=bool)
+    for axis, (idx, n, p) in enumerate(zip((ii, jj), (nx, ny), periodic)):
+        if p:
+            continue
+        w = (idx == 0) | (idx == n - 1)
+        on_wall |= w
+        if walls == "slip":
+            bc[w] |= (BC_SLIP_X, BC_SLIP_Y)[axis]
+
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        disp = rng.uniform(-1.0, 1.0, size=(N, 2)) * (jitter * np.asarray(hs))[None, :]
+        disp[on_wall] = 0.0
+        x[:, :2] += disp
+
+    cj, ci = np.meshgrid(np.arange(ncell[1]), np.arange(ncell[0]), indexing="ij")
+    ci, cj = ci.ravel(), cj.ravel()
+    C = ci.shape[0]
+    cells = np.empty((C, 4), dtype=np.int64)
+    cell_xyz = np.zeros((C, 4, 3))
+    L = np.asarray(hi) - np.asarray(lo)
+    for v in range(4):
+        gi, gj = ci + (v & 1), cj + ((v >> 1) & 1)
+        wrap = [np.zeros(C, dtype=bool)] * 2
+        if periodic[0]:
+            wrap[0] = gi == nx
+            gi = gi % nx
+        if periodic[1]:
+            wrap[1] = gj == ny
+            gj = gj % ny
+        node = gi + nx * gj
+        cells[:, v] = node
+        pos = x[node].copy()
+        for axis in range(2):
+            pos[wrap[axis], axis] += L[axis]
+        cell_xyz[:, v, :] = pos
+    return HexMesh(x=x, cells=cells, cell_xyz=cell_xyz, bc=bc, volume=float(np.prod(L)),
+                   name=name or f"rect{nx}x{ny}", lo=lo + (0.0,), hi=hi + (0.0,), periodic=tuple(periodic) + (False,),
+                   meta={"shape": (nx, ny), "h": tuple(hs), "jitter": jitter, "seed": seed})
+
+
+def forward_step_mesh_2d(m=1000, jitter=0.2, seed=2007) -> HexMesh:
+    """2D Mach 3 forward-facing step (Woodward-Colella) [0,3]x[0,1], step x>=0.6, y<=0.2.
+
+    Q1 quadrilaterals of spacing ``h = 1/m`` (``m`` a multiple of 5); nodes
+    strictly inside the step removed, interior nodes jittered by
+    ``U[-jitter*h, jitter*h]`` per coordinate (seeded).  Flags: x=0 inflow,
+    x=3 outflow, y=0, y=1, the step top and the step face slip.  ``m=1000``
+    gives 2,524,001 nodes.
+    """
+    if m % 5:
+        raise ValueError("m must be a multiple of 5")
+    h = 1.0 / m
+    nx, ny = 3 * m + 1, m + 1
+    sx, sy = (3 * m) // 5, m // 5
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()
+    keep = ~((ii > sx) & (jj < sy))
+    gid = -np.ones(ii.shape[0], dtype=np.int64)
+    gid[keep] = np.arange(int(keep.sum()))
+    ii, jj = ii[keep], jj[keep]
+    N = ii.shape[0]
+    x = np.zeros((N, 3))
+    x[:, 0] = ii * h
+    x[:, 1] = jj * h
+
+    bc = np.zeros(N, dtype=np.int32)
+    wall_y = (jj == 0) | (jj == ny - 1) | ((jj == sy) & (ii >= sx))
+    wall_x = (ii == sx) & (jj <= sy)
+    bc[wall_x] |= BC_SLIP_X
+    bc[wall_y] |= BC_SLIP_Y
+    inflow = ii == 0
+    bc[inflow] = BC_INFLOW
+    boundary = wall_x | wall_y | inflow | (ii == nx - 1)
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        disp = rng.uniform(-jitter * h, jitter * h, size=(N, 2))
+        disp[boundary] = 0.0
+        x[:, :2] += disp
+
+    cj, ci = np.meshgrid(np.arange(ny - 1), np.arange(nx - 1), indexing="ij")
+    ci, cj = ci.ravel(), cj.ravel()
+    ckeep = ~((ci >= sx) & (cj < sy))
+    ci, cj = ci[ckeep], cj[ckeep]
+    cells = np.empty((ci.shape[0], 4), dtype=np.int64)
+    for v in range(4):
+        cells[:, v] = gid[(ci + (v & 1)) + nx * (cj + ((v >> 1) & 1))]
+    assert (cells >= 0).all()
+    U_in = primitive_to_conserved(np.array([1.4]), np.array([[3.0], [0.0], [0.0]]), np.array([1.0]))[:, 0]
+    return HexMesh(x=x, cells=cells, cell_xyz=x[cells], bc=bc, volume=3.0 - 2.4 * 0.2, name=f"ffs2d_m{m}",
+                   lo=(0.0, 0.0, 0.0), hi=(3.0, 1.0, 0.0), periodic=(False, False, False),
+                   inflow=U_in, meta={"m": m, "h": h, "jitter": jitter, "seed": seed})
+
+
+def vortex_mesh_2d(n, jitter=0.0, seed=0):
+    """Periodic unit square with ``n`` nodes along x and y (Q1 quadrilaterals)."""
+    return rect_mesh((n, n), periodic=(True, True), jitter=jitter, seed=seed, name=f"vortex2d_{n}")
+
+
+def sod_mesh_2d(nx, ny=4):
+    """2D shock tube [0,1]x[0,1], slip walls along x, periodic in y."""
+    return rect_mesh((nx, ny), periodic=(False, True), walls="slip", name=f"sod2d_{nx}")
+
+
 # ---------------------------------------------------------------------------
 # Initial states (conserved variables, gamma = 7/5 polytropic gas, Sec. 2)
 # ---------------------------------------------------------------------------
@@ -316,6 +448,27 @@ def random_riemann_batch(n_instances=256, side_range=(8, 48), seed=4):
         nrm = rng.normal(size=3)
         nrm /= np.linalg.norm(nrm)
         out.append((mesh, riemann_state(mesh.x, states[0], states[1], normal=tuple(nrm))))
+    return out
+
+
+def random_riemann_batch_2d(n_instances=256, side_range=(16, 160), seed=6):
+    """Independent 2D Riemann problems on slip-walled unit squares of random size
+    (Q1 quadrilaterals); states drawn as in ``random_riemann_batch`` with u_z = 0
+    and a uniformly random in-plane interface normal."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_instances):
+        n = int(rng.integers(side_range[0], side_range[1] + 1))
+        mesh = rect_mesh((n, n), periodic=(False, False), walls="slip", name=f"riemann2d{k}_{n}")
+        states = []
+        for _ in range(2):
+            rho = rng.uniform(0.1, 2.0)
+            u = tuple(rng.uniform(-2.0, 2.0, size=2)) + (0.0,)
+            p = rng.uniform(0.1, 10.0)
+            states.append((rho, u, p))
+        a = rng.uniform(0.0, 2.0 * np.pi)
+        out.append((mesh, riemann_state(mesh.x, states[0], states[1], normal=(np.cos(a), np.sin(a), 0.0),
+                                        point=(0.5, 0.5, 0.0))))
     return out
 
 

@@ -41,6 +41,8 @@ def _perturb(mesh, U, amp, seed):
     eps = U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
     p = 0.4 * eps * (1.0 + amp * rng.standard_normal(n))
     u = np.where((mesh.bc & np.array([[1], [2], [4]])) > 0, 0.0, u)
+    if mesh.dim == 2:
+        u[2] = 0.0
     return W.primitive_to_conserved(rho, u, p)
 
 
@@ -61,10 +63,17 @@ def _case(name):
     if name == "ffs":
         m = W.forward_step_mesh(m=10, jitter=0.2, seed=2007)
         return m, _perturb(m, W.forward_step_state(m), 1e-2, 9)
+    if name == "rect2d":
+        m = W.rect_mesh((9, 8), hi=(1.1, 0.9), periodic=(False, False), jitter=0.2, seed=12)
+        rho, u, p = W.vortex_primitive(m.x)
+        return m, _perturb(m, W.primitive_to_conserved(rho, u, p), 1e-3, 13)
+    if name == "ffs2d":
+        m = W.forward_step_mesh_2d(m=10, jitter=0.2, seed=2007)
+        return m, _perturb(m, W.forward_step_state(m), 1e-2, 14)
     raise KeyError(name)
 
 
-CASES = ["vortex", "wallbox", "sod", "ffs"]
+CASES = ["vortex", "wallbox", "sod", "ffs", "rect2d", "ffs2d"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -113,7 +122,7 @@ def test_adjoint_euler_step_matches_reference_gradient(name, fixed_tau):
         assert abs(gtau - float(gtau_ref)) <= ADJ_TOL * max(abs(float(gtau_ref)), 1e-300), (gtau, float(gtau_ref))
 
 
-@pytest.mark.parametrize("name", ["wallbox", "sod", "vortex"])
+@pytest.mark.parametrize("name", ["wallbox", "sod", "vortex", "rect2d"])
 def test_adjoint_rk3_run_matches_reference_gradient(name):
     """Three SSP-RK3 steps, checkpoints every second step (two segments)."""
     mesh, U = _case(name)

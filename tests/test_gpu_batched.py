@@ -156,3 +156,33 @@ def test_batch_with_relaxed_bounds_equals_instances_alone(batch, precision):
         a.step(2)
         a.synchronize()
         np.testing.assert_array_equal(out[:, off[k]:off[k + 1]], a.get_state())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_2d_batch_equals_instances_alone_and_matches_oracle(precision, n_threads):
+    """A batch of 2D Riemann problems (Q1 quadrilaterals): bitwise equal to each
+    instance alone, and (FP64) within the parity tolerance of the oracle."""
+    parts = W.random_riemann_batch_2d(n_instances=4, side_range=(6, 15), seed=6)
+    mesh, off, U = W.concat_meshes([m for m, _ in parts], [u for _, u in parts])
+    s = _solver(mesh, precision=precision)
+    s.set_instances(off)
+    s.init_state(U)
+    s.step(2)
+    s.synchronize()
+    out = s.get_state()
+    assert not out[3].any()
+    for k, (m, u) in enumerate(parts):
+        a = _solver(m, precision=precision)
+        a.init_state(u)
+        a.step(2)
+        a.synchronize()
+        got = out[:, off[k]:off[k + 1]]
+        np.testing.assert_array_equal(got, a.get_state())
+        if precision == 0:
+            om = O.assemble(m)
+            ref = u
+            for _ in range(2):
+                ref, _, st = O.ssprk3_step(om, ref, O.default_params(n_threads=n_threads))
+                assert st == 0
+            assert rel_field_err_l2(got, ref).max() <= 1e-12
+            assert rel_field_err(got, ref).max() <= 1e-11

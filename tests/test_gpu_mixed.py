@@ -36,7 +36,7 @@ def _l1_rel(a, b):
     return np.abs(a - b).mean(axis=1) / scale
 
 
-@pytest.mark.parametrize("name", ["sod_jitter", "ffs10", "wallbox_jitter", "vortex17"])
+@pytest.mark.parametrize("name", ["sod_jitter", "ffs10", "wallbox_jitter", "vortex17", "ffs2d_10", "wallrect_jitter"])
 def test_fp32_wavespeed_bound_stays_above_fp64(name):
     mesh, U = _mesh(name)
     s64 = _solver(mesh)
@@ -51,7 +51,8 @@ def test_fp32_wavespeed_bound_stays_above_fp64(name):
     assert (dm[off] <= d64[off] * (1.0 + 2e-5)).all()
 
 
-@pytest.mark.parametrize("name,tol", [("sod_jitter", 2e-4), ("ffs10", 5e-4), ("vortex17", 2e-3)])
+@pytest.mark.parametrize("name,tol", [("sod_jitter", 2e-4), ("ffs10", 5e-4), ("vortex17", 2e-3), ("ffs2d_10", 1e-3),
+                                      ("wallrect_jitter", 5e-4), ("bumpy2d_jitter", 2e-3)])
 def test_mixed_accuracy_against_oracle(name, tol, n_threads):
     mesh, U = _mesh(name)
     om = O.assemble(mesh)
@@ -69,7 +70,7 @@ def test_mixed_accuracy_against_oracle(name, tol, n_threads):
     assert (out[0] > 0).all() and (internal_energy(out) > 0).all()
 
 
-@pytest.mark.parametrize("name", ["sod_jitter", "ffs10", "vortex17", "tiny3"])
+@pytest.mark.parametrize("name", ["sod_jitter", "ffs10", "vortex17", "tiny3", "ffs2d_10", "bumpy2d_jitter"])
 def test_mixed_invariants(name):
     mesh, U = _mesh(name)
     s = _solver(mesh, precision=1)

@@ -40,10 +40,29 @@ def _mesh(name):
     if name == "tiny3":
         m = W.vortex_mesh(3)
         return m, W.vortex_state(m)
+    # 2D Q1 (quadrilaterals, 9-point stencil)
+    if name == "bumpy2d_jitter":
+        # density bumps make the entropy non-constant (see gpu_common on the isentropic case)
+        m = W.rect_mesh((37, 29), periodic=(True, True), jitter=0.25, seed=8)
+        return m, W.bumpy_vortex_state(m, amplitude=5e-2)
+    if name == "wallrect_jitter":
+        m = W.rect_mesh((41, 35), hi=(1.2, 1.0), periodic=(False, False), jitter=0.25, seed=9)
+        U = W.riemann_state(m.x, (1.0, (0.3, -0.2, 0.0), 1.0), (0.2, (-0.5, 0.4, 0.0), 0.15),
+                            normal=(0.8, 0.6, 0.0), point=(0.55, 0.45, 0.0))
+        U[1:3] = np.where((m.bc & np.array([[1], [2]])) > 0, 0.0, U[1:3])
+        return m, U
+    if name == "ffs2d_10":
+        m = W.forward_step_mesh_2d(m=10, jitter=0.2, seed=2007)
+        return m, W.forward_step_state(m)
     raise KeyError(name)
 
 
-CASES = ["vortex17", "wallbox_jitter", "sod_jitter", "ffs10", "tiny3"]
+CASES = ["vortex17", "wallbox_jitter", "sod_jitter", "ffs10", "tiny3", "bumpy2d_jitter", "wallrect_jitter",
+         "ffs2d_10"]
+
+
+def _isentropic(name):
+    return name.startswith("vortex")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,7 +111,7 @@ def test_euler_step_trace_parity(name, n_threads):
     np.maximum.at(var, rows, np.abs(U[:, om.col] - U[:, rows]).max(axis=0) / Umax)
     assert (np.abs(s.field("alpha") - tr["alpha"]) * var).max() <= 1e-12
     # state-sized quantities against the state scale
-    max_tol = ISENTROPIC_MAX_TOL if name == "vortex17" else 1e-12
+    max_tol = ISENTROPIC_MAX_TOL if _isentropic(name) else 1e-12
     for key, tol in (("UL", 1e-13), ("bounds", 1e-13), ("U5", max_tol), ("Ulim", max_tol)):
         err = rel_field_err(s.field(key), tr[key])
         assert err.max() <= tol, (key, err)
@@ -110,7 +129,7 @@ def test_euler_step_trace_parity(name, n_threads):
     Pn = np.abs(P).max(axis=0) / Umax
     for key in ("l4", "l5"):
         dl = np.abs(s.field(key) - tr[key])[off]
-        assert (dl * Pn[off]).max() <= (1e-9 if name == "vortex17" else 1e-11), key
+        assert (dl * Pn[off]).max() <= (1e-9 if _isentropic(name) else 1e-11), key
     out = s.get_state()
     assert rel_field_err(out, ref).max() <= max_tol
     assert rel_field_err_l2(out, ref).max() <= 1e-12
@@ -130,11 +149,13 @@ def test_rk3_step_parity_and_invariants(name, n_threads):
     s.step(3)
     s.synchronize()
     out = s.get_state()
-    assert rel_field_err(out, ref).max() <= (ISENTROPIC_MAX_TOL if name == "vortex17" else 1e-12)
+    assert rel_field_err(out, ref).max() <= (ISENTROPIC_MAX_TOL if _isentropic(name) else 1e-12)
     assert rel_field_err_l2(out, ref).max() <= 1e-12
     assert (out[0] > 0).all() and (internal_energy(out) > 0).all()
     st, rep = s.check_bounds()
     assert st == 0 and rep.n_rho_nonpositive == 0 and rep.n_eps_nonpositive == 0
+    if mesh.dim == 2:  # c_ij has no z component: m_z = 0 stays exactly 0
+        assert not out[3].any()
 
 
 def test_local_bounds_hold_on_gpu():
@@ -236,7 +257,7 @@ def test_torch_device_buffers():
     np.testing.assert_array_equal(out.cpu().numpy(), s2.get_state())
 
 
-@pytest.mark.parametrize("name", ["wallbox_jitter", "sod_jitter", "vortex17"])
+@pytest.mark.parametrize("name", ["wallbox_jitter", "sod_jitter", "vortex17", "wallrect_jitter"])
 def test_relaxed_bounds_parity(name, n_threads):
     """Bound relaxation (idp_config.relax, Reading A14) against the oracle with
     the same option: the relaxed bounds, one euler_step and one SSP-RK3 step."""
