@@ -17,6 +17,12 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["idp_stage.cu", "idp_mixed.cu", "idp_api.cu", "idp_noalloc.cu", "idp_adjoint.cu"]
 CXX_SOURCES = ["idp_mesh.cpp"]
+# The FP32-mixed kernels run the same row functions in the per-step kernels and
+# in the persistent kernel, whose results must be bitwise equal.  Without FMA
+# contraction every multiply and add is rounded as written (fused only where
+# the source says fmaf/fma), so the result does not depend on how the code
+# generator schedules each kernel.
+EXTRA_FLAGS = {"idp_mixed.cu": ["-fmad=false"]}
 
 
 def _sources():
@@ -39,8 +45,8 @@ def _stale() -> bool:
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-I", INCLUDE,
-               "-I", CSRC, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", *EXTRA_FLAGS.get(os.path.basename(src), []),
+               "-Xcompiler", "-fPIC,-fopenmp", "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:

@@ -72,11 +72,11 @@ __device__ __forceinline__ void flux_dot_f(float m1, float m2, float m3, float i
 // Two-rarefaction wavespeed bound of Sec. 3.7 in FP32 (same algebra as the
 // FP64 version in idp_device.cuh), times the safety factor.
 __device__ __forceinline__ float lambda_max_f(float nx, float ny, float nz, const SideF& L, const SideF& R) {
-  const float uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
-  const float uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
-  float num = L.c + R.c - 0.2f * (uR - uL);
+  const float uL = fmaf(L.mz, nz, fmaf(L.my, ny, L.mx * nx)) * L.inv_rho;
+  const float uR = fmaf(R.mz, nz, fmaf(R.my, ny, R.mx * nx)) * R.inv_rho;
+  float num = fmaf(-0.2f, uR - uL, L.c + R.c);
   num = num > 0.0f ? num : 0.0f;
-  const float x = num / (L.c * L.pm + R.c * R.pm);
+  const float x = num / fmaf(L.c, L.pm, R.c * R.pm);
   const float x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
   const float p_tr = x6 * x;
   const bool left_high = L.p >= R.p;
@@ -88,8 +88,8 @@ __device__ __forceinline__ float lambda_max_f(float nx, float ny, float nz, cons
   const bool psi_negative = du < 0.0f && 2.0f * dp * dp < du * du * (rho_low * (2.4f * p_max + 0.4f * p_low));
   const float p_star = psi_negative ? p_tr : fminf(p_max, p_tr);
   const float k = 6.0f / 7.0f;
-  const float lam1 = uL - L.c * sqrtf(1.0f + k * fmaxf((p_star - L.p) * L.inv_p, 0.0f));
-  const float lam3 = uR + R.c * sqrtf(1.0f + k * fmaxf((p_star - R.p) * R.inv_p, 0.0f));
+  const float lam1 = fmaf(-L.c, sqrtf(fmaf(k, fmaxf((p_star - L.p) * L.inv_p, 0.0f), 1.0f)), uL);
+  const float lam3 = fmaf(R.c, sqrtf(fmaf(k, fmaxf((p_star - R.p) * R.inv_p, 0.0f), 1.0f)), uR);
   return fmaxf(fmaxf(-lam1, 0.0f), fmaxf(lam3, 0.0f)) * kLambdaSafety;
 }
 
@@ -137,8 +137,8 @@ struct PsiLine {
 
 __device__ __forceinline__ PsiLine make_line(const PsiAnchor& a, const float* P) {
   PsiLine L;
-  L.g = P[0] * a.u[4] + a.u[0] * P[4] - (a.u[1] * P[1] + a.u[2] * P[2] + a.u[3] * P[3]);
-  L.h = P[0] * P[4] - 0.5f * (P[1] * P[1] + P[2] * P[2] + P[3] * P[3]);
+  L.g = fmaf(P[0], a.u[4], a.u[0] * P[4]) - fmaf(a.u[3], P[3], fmaf(a.u[2], P[2], a.u[1] * P[1]));
+  L.h = fmaf(-0.5f, fmaf(P[3], P[3], fmaf(P[2], P[2], P[1] * P[1])), P[0] * P[4]);
   L.sr = P[0] * a.inv_rho0;
   L.gabs = fabsf(P[0] * a.u[4]) + fabsf(a.u[0] * P[4]) + fabsf(a.u[1] * P[1]) + fabsf(a.u[2] * P[2]) +
            fabsf(a.u[3] * P[3]);
@@ -152,10 +152,10 @@ __device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, fl
   const float s = t * L.sr;  // > -1 inside the density interval
   const float lg = log1pf(s);
   const float q = expm1f(2.4f * lg);
-  if (dpsi) *dpsi = L.g + 2.0f * t * L.h - a.phi_pow0 * 2.4f * ((1.0f + q) / (1.0f + s)) * L.sr;
+  if (dpsi) *dpsi = fmaf(2.0f * t, L.h, L.g) - a.phi_pow0 * 2.4f * ((1.0f + q) / (1.0f + s)) * L.sr;
   *lg_out = lg;
   *q_out = q;
-  return a.psi0 + t * (L.g + t * L.h) - a.phi_pow0 * q - a.margin;
+  return fmaf(t, fmaf(t, L.h, L.g), a.psi0) - fmaf(a.phi_pow0, q, a.margin);
 }
 
 // Bound on |psi_at(t) - (Psi(t) - margin)|, Psi in exact arithmetic along
@@ -304,7 +304,7 @@ __device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGrap
     float fj[kFields], fi[kFields];
     flux_dot_f(sj.mx, sj.my, sj.mz, sj.inv_rho, sj.p, h_j, cx, cy, cz, fj);
     flux_dot_f(si.mx, si.my, si.mz, si.inv_rho, si.p, h_i, cx, cy, cz, fi);
-    a += (s_j - s_i) * fj[0];
+    a = fmaf(s_j - s_i, fj[0], a);
     float df[kFields];
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
@@ -429,15 +429,15 @@ __device__ __forceinline__ void row_low_order_m(const DeviceGraph& G, const Stag
     }
     const float dH = dij * (a_i + alpha[j]) * 0.5f;
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * diff[f];
+    for (int f = 0; f < kFields; ++f) rr[f] += fmaf(dH, diff[f], -df[f]);
     if (dij != 0.0f && j != r) {
       const float inv2d = dinv[p];
       const float coef = two_tau_m * dij;
       float db[kFields];
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        db[f] = 0.5f * diff[f] - df[f] * inv2d;
-        inc[f] += coef * db[f];
+        db[f] = fmaf(-df[f], inv2d, 0.5f * diff[f]);
+        inc[f] = fmaf(coef, db[f], inc[f]);
       }
       dmin = fminf(dmin, db[0]);
       dmax = fmaxf(dmax, db[0]);
@@ -512,7 +512,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
     const float dd = dij * (a_i + alpha[j]) * 0.5f - dij;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
-      pij[f] = scale * (b_ij * R[f * n + j] - b_ji * ri[f] + dd * (Uf[f * n + j] - ui[f]));
+      pij[f] = scale * fmaf(b_ij, R[f * n + j], fmaf(-b_ji, ri[f], dd * (Uf[f * n + j] - ui[f])));
       P[f * ns + p] = pij[f];
     }
     l[p] = limiter_mixed(ul, anchor, pij, pmin, C.lim);
@@ -546,7 +546,7 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
     if (G.col[p] == r) continue;
     const float w = lam * fminf(lold[p], lold[G.tpos[p]]);
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) inc[f] += w * P[f * ns + p];
+    for (int f = 0; f < kFields; ++f) inc[f] = fmaf(w, P[f * ns + p], inc[f]);
   }
   double u[kFields];
 #pragma unroll
@@ -556,18 +556,36 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
   }
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
   const PsiAnchor anchor = make_anchor(u, rmin, rmax, pmin);
+  // Software pipeline: the loads of entry k + 1 are issued before the limiter
+  // of entry k, so their latency overlaps its arithmetic (they read P and l_old
+  // slots that iteration k does not write).
+  bool diag_n = false;
+  float lk_n = 0.0f, p_n[kFields];
+  auto fetch = [&](int k) {
+    const int64_t q = base + 32 * (int64_t)k;
+    diag_n = G.col[q] == r;
+    lk_n = fminf(lold[q], lold[G.tpos[q]]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) p_n[f] = P[f * ns + q];
+  };
+  if (len > 0) fetch(0);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) {
+    const bool diag = diag_n;
+    const float lk = lk_n;
+    float pold[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) pold[f] = p_n[f];
+    if (k + 1 < len) fetch(k + 1);
+    if (diag) {
       lnew[p] = 0.0f;
       continue;
     }
-    const float lk = fminf(lold[p], lold[G.tpos[p]]);
     float pij[kFields];
     bool zero = true;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
-      pij[f] = (1.0f - lk) * P[f * ns + p];
+      pij[f] = (1.0f - lk) * pold[f];
       P[f * ns + p] = pij[f];
       zero &= pij[f] == 0.0f;
     }
@@ -575,7 +593,7 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
   }
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock, 4) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
                                                            double* __restrict__ Unext, float* __restrict__ P,
                                                            const float* __restrict__ lold, float* __restrict__ lnew,
                                                            const double* __restrict__ bnd) {
@@ -599,7 +617,7 @@ __device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageCon
     if (G.col[p] == r) continue;
     const float w = lam * fminf(l[p], l[G.tpos[p]]);
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) inc[f] += w * P[f * ns + p];
+    for (int f = 0; f < kFields; ++f) inc[f] = fmaf(w, P[f * ns + p], inc[f]);
   }
   double u[kFields];
 #pragma unroll
@@ -622,8 +640,8 @@ __device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageCon
 #pragma unroll
   for (int f = 0; f < kFields; ++f) {
     double v = u[f];
-    if (blend == kBlendStage2) v = 0.75 * Un[f * n + r] + 0.25 * u[f];
-    if (blend == kBlendStage3) v = (1.0 / 3.0) * Un[f * n + r] + (2.0 / 3.0) * u[f];
+    if (blend == kBlendStage2) v = fma(0.75, Un[f * n + r], 0.25 * u[f]);
+    if (blend == kBlendStage3) v = fma(1.0 / 3.0, Un[f * n + r], (2.0 / 3.0) * u[f]);
     out[f] = v;
     finite &= isfinite(v);
   }

@@ -352,20 +352,36 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
   for (int f = 0; f < kFields; ++f) Unext[f * n + r] = u[f];
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
   const PsiCheck32 pre = make_psi_check(u, pmin);
+  // Software pipeline: entry k + 1's loads are issued before entry k's limiter.
+  bool diag_n = false;
+  double lk_n = 0.0, p_n[kFields];
+  auto fetch = [&](int k) {
+    const int64_t q = base + 32 * (int64_t)k;
+    diag_n = G.col[q] == r;
+    lk_n = min_k(lold[q], lold[G.tpos[q]]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) p_n[f] = P[f * ns + q];
+  };
+  if (len > 0) fetch(0);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) {
+    const bool diag = diag_n;
+    const double lk = lk_n;
+    double pold[kFields];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) pold[f] = p_n[f];
+    if (k + 1 < len) fetch(k + 1);
+    if (diag) {
       lnew[p] = 0.0;
       continue;
     }
-    const double lk = min_k(lold[p], lold[G.tpos[p]]);
     double pij[kFields];
     bool zero = true;
     if (is_one(lk)) {
       // l = 1: (1 - l) P_ij is a zero with the sign of P_ij
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        pij[f] = __hiloint2double(__double2hiint(P[f * ns + p]) & (int)0x80000000, 0);
+        pij[f] = __hiloint2double(__double2hiint(pold[f]) & (int)0x80000000, 0);
         P[f * ns + p] = pij[f];
       }
     } else {
@@ -373,7 +389,7 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
         // l = 0 leaves P_ij as it is
-        pij[f] = keep ? P[f * ns + p] : (1.0 - lk) * P[f * ns + p];
+        pij[f] = keep ? pold[f] : (1.0 - lk) * pold[f];
         if (!keep) P[f * ns + p] = pij[f];
         zero &= ((((unsigned int)__double2hiint(pij[f])) << 1) | (unsigned int)__double2loint(pij[f])) == 0u;
       }
