@@ -36,6 +36,16 @@ UNIT = "node-stage updates/s"
 # by their flops).  Step 5 is the limiter pass, step 6 the final update.
 FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "flux_limit": 183.0,
                 "limiter_pass": 155.0, "final": 12.0}
+# FP64 arithmetic the kernels execute per stored entry: thread-level
+# 2 x DFMA + DADD + DMUL from ncu (smsp__sass_thread_inst_executed_op_d*) on
+# the step channel at h = 1/80 (17,679,673 entries).  This is the `achieved`
+# work of the FP64 roofline; the paper's per-step counts above overstate what
+# these kernels execute (lambda_max once per unordered edge, powers without
+# pow, tests on 32-bit words), so a rate from them can exceed the pipe.
+FP64_FLOP_PER_NNZ_EXECUTED = {"edge": 84.0, "low_order": 55.0, "flux_limit": 51.1, "limiter_pass": 13.4}
+# FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, % of active cycles) of
+# the same capture: the pipe also issues compares, conversions and min/max.
+FP64_PIPE_BUSY_NCU = {"edge": 0.876, "low_order": 0.870, "flux_limit": 0.873, "limiter_pass": 0.704}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s; a dependent-free DFMA
 # stream measured 1.197 TFLOP/s at 1.97 GHz on this machine).
@@ -44,9 +54,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # for the workloads of this file, keyed by kernel.  Captured on smaller meshes
 # of the same workloads (the full-size inputs are too large for an ncu replay)
 # and scaled by the number of matrix entries (profiles/ holds the captures):
-# FP64 k_flux_limit 1.266 GB at h = 1/80 (17,679,673 entries) -> h = 1/120;
+# FP64 at h = 1/80 (17,679,673 entries) -> h = 1/120;
 # FP32-mixed k_limiter_pass_m 1.976 GB at 96^3 (23,393,656 entries) -> 128^3.
-NCU_TRAFFIC_BYTES = {"flux_limit": 1.265932e9 * 59373973 / 17679673}
+NCU_TRAFFIC_BYTES = {k: v * 59373973 / 17679673 for k, v in
+                     {"edge": 1.583067e9, "flux_limit": 1.265618e9, "low_order": 1.210931e9,
+                      "limiter_pass": 2.497277e9}.items()}
 NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 1.976342e9 * 55742968 / 23393656}
 
 
@@ -297,10 +309,11 @@ def pattern_q1_2d(stream, args):
         dom_ms, dom_n = prof[dom]
         per_launch_s = dom_ms / dom_n * 1e-3
         if prec == 0:
-            achieved = FLOP_PER_NNZ[dom] * s.nnz / per_launch_s / 1e12
+            achieved = FP64_FLOP_PER_NNZ_EXECUTED[dom] * s.nnz / per_launch_s / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                    "work": f"{FLOP_PER_NNZ[dom]:.0f} flop/nnz x {s.nnz} nnz per launch"}
+                    "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, 3D step channel) x "
+                            f"{s.nnz} nnz per launch"}
         else:
             per_slot, per_node = MIXED_BYTES[dom]
             achieved = (per_slot * s.nnz + per_node * mesh.n_nodes) / per_launch_s / 1e9
@@ -588,7 +601,7 @@ def main():
         dom = max(prof, key=lambda k: prof[k][0])
         dom_ms, dom_n = prof[dom]
         per_launch_s = dom_ms / dom_n * 1e-3
-        achieved = FLOP_PER_NNZ[dom] * nnz / per_launch_s / 1e12
+        achieved = FP64_FLOP_PER_NNZ_EXECUTED[dom] * nnz / per_launch_s / 1e12
         traffic = NCU_TRAFFIC_BYTES.get(dom) if args.m == 120 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -601,7 +614,10 @@ def main():
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "peak_source": "FP64 pipe from unit counts and max clock (nominal 1.25 TFLOP/s)",
-                         "work": f"{FLOP_PER_NNZ[dom]:.0f} flop/nnz x {nnz} nnz per launch"},
+                         "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, h = 1/80) x {nnz} "
+                                 f"nnz per launch",
+                         "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU.get(dom),
+                         "paper_flop_rate": FLOP_PER_NNZ[dom] * nnz / per_launch_s / 1e12},
             "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]},
             "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
             "clocks": clocks,
