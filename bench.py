@@ -162,6 +162,7 @@ def pattern_mixed(stream, args):
         entry = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                  "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
         if prec == 1:
+            entry["entry_table_values"] = s.entry_table_size()
             dom = max(prof, key=lambda k: prof[k][0])
             dom_ms, dom_n = prof[dom]
             per_slot, per_node = MIXED_BYTES[dom]
@@ -174,6 +175,13 @@ def pattern_mixed(stream, args):
                                  "work": f"{per_slot} B/entry x {s.nnz} + {per_node} B/node x {mesh.n_nodes}"}
         out[name] = entry
         s.close()
+    # the same mixed stage reading per-entry FP32 arrays instead of the entry table
+    s = Solver(mesh, stream=stream, precision=1, entry_table=0)
+    s.init_state(U0)
+    ms_pe, prof_pe = _time_steps(s, stream, args.pattern_steps, args.warmup)
+    s.close()
+    out["fp32_mixed"]["per_entry_arrays"] = {
+        "ms_per_step": ms_pe, "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof_pe.items() if v[1]}}
     ref = states["fp64"]
     scale = np.abs(ref).max(axis=1)
     scale = np.where(scale > 1e-12 * scale.max(), scale, scale.max())

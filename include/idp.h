@@ -63,10 +63,17 @@ typedef struct {
                                phi_min (1 - r_i) with r_i = (m_i / |Omega|)^(1/2), |Omega| the volume of
                                the node's instance (Sec. 3.9 remark; the formula is project-defined);
                                0 (default): the bounds as Alg. 1 states them */
+  int entry_table;          /* FP32-mixed only.  1 (default): when the mesh has at most 4096 distinct
+                               FP32 entries (c_ij, m_ij, |c_ij|, 1/|c_ij|) -- uniform tensor grids --
+                               store each stored entry as a 16-bit index into a table of the distinct
+                               values instead of six per-entry floats (the matrices of Sec. 3.1,
+                               precomputed once as Sec. 3.2 asks); 0: per-entry arrays.  Results are
+                               bitwise the same either way. */
 } idp_config;
 
 /* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,
- * newton_tol 1e-10, newton_eps = DBL_EPSILON, FP64, schedule 0. */
+ * newton_tol 1e-10, newton_eps = DBL_EPSILON, FP64, schedule 0, no bound
+ * relaxation, entry table on. */
 void idp_config_default(idp_config* cfg);
 
 /* Creates a context on the current CUDA device.  cuda_stream is a
@@ -105,6 +112,12 @@ idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, 
 /* Number of nodes and of stored matrix entries (the stencil sizes I(i) of
  * Sec. 3.1 summed over i). */
 idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz);
+
+/* Number of distinct FP32 entries in the table of idp_config.entry_table
+ * (*n_values = 0: the mixed stage reads per-entry arrays, because the context
+ * is FP64, the table is off, or the mesh has more than 4096 distinct entries).
+ * IDP_ERR_STATE before a mesh is uploaded. */
+idp_status idp_entry_table_size(idp_ctx* ctx, int64_t* n_values);
 
 /* Copies the assembled matrices back in the caller's numbering as CSR with
  * columns sorted by the caller's node id: rowptr (n+1), col (nnz), mij (nnz),

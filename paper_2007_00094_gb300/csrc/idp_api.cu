@@ -1,9 +1,11 @@
 // C ABI of libidp (include/idp.h): context, uploads, stepping, read-back.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,6 +28,7 @@ struct idp_ctx {
   idp::StageBuffers B{};
   idp::StageConfig C{};
   idp::MixedGraph MG{};
+  int64_t n_entry_values = 0;  // size of the mixed stage's entry table (0: per-entry arrays)
   idp::MixedBuffers MB{};
   bool mixed = false;
   std::vector<void*> allocations;
@@ -291,6 +294,7 @@ void idp_config_default(idp_config* cfg) {
   cfg->precision = IDP_PRECISION_FP64;
   cfg->schedule = 0;
   cfg->barrier_spin_limit = 1 << 26;
+  cfg->entry_table = 1;
 }
 
 const char* idp_status_string(idp_status s) {
@@ -366,6 +370,42 @@ extern "C" idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_
 }
 
 namespace {
+// Entry table of the mixed stage (idp_config.entry_table): the distinct FP32
+// tuples (c_x, c_y, c_z, m_ij, |c_ij|, 1/|c_ij|) of all slots, padding
+// included, compared bitwise.  Left off when there are more than
+// kEntryTableMax of them.
+idp_status upload_entry_table(idp_ctx* ctx, const idp::HostEntriesF& E) {
+  const size_t ns = E.cx.size();
+  std::map<std::array<uint32_t, 6>, uint16_t> index;
+  std::vector<uint16_t> code(ns);
+  std::vector<float4> tab;
+  auto bits = [](float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+  };
+  for (size_t p = 0; p < ns; ++p) {
+    const std::array<uint32_t, 6> key = {bits(E.cx[p]), bits(E.cy[p]), bits(E.cz[p]),
+                                         bits(E.m[p]),  bits(E.cn[p]), bits(E.inv_cn[p])};
+    auto it = index.find(key);
+    if (it == index.end()) {
+      if ((int)index.size() == idp::kEntryTableMax) return IDP_OK;  // not a table mesh: per-entry arrays
+      it = index.emplace(key, (uint16_t)index.size()).first;
+      tab.push_back(make_float4(E.cx[p], E.cy[p], E.cz[p], E.m[p]));
+      tab.push_back(make_float4(E.cn[p], E.inv_cn[p], 0.0f, 0.0f));
+    }
+    code[p] = it->second;
+  }
+  uint16_t* dcode;
+  float4* dtab;
+  idp_status st;
+  if ((st = upload(ctx, &dcode, code)) || (st = upload(ctx, &dtab, tab))) return st;
+  ctx->MG.ecode = dcode;
+  ctx->MG.etab = dtab;
+  ctx->n_entry_values = (int64_t)index.size();
+  return IDP_OK;
+}
+
 idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
                        const double* cell_x, const int32_t* node_bc, const double* inflow_state) {
   if (!ctx || !cells || !cell_x || n_nodes <= 0 || n_cells <= 0) return fail(ctx, IDP_ERR_ARG, "bad mesh arguments");
@@ -438,14 +478,37 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
     IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
     IDP_CUDA(ctx, cudaMemset(B.dinv, 0, sizeof(double) * ns));
   } else {
+    // FP32 copies of the entries.  A component of c_ij below 2^-24 of the
+    // largest |c| is assembly rounding of a zero (e.g. c_x between nodes of
+    // equal x on a uniform grid) and beneath FP32 resolution on the matrix's
+    // scale: it becomes an exact zero.
+    double cscale = 0.0;
+    for (size_t p = 0; p < ns; ++p) cscale = std::fmax(cscale, L.cn[p]);
     auto to_float = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
-    float *fcx, *fcy, *fcz, *fm, *fcn, *finv, *fimi;
-    if ((st = upload(ctx, &fcx, to_float(L.cx))) || (st = upload(ctx, &fcy, to_float(L.cy))) ||
-        (st = upload(ctx, &fcz, to_float(L.cz))) || (st = upload(ctx, &fm, to_float(L.mij))) ||
-        (st = upload(ctx, &fcn, to_float(L.cn))) || (st = upload(ctx, &finv, to_float(L.inv_cn))) ||
-        (st = upload(ctx, &fimi, to_float(L.inv_mi))))
-      return st;
-    ctx->MG = idp::MixedGraph{fcx, fcy, fcz, fm, fcn, finv, fimi};
+    auto c_float = [&](const std::vector<double>& v) {
+      std::vector<float> f(v.size());
+      for (size_t p = 0; p < v.size(); ++p) f[p] = std::fabs(v[p]) < cscale * 0x1p-24 ? 0.0f : (float)v[p];
+      return f;
+    };
+    const idp::HostEntriesF E{c_float(L.cx), c_float(L.cy), c_float(L.cz), to_float(L.mij), to_float(L.cn),
+                              to_float(L.inv_cn)};
+    float* fimi;
+    if ((st = upload(ctx, &fimi, to_float(L.inv_mi)))) return st;
+    ctx->MG = idp::MixedGraph{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fimi, nullptr, nullptr};
+    ctx->n_entry_values = 0;
+    if (ctx->cfg.entry_table && (st = upload_entry_table(ctx, E))) return st;
+    if (!ctx->MG.ecode) {
+      float *fcx, *fcy, *fcz, *fm, *fcn, *finv;
+      if ((st = upload(ctx, &fcx, E.cx)) || (st = upload(ctx, &fcy, E.cy)) || (st = upload(ctx, &fcz, E.cz)) ||
+          (st = upload(ctx, &fm, E.m)) || (st = upload(ctx, &fcn, E.cn)) || (st = upload(ctx, &finv, E.inv_cn)))
+        return st;
+      ctx->MG.cx = fcx;
+      ctx->MG.cy = fcy;
+      ctx->MG.cz = fcz;
+      ctx->MG.mij = fm;
+      ctx->MG.cn = fcn;
+      ctx->MG.inv_cn = finv;
+    }
     idp::MixedBuffers& X = ctx->MB;
     if ((st = dalloc(ctx, &X.Uf, 5 * n)) || (st = dalloc(ctx, &X.Q, idp::kNodeQ * n)) || (st = dalloc(ctx, &X.d, ns)) ||
         (st = dalloc(ctx, &X.dinv, ns)) || (st = dalloc(ctx, &X.P, 5 * ns)) || (st = dalloc(ctx, &X.l[0], ns)) ||
@@ -466,6 +529,12 @@ idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz) {
   if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
   if (n_nodes) *n_nodes = ctx->M.n;
   if (nnz) *nnz = ctx->M.rowptr[ctx->M.n];
+  return IDP_OK;
+}
+
+idp_status idp_entry_table_size(idp_ctx* ctx, int64_t* n_values) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (n_values) *n_values = ctx->n_entry_values;
   return IDP_OK;
 }
 

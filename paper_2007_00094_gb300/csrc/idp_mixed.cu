@@ -298,7 +298,8 @@ __device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGrap
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
     const uint8_t fl = G.flags[p];
-    const float cx = M.cx[p], cy = M.cy[p], cz = M.cz[p];
+    const EntryF e = entry_f(M, p);
+    const float cx = e.cx, cy = e.cy, cz = e.cz;
     const SideF sj = load_side_f(U, Q, n, j);
     const float s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
     float fj[kFields], fi[kFields];
@@ -317,18 +318,18 @@ __device__ __forceinline__ void row_edge_m(const DeviceGraph& G, const MixedGrap
     b3 += df[3];
     b4 += df[4];
     if (fl & kEntryUpper) {
-      const float nc = M.cn[p];
+      const float nc = e.cn;
       float dij = 0.0f;
       if (nc > 0.0f) {
-        const float inv = M.inv_cn[p];
+        const float inv = e.inv_cn;
         dij = lambda_max_f(cx * inv, cy * inv, cz * inv, si, sj) * nc;
       }
       if (!(fl & kEntrySkew)) {
-        const int64_t pt = G.tpos[p];
-        const float nt = M.cn[pt];
+        const EntryF et = entry_f(M, G.tpos[p]);
+        const float nt = et.cn;
         if (nt > 0.0f) {
-          const float inv = M.inv_cn[pt];
-          dij = fmaxf(dij, lambda_max_f(M.cx[pt] * inv, M.cy[pt] * inv, M.cz[pt] * inv, sj, si) * nt);
+          const float inv = et.inv_cn;
+          dij = fmaxf(dij, lambda_max_f(et.cx * inv, et.cy * inv, et.cz * inv, sj, si) * nt);
         }
       }
       d[p] = dij;
@@ -505,7 +506,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
       continue;
     }
     float pij[kFields];
-    const float m = M.mij[p];
+    const float m = entry_f(M, p).m;
     const float b_ij = -m * M.inv_mi[j];
     const float b_ji = -m * inv_mi;
     const float dij = d[p];

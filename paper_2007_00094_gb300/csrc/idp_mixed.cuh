@@ -1,6 +1,8 @@
 // FP32-mixed stage: FP32 copies of the per-entry matrices and FP32 work
 // buffers next to the FP64 state buffers of StageBuffers.
 #pragma once
+#include <vector>
+
 #include "idp_stage.cuh"
 
 namespace idp {
@@ -13,7 +15,47 @@ struct MixedGraph {
   const float* cn;
   const float* inv_cn;
   const float* inv_mi;  // per node
+  // Entry table (nullptr: per-entry arrays above): slot p holds the index
+  // ecode[p] of its values (cx, cy, cz, m_ij) = etab[2 ecode[p]],
+  // (|c|, 1/|c|, 0, 0) = etab[2 ecode[p] + 1].
+  const uint16_t* ecode;
+  const float4* etab;
 };
+
+constexpr int kEntryTableMax = 4096;
+
+// Host-side FP32 copies of the per-slot entries (SELL order).
+struct HostEntriesF {
+  std::vector<float> cx, cy, cz, m, cn, inv_cn;
+};
+
+// FP32 values of stored entry p (Sec. 3.1 matrices) from the table or the
+// per-entry arrays; the compiler drops the loads of unused fields.
+struct EntryF {
+  float cx, cy, cz, m, cn, inv_cn;
+};
+
+__device__ __forceinline__ EntryF entry_f(const MixedGraph& M, int64_t p) {
+  EntryF e;
+  if (M.ecode) {
+    const int c = M.ecode[p];
+    const float4 a = __ldg(&M.etab[2 * c]), b = __ldg(&M.etab[2 * c + 1]);
+    e.cx = a.x;
+    e.cy = a.y;
+    e.cz = a.z;
+    e.m = a.w;
+    e.cn = b.x;
+    e.inv_cn = b.y;
+  } else {
+    e.cx = M.cx[p];
+    e.cy = M.cy[p];
+    e.cz = M.cz[p];
+    e.m = M.mij[p];
+    e.cn = M.cn[p];
+    e.inv_cn = M.inv_cn[p];
+  }
+  return e;
+}
 
 struct MixedBuffers {
   float* Uf;     // 5n: FP32 copy of the stage input

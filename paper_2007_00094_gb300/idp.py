@@ -32,7 +32,8 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_step", "idp_euler_step", "idp_synchronize", "idp_get_time", "idp_set_time", "idp_get_field",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
-            "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad"]
+            "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad",
+            "idp_entry_table_size"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -41,7 +42,8 @@ KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "f
 class IdpConfig(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter_passes", C.c_int), ("newton_max", C.c_int),
                 ("newton_tol", C.c_double), ("newton_eps", C.c_double), ("precision", C.c_int),
-                ("schedule", C.c_int), ("barrier_spin_limit", C.c_int64), ("relax", C.c_int)]
+                ("schedule", C.c_int), ("barrier_spin_limit", C.c_int64), ("relax", C.c_int),
+                ("entry_table", C.c_int)]
 
 
 class BoundsReport(C.Structure):
@@ -82,6 +84,7 @@ def load(path: str = LIB_PATH):
     L.idp_upload_mesh_hex.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
     L.idp_upload_mesh_quad.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
     L.idp_mesh_info.argtypes = [_vp, _i64p, _i64p]
+    L.idp_entry_table_size.argtypes = [_vp, _i64p]
     L.idp_get_matrices.argtypes = [_vp, _i64p, _i64p, _dp, _dp, _dp]
     L.idp_init_state.argtypes = [_vp, _vp, C.c_int]
     L.idp_get_state.argtypes = [_vp, _vp, C.c_int]
@@ -231,6 +234,12 @@ class Solver:
         if name == "tau_max":
             return float(out[0])
         return out.reshape(shapes[name]) if name in shapes else out
+
+    def entry_table_size(self) -> int:
+        """Distinct FP32 entries in the mixed stage's entry table (0: per-entry arrays)."""
+        v = C.c_int64(0)
+        _check(self._ctx, load().idp_entry_table_size(self._ctx, C.byref(v)))
+        return int(v.value)
 
     def matrices(self):
         n, nnz = self.n, self.nnz

@@ -130,3 +130,37 @@ def test_mixed_keeps_the_discretization_error_on_sod():
         assert s.check_bounds()[0] == 0
     assert err[0] < 0.015 and err[1] < 0.015
     assert abs(err[1] - err[0]) <= 0.01 * err[0], err
+
+
+@pytest.mark.parametrize("case", ["slip_cube", "periodic_vortex", "rect2d", "jittered"])
+def test_entry_table_gives_bitwise_the_per_entry_result(case):
+    """The FP32 entries stored as 16-bit indices into a table of the distinct
+    values (uniform grids) give bitwise the result of per-entry arrays; a
+    jittered mesh has too many distinct entries and keeps the arrays."""
+    from paper_2007_00094_gb300 import workloads as W
+    if case == "slip_cube":
+        mesh = W.sod_cube_mesh(20)
+        U = W.sod_state(mesh)
+    elif case == "periodic_vortex":
+        mesh = W.vortex_mesh(18)
+        U = W.bumpy_vortex_state(mesh)
+    elif case == "rect2d":
+        mesh = W.rect_mesh((40, 30), periodic=(False, True))
+        U = W.riemann_state(mesh.x, (1.0, (0.2, 0.1, 0.0), 1.0), (0.3, (-0.4, 0.2, 0.0), 0.2),
+                            normal=(0.6, 0.8, 0.0), point=(0.5, 0.5, 0.0))
+    else:
+        mesh = W.box_mesh((20, 18, 16), periodic=(False, False, False), jitter=0.2, seed=4)
+        U = W.sod_state(mesh)
+    out, sizes = [], []
+    for table in (1, 0):
+        s = _solver(mesh, precision=1, entry_table=table)
+        sizes.append(s.entry_table_size())
+        s.init_state(U)
+        s.step(4)
+        s.synchronize()
+        out.append(s.get_state())
+    if case == "jittered":
+        assert sizes == [0, 0]
+    else:
+        assert 0 < sizes[0] <= 729 and sizes[1] == 0
+    np.testing.assert_array_equal(out[0], out[1])
