@@ -25,6 +25,13 @@ __device__ __forceinline__ double ipow(double w) {
 // corrected with the second-order series of
 // (1 - delta)^(-1/K) = 1 + delta/K + (K+1) delta^2/(2K^2) + O(delta^3), where
 // delta = 1 - x w0^K; the neglected term is ~delta^3 < 1e-17 for K <= 12.
+// Seed for x outside the normal float range (out of line, so that its
+// conversions are not executed speculatively on the common path).
+template <int K>
+__device__ __noinline__ double inv_root_seed_wide(double x) {
+  return (double)powf((float)x, -1.0f / (float)K);
+}
+
 template <int K>
 __device__ __forceinline__ double inv_root(double x) {
   double w0;
@@ -37,7 +44,7 @@ __device__ __forceinline__ double inv_root(double x) {
       const unsigned int we = ((wb >> 23) & 0xffu) - 127u + 1023u;
       w0 = __hiloint2double((int)((we << 20) | ((wb & 0x7fffffu) >> 3)), (int)((wb & 7u) << 29));
     } else {
-      w0 = (double)powf((float)x, -1.0f / (float)K);
+      w0 = inv_root_seed_wide<K>(x);
     }
   }
   const double delta = 1.0 - x * ipow<K>(w0);
@@ -199,15 +206,16 @@ __device__ __forceinline__ double psi_slack(double rho_eps, double phi_term) {
 
 // Double to float rounded toward zero by bit arithmetic (integer pipe): the
 // sign, the exponent rebiased and the top 23 mantissa bits; relative error
-// below 2^-23.  Zero maps to zero; doubles outside the normal float range
-// take the conversion instruction.
+// below 2^-23.  Zero maps to zero.  A double outside the normal float range
+// maps to NaN, which fails every test of the FP32 pre-check below, so such
+// inputs take the FP64 path (no conversion instruction, whose FP64-pipe cost
+// the compiler would otherwise pay speculatively on every call).
 __device__ __forceinline__ float to_float_rz(double x) {
   const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
   const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
   if (e > 0 && e < 255)
     return __uint_as_float((hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
-  if (((hi << 1) | lo) == 0u) return 0.0f;
-  return __double2float_rz(x);
+  return ((hi << 1) | lo) == 0u ? 0.0f : __uint_as_float(0x7fc00000u);
 }
 
 // FP32 pre-check of the FP64 limiter's acceptance test.  Per row, Psi(0) =

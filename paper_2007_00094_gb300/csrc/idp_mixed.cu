@@ -174,6 +174,19 @@ __device__ __forceinline__ float psi_error_bound(const PsiAnchor& a, const PsiLi
   return 5.9604645e-8f * (7.0f * S + fabsf(a.psi0) + 7.0f * tg + 5.0f * th + a.phi_pow0 * dq);
 }
 
+// FP64 test of the entropy bound at U + tP (Reading A30).  Out of line and
+// with scalar arguments: it runs on few entries, and inlined the compiler
+// would convert P and t to FP64 (FP64-pipe instructions) on every entry.
+__device__ __noinline__ bool psi_holds_fp64(double u0, double u1, double u2, double u3, double u4, float p0,
+                                            float p1, float p2, float p3, float p4, float t, double phi_min) {
+  const double td = (double)t;
+  const double v0 = u0 + td * (double)p0, v1 = u1 + td * (double)p1, v2 = u2 + td * (double)p2;
+  const double v3 = u3 + td * (double)p3, v4 = u4 + td * (double)p4;
+  const double re = v0 * v4 - 0.5 * (v1 * v1 + v2 * v2 + v3 * v3);
+  const double pw = phi_min * pow_12_5(v0);
+  return v0 > 0.0 && re - pw >= -1e-13 * (fabs(re) + fabs(pw));
+}
+
 // limiter.compute of Alg. 2 for the mixed path.  U (FP64) is the row state,
 // P (FP32) the direction.  Returns t in [0, 1].
 __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor& A, const float* P, double phi_min,
@@ -236,14 +249,9 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
   // FP64 check of the entropy bound where the FP32 evaluation cannot
   // guarantee it: psiAtL >= 0 means Psi(t) >= margin - error, so the check is
   // needed only when the rounding bound reaches the margin
-  if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, lgL, qL) >= A.margin)) {
-    double V[kFields];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) V[f] = U[f] + (double)tL * (double)P[f];
-    const double re = V[0] * V[4] - 0.5 * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
-    const double pw = phi_min * pow_12_5(V[0]);
-    if (!(V[0] > 0.0) || re - pw < -1e-13 * (fabs(re) + fabs(pw))) tL = 0.0f;
-  }
+  if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, lgL, qL) >= A.margin) &&
+      !psi_holds_fp64(U[0], U[1], U[2], U[3], U[4], P[0], P[1], P[2], P[3], P[4], tL, phi_min))
+    tL = 0.0f;
   return tL;
 }
 
