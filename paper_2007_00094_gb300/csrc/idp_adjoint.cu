@@ -737,7 +737,11 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
         const double nc = G.cn[p];
         bool transposed = false;
         if (!(G.flags[p] & kEntrySkew) && G.cn[pt] > 0.0) {
-          const double d1 = nc > 0.0 ? lambda_max(cx * G.inv_cn[p], cy * G.inv_cn[p], cz * G.inv_cn[p], si, sj) * nc
+          // d1 as the forward sweep forms it (normal speeds from m.c)
+          const double ic = G.inv_cn[p];
+          const double d1 = nc > 0.0 ? lambda_max_u(normal_speed(m_dot_c(si.mx, si.my, si.mz, cx, cy, cz), si.inv_rho, ic),
+                                                    normal_speed(m_dot_c(sj.mx, sj.my, sj.mz, cx, cy, cz), sj.inv_rho, ic),
+                                                    si, sj) * nc
                                      : 0.0;
           const double it = G.inv_cn[pt];
           const double d2 = lambda_max(G.cx[pt] * it, G.cy[pt] * it, G.cz[pt] * it, sj, si) * G.cn[pt];

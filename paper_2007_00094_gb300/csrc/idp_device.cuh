@@ -110,9 +110,14 @@ __device__ __forceinline__ bool is_pos_zero(double x) { return __double2hiint(x)
 // operation sequence pinned by rounding intrinsics so that equal states give
 // bitwise equal fluxes (differences f_j - f_i then vanish exactly, as in the
 // oracle).
+// m . c with a pinned operation sequence (the f[0] of flux_dot)
+__device__ __forceinline__ double m_dot_c(double m1, double m2, double m3, double cx, double cy, double cz) {
+  return __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
+}
+
 __device__ __forceinline__ void flux_dot(double m1, double m2, double m3, double inv_rho, double p, double h,
                                          double cx, double cy, double cz, double* f) {
-  const double mc = __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
+  const double mc = m_dot_c(m1, m2, m3, cx, cy, cz);
   f[0] = mc;
   f[1] = __fma_rn(p, cx, __dmul_rn(__dmul_rn(m1, inv_rho), mc));
   f[2] = __fma_rn(p, cy, __dmul_rn(__dmul_rn(m2, inv_rho), mc));
@@ -125,7 +130,7 @@ __device__ __forceinline__ void flux_dot(double m1, double m2, double m3, double
 // so that the result is bitwise that of flux_dot)
 __device__ __forceinline__ void flux_dot_v(double m1, double m2, double m3, double v1, double v2, double v3, double p,
                                            double h, double cx, double cy, double cz, double* f) {
-  const double mc = __fma_rn(m3, cz, __fma_rn(m2, cy, __dmul_rn(m1, cx)));
+  const double mc = m_dot_c(m1, m2, m3, cx, cy, cz);
   f[0] = mc;
   f[1] = __fma_rn(p, cx, __dmul_rn(v1, mc));
   f[2] = __fma_rn(p, cy, __dmul_rn(v2, mc));
@@ -139,9 +144,8 @@ __device__ __forceinline__ void flux_dot_v(double m1, double m2, double m3, doub
 // projection leaves the pressure unchanged (E~ - m~^2/(2 rho) = epsilon).
 // psi is needed at p_max, where only the side with the smaller pressure
 // contributes (its shock branch); the other side's f vanishes.
-__device__ __forceinline__ double lambda_max(double nx, double ny, double nz, const Side& L, const Side& R) {
-  const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
-  const double uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
+// lambda_max_u takes the normal velocities u_L = m_L.n / rho_L, u_R directly.
+__device__ __forceinline__ double lambda_max_u(double uL, double uR, const Side& L, const Side& R) {
   double num = L.c + R.c - 0.2 * (uR - uL);
   num = positive_k(num) ? num : 0.0;  // vacuum: p~* = 0
   const double x = num / (L.c * L.pm + R.c * R.pm);
@@ -166,6 +170,19 @@ __device__ __forceinline__ double lambda_max(double nx, double ny, double nz, co
   const double lam3 = uR + R.c * (positive_k(zR) ? sqrt(1.0 + k * zR) : 1.0);
   const double a = negative_k(-lam1) ? 0.0 : -lam1, b = negative_k(lam3) ? 0.0 : lam3;
   return max_k(a, b);
+}
+
+__device__ __forceinline__ double lambda_max(double nx, double ny, double nz, const Side& L, const Side& R) {
+  const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
+  const double uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
+  return lambda_max_u(uL, uR, L, R);
+}
+
+// u = m.n / rho with n = c/|c| from m.c (as m_dot_c gives it), 1/rho and
+// 1/|c|: the normal velocities of lambda_max_u for the orientation c_ij,
+// reusing the m.c of the flux contractions
+__device__ __forceinline__ double normal_speed(double mc, double inv_rho, double inv_cn) {
+  return __dmul_rn(__dmul_rn(mc, inv_rho), inv_cn);
 }
 
 struct LimiterParams {

@@ -117,7 +117,7 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
       double dij = 0.0;
       if (positive_k(nc)) {
         const double inv = G.inv_cn[p];
-        dij = lambda_max(cx * inv, cy * inv, cz * inv, si, sj) * nc;
+        dij = lambda_max_u(normal_speed(fi[0], si.inv_rho, inv), normal_speed(fj[0], sj.inv_rho, inv), si, sj) * nc;
       }
       if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
         const int64_t pt = G.tpos[p];
