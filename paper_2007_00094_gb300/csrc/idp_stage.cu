@@ -97,16 +97,21 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
     const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
     const Side sj = load_side(U, Q, n, j);
     const double s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
-    double fj[kFields], fi[kFields];
-    flux_dot_v(sj.mx, sj.my, sj.mz, Q[kQVx * n + j], Q[kQVy * n + j], Q[kQVz * n + j], sj.p, h_j, cx, cy, cz, fj);
-    flux_dot_v(si.mx, si.my, si.mz, vxi, vyi, vzi, si.p, h_i, cx, cy, cz, fi);
-    a += (s_j - s_i) * fj[0];
+    // (f_j - f_i).c_ij formed from m.c of both sides and the pressure
+    // difference: every term is rounded alike on both sides, so equal states
+    // still give exact zeros, with fewer FP64 operations than two fluxes
+    const double mcj = m_dot_c(sj.mx, sj.my, sj.mz, cx, cy, cz);
+    const double mci = m_dot_c(si.mx, si.my, si.mz, cx, cy, cz);
+    const double dp = sj.p - si.p;
     double df[kFields];
+    df[0] = mcj - mci;
+    df[1] = fma(dp, cx, __dmul_rn(Q[kQVx * n + j], mcj) - __dmul_rn(vxi, mci));
+    df[2] = fma(dp, cy, __dmul_rn(Q[kQVy * n + j], mcj) - __dmul_rn(vyi, mci));
+    df[3] = fma(dp, cz, __dmul_rn(Q[kQVz * n + j], mcj) - __dmul_rn(vzi, mci));
+    df[4] = __dmul_rn(h_j, mcj) - __dmul_rn(h_i, mci);
+    a += (s_j - s_i) * mcj;
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      df[f] = fj[f] - fi[f];
-      dF[f * ns + p] = df[f];
-    }
+    for (int f = 0; f < kFields; ++f) dF[f * ns + p] = df[f];
     b0 += df[0];
     b1 += df[1];
     b2 += df[2];
@@ -117,7 +122,7 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
       double dij = 0.0;
       if (positive_k(nc)) {
         const double inv = G.inv_cn[p];
-        dij = lambda_max_u(normal_speed(fi[0], si.inv_rho, inv), normal_speed(fj[0], sj.inv_rho, inv), si, sj) * nc;
+        dij = lambda_max_u(normal_speed(mci, si.inv_rho, inv), normal_speed(mcj, sj.inv_rho, inv), si, sj) * nc;
       }
       if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
         const int64_t pt = G.tpos[p];
@@ -204,7 +209,7 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
   double ui[kFields];
   load5(U, n, r, ui);
   const double a_i = alpha[r];
-  const double two_tau_m = 2.0 * tau * G.inv_mi[r];
+  const double tau_m = tau * G.inv_mi[r];
   double ul[kFields], rr[kFields];
   {
     double fs[kFields];  // f_i . s_i
@@ -216,7 +221,11 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
       rr[f] = -fs[f];
     }
   }
-  double rho_min = INFINITY, rho_max = -INFINITY, phi_min = INFINITY;
+  // The bar states are formed doubled, 2 Ubar_ij = U_i + U_j - (f_j - f_i).c_ij / d_ij,
+  // with half the coefficient: scaling by 2 commutes with rounding, so U^L and
+  // the bounds are bitwise those of 2 tau d_ij / m_i times Ubar_ij, and the
+  // multiplications by 1/2 drop out.
+  double rho_min2 = INFINITY, rho_max2 = -INFINITY, phi_min = INFINITY;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
@@ -229,16 +238,16 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
 #pragma unroll
     for (int f = 0; f < kFields; ++f) rr[f] += -df[f] + dH * (uj[f] - ui[f]);
     if (!dzero(dij)) {
-      const double inv2d = dinv[p];
-      const double coef = two_tau_m * dij;
-      double ub[kFields];
+      const double inv_d = 2.0 * dinv[p];  // 1/d_ij
+      const double coef_h = tau_m * dij;   // (2 tau d_ij / m_i) / 2
+      double ub2[kFields];
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        ub[f] = 0.5 * (ui[f] + uj[f]) - df[f] * inv2d;
-        ul[f] += coef * ub[f];
+        ub2[f] = fma(-df[f], inv_d, ui[f] + uj[f]);
+        ul[f] = fma(coef_h, ub2[f], ul[f]);
       }
-      rho_min = min_k(rho_min, ub[0]);
-      rho_max = max_k(rho_max, ub[0]);
+      rho_min2 = min_k(rho_min2, ub2[0]);
+      rho_max2 = max_k(rho_max2, ub2[0]);
     }
     phi_min = min_k(phi_min, Q[kQPhi * n + j]);
   }
@@ -247,6 +256,7 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
     UL[f * n + r] = ul[f];
     R[f * n + r] = rr[f];
   }
+  double rho_min = 0.5 * rho_min2, rho_max = 0.5 * rho_max2;
   if (G.relax) {  // bound relaxation (off unless configured)
     const double q = G.relax[r];
     rho_min *= 1.0 - q;
