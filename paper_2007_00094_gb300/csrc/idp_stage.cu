@@ -222,9 +222,8 @@ __device__ __forceinline__ void row_low_order(const DeviceGraph& G, const StageC
     }
   }
   // The bar states are formed doubled, 2 Ubar_ij = U_i + U_j - (f_j - f_i).c_ij / d_ij,
-  // with half the coefficient: scaling by 2 commutes with rounding, so U^L and
-  // the bounds are bitwise those of 2 tau d_ij / m_i times Ubar_ij, and the
-  // multiplications by 1/2 drop out.
+  // against half the coefficient, tau d_ij / m_i: the same products (scaling by
+  // 2 is exact) without the multiplications by 1/2; the bounds are halved once.
   double rho_min2 = INFINITY, rho_max2 = -INFINITY, phi_min = INFINITY;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
@@ -300,6 +299,7 @@ __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const Stage
   const double a_i = alpha[r];
   const double inv_mi = G.inv_mi[r];
   const double scale = tau * inv_mi * (double)(len - 1);  // tau / (m_i lambda_i)
+  const double scale_i = scale * inv_mi;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
@@ -312,14 +312,17 @@ __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const Stage
     double uj[kFields], rj[kFields], pij[kFields];
     load5(U, n, j, uj);
     load5(R, n, j, rj);
+    // the coefficients scaled once per entry instead of each field:
+    // scale b_ij = -scale m_ij / m_j, scale b_ji = -m_ij scale / m_i,
+    // scale (d^H_ij - d^L_ij)
     const double m = G.mij[p];
-    const double b_ij = -m * G.inv_mi[j];
-    const double b_ji = -m * inv_mi;
+    const double sb_ij = -(scale * m) * G.inv_mi[j];
+    const double sb_ji = -m * scale_i;
     const double dij = d[p];
-    const double dd = dij * (a_i + alpha[j]) * 0.5 - dij;  // d^H_ij - d^L_ij
+    const double sdd = scale * (dij * (a_i + alpha[j]) * 0.5 - dij);
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
-      pij[f] = scale * (b_ij * rj[f] - b_ji * ri[f] + dd * (uj[f] - ui[f]));
+      pij[f] = fma(sb_ij, rj[f], fma(-sb_ji, ri[f], sdd * (uj[f] - ui[f])));
       P[f * ns + p] = pij[f];
     }
     l[p] = limiter(ul, pij, rmin, rmax, pmin, C.lim, &pre);
