@@ -42,10 +42,10 @@ FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "fl
 # work of the FP64 roofline; the paper's per-step counts above overstate what
 # these kernels execute (lambda_max once per unordered edge, powers without
 # pow, tests on 32-bit words), so a rate from them can exceed the pipe.
-FP64_FLOP_PER_NNZ_EXECUTED = {"edge": 84.0, "low_order": 55.0, "flux_limit": 51.1, "limiter_pass": 13.4}
+FP64_FLOP_PER_NNZ_EXECUTED = {"edge": 74.1, "low_order": 51.0, "flux_limit": 48.3, "limiter_pass": 13.5}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, % of active cycles) of
 # the same capture: the pipe also issues compares, conversions and min/max.
-FP64_PIPE_BUSY_NCU = {"edge": 0.876, "low_order": 0.870, "flux_limit": 0.873, "limiter_pass": 0.704}
+FP64_PIPE_BUSY_NCU = {"edge": 0.868, "low_order": 0.892, "flux_limit": 0.878, "limiter_pass": 0.664}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s; a dependent-free DFMA
 # stream measured 1.197 TFLOP/s at 1.97 GHz on this machine).
@@ -57,8 +57,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP64 at h = 1/80 (17,679,673 entries) -> h = 1/120;
 # FP32-mixed k_limiter_pass_m 1.976 GB at 96^3 (23,393,656 entries) -> 128^3.
 NCU_TRAFFIC_BYTES = {k: v * 59373973 / 17679673 for k, v in
-                     {"edge": 1.583067e9, "flux_limit": 1.265618e9, "low_order": 1.210931e9,
-                      "limiter_pass": 2.497277e9}.items()}
+                     {"edge": 1.583546e9, "flux_limit": 1.265060e9, "low_order": 1.210403e9,
+                      "limiter_pass": 2.512997e9}.items()}
 NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 1.976342e9 * 55742968 / 23393656}
 
 
