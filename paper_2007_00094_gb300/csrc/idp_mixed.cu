@@ -146,14 +146,31 @@ __device__ __forceinline__ PsiLine make_line(const PsiAnchor& a, const float* P)
   return L;
 }
 
-// Psi(t) - margin; also dPsi/dt and lg = log1p(s), q (for the error bound)
-__device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, float t, float* dpsi, float* lg_out,
+// Binomial coefficients C(12/5, k), k = 1..7, of (1 + s)^(12/5) - 1
+constexpr float kQ1 = 2.4f, kQ2 = 1.68f, kQ3 = 0.224f, kQ4 = -0.0336f, kQ5 = 0.010752f, kQ6 = -0.0046592f,
+                kQ7 = 0.00239616f;
+
+// Psi(t) - margin; also dPsi/dt, q = (1 + s)^(12/5) - 1 and fe, the error of
+// the evaluation of q in units of u (for the error bound).  For |s| <= 1/8 q
+// is the binomial series to s^7 by Horner's rule: rounding (seven fused
+// steps and the coefficients' own rounding) stays below 15 u sum_k |C_k||s|^k
+// <= 15 * 2.62 u |s|, truncation below 0.0015 |s|^8 / (1 - 0.075) < 0.02 u |s|,
+// so fe = 40 |s|.  Otherwise q = expm1(2.4 log1p(s)) with an ulp in each
+// function amplified by 2.4 (1 + q): fe = 4.8 (1 + q) |log1p(s)|.
+__device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, float t, float* dpsi, float* fe_out,
                                         float* q_out) {
   const float s = t * L.sr;  // > -1 inside the density interval
-  const float lg = log1pf(s);
-  const float q = expm1f(2.4f * lg);
+  float q, fe;
+  if (fabsf(s) <= 0.125f) {
+    q = s * fmaf(s, fmaf(s, fmaf(s, fmaf(s, fmaf(s, fmaf(s, kQ7, kQ6), kQ5), kQ4), kQ3), kQ2), kQ1);
+    fe = 40.0f * fabsf(s);
+  } else {
+    const float lg = log1pf(s);
+    q = expm1f(2.4f * lg);
+    fe = 4.8f * (1.0f + q) * fabsf(lg);
+  }
   if (dpsi) *dpsi = fmaf(2.0f * t, L.h, L.g) - a.phi_pow0 * 2.4f * ((1.0f + q) / (1.0f + s)) * L.sr;
-  *lg_out = lg;
+  *fe_out = fe;
   *q_out = q;
   return fmaf(t, fmaf(t, L.h, L.g), a.psi0) - fmaf(a.phi_pow0, q, a.margin);
 }
@@ -161,16 +178,16 @@ __device__ __forceinline__ float psi_at(const PsiAnchor& a, const PsiLine& L, fl
 // Bound on |psi_at(t) - (Psi(t) - margin)|, Psi in exact arithmetic along
 // U + tP with the FP64 U and the FP32 P, from the rounding of every FP32
 // operation (unit roundoff u = 2^-24): the FP32 copies of U and Psi(0), g and
-// h (a few roundings of their terms each), s = t P_rho/rho, log1p/expm1
-// (about one ulp each, amplified by 2.4 (1 + q) through q = (1 + s)^2.4 - 1)
-// and the seven operations that combine them, each at most u times the sum
-// S of the magnitudes involved.
-__device__ __forceinline__ float psi_error_bound(const PsiAnchor& a, const PsiLine& L, float t, float lg, float q) {
+// h (a few roundings of their terms each), s = t P_rho/rho (amplified by
+// dq/ds = 2.4 (1 + q)/(1 + s)), the evaluation of q (fe from psi_at) and the
+// seven operations that combine them, each at most u times the sum S of the
+// magnitudes involved.
+__device__ __forceinline__ float psi_error_bound(const PsiAnchor& a, const PsiLine& L, float t, float fe, float q) {
   const float s = t * L.sr;
   const float tg = t * L.gabs, th = t * t * L.habs;
   const float qa = fabsf(q);
   const float S = fabsf(a.psi0) + tg + th + a.phi_pow0 * qa + a.margin;
-  const float dq = (1.0f + q) * (4.8f * fabsf(lg) + 7.2f * fabsf(s) / fmaxf(1.0f + s, 1e-30f)) + 3.0f * qa;
+  const float dq = fe + (1.0f + q) * 7.2f * fabsf(s) / fmaxf(1.0f + s, 1e-30f) + 3.0f * qa;
   return 5.9604645e-8f * (7.0f * S + fabsf(a.psi0) + 7.0f * tg + 5.0f * th + a.phi_pow0 * dq);
 }
 
@@ -201,21 +218,21 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
   tR = fminf(fmaxf(tR, 0.0f), 1.0f);
   float tL = 0.0f;
   const PsiLine L = make_line(A, P);
-  float psiL = 0.0f, dpsiL = 0.0f, psiAtL, lgL = 0.0f, qL = 0.0f;
+  float psiL = 0.0f, dpsiL = 0.0f, psiAtL, feL = 0.0f, qL = 0.0f;
   bool haveL = false, accepted = false;
   for (int step = 0; step < prm.newton_max; ++step) {
-    float dpsiR, lgR, qR;
-    const float psiR = psi_at(A, L, tR, &dpsiR, &lgR, &qR);
+    float dpsiR, feR, qR;
+    const float psiR = psi_at(A, L, tR, &dpsiR, &feR, &qR);
     if (psiR >= 0.0f) {
       tL = tR;
       psiAtL = psiR;
-      lgL = lgR;
+      feL = feR;
       qL = qR;
       accepted = true;
       break;
     }
     if (!haveL) {
-      psiL = psi_at(A, L, tL, &dpsiL, &lgL, &qL);
+      psiL = psi_at(A, L, tL, &dpsiL, &feL, &qL);
       haveL = true;
     }
     const float tol = (float)prm.newton_tol * (A.psi0 + A.phi_pow0);
@@ -230,12 +247,12 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
     float nR = tR - 2.0f * psiR / (dpsiR - sqrtf(lamR));
     if (!(nL >= tL)) nL = tL;
     if (!(nL <= tR)) nL = tR;
-    float dpsiN, lgN, qN;
-    const float psiN = psi_at(A, L, nL, &dpsiN, &lgN, &qN);
+    float dpsiN, feN, qN;
+    const float psiN = psi_at(A, L, nL, &dpsiN, &feN, &qN);
     if (psiN >= 0.0f) {
       psiL = psiN;
       dpsiL = dpsiN;
-      lgL = lgN;
+      feL = feN;
       qL = qN;
     } else {
       nL = tL;
@@ -245,11 +262,11 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
     tL = nL;
     tR = nR;
   }
-  if (!accepted) psiAtL = haveL ? psiL : psi_at(A, L, tL, nullptr, &lgL, &qL);
+  if (!accepted) psiAtL = haveL ? psiL : psi_at(A, L, tL, nullptr, &feL, &qL);
   // FP64 check of the entropy bound where the FP32 evaluation cannot
   // guarantee it: psiAtL >= 0 means Psi(t) >= margin - error, so the check is
   // needed only when the rounding bound reaches the margin
-  if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, lgL, qL) >= A.margin) &&
+  if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, feL, qL) >= A.margin) &&
       !psi_holds_fp64(U[0], U[1], U[2], U[3], U[4], P[0], P[1], P[2], P[3], P[4], tL, phi_min))
     tL = 0.0f;
   return tL;
