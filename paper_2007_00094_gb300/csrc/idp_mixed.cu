@@ -106,9 +106,11 @@ struct PsiAnchor {
   float margin;      // admissibility margin of the FP32 line search
   float gap_max;     // rho_max - rho(U), rounded toward zero
   float gap_min;     // rho_min - rho(U), rounded toward zero
+  float tol;         // Newton stopping threshold of Alg. 2 for this row
 };
 
-__device__ __forceinline__ PsiAnchor make_anchor(const double* U, double rho_min, double rho_max, double phi_min) {
+__device__ __forceinline__ PsiAnchor make_anchor(const double* U, double rho_min, double rho_max, double phi_min,
+                                                 double newton_tol) {
   PsiAnchor a;
 #pragma unroll
   for (int f = 0; f < kFields; ++f) a.u[f] = (float)U[f];
@@ -123,6 +125,7 @@ __device__ __forceinline__ PsiAnchor make_anchor(const double* U, double rho_min
   // density gaps in FP64, rounded toward zero so that FP32 cuts stay inside
   a.gap_max = __double2float_rz(rho_max - U[0]);
   a.gap_min = __double2float_rz(rho_min - U[0]);
+  a.tol = (float)newton_tol * (a.psi0 + a.phi_pow0);
   return a;
 }
 
@@ -191,22 +194,46 @@ __device__ __forceinline__ float psi_error_bound(const PsiAnchor& a, const PsiLi
   return 5.9604645e-8f * (7.0f * S + fabsf(a.psi0) + 7.0f * tg + 5.0f * th + a.phi_pow0 * dq);
 }
 
-// FP64 test of the entropy bound at U + tP (Reading A30).  Out of line and
-// with scalar arguments: it runs on few entries, and inlined the compiler
-// would convert P and t to FP64 (FP64-pipe instructions) on every entry.
-__device__ __noinline__ bool psi_holds_fp64(double u0, double u1, double u2, double u3, double u4, float p0,
-                                            float p1, float p2, float p3, float p4, float t, double phi_min) {
-  const double td = (double)t;
-  const double v0 = u0 + td * (double)p0, v1 = u1 + td * (double)p1, v2 = u2 + td * (double)p2;
-  const double v3 = u3 + td * (double)p3, v4 = u4 + td * (double)p4;
+// Float to double by bit arithmetic on the integer pipe, exact for every
+// float (subnormals normalised with a leading-zero count).  The conversion
+// instruction runs on the FP64 pipe, and the compiler executes the
+// conversions of the rarely taken FP64 check below speculatively on every
+// entry (ncu: ~6 per entry), which this form keeps off the FP64 pipe.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned int b = __float_as_uint(x), sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+  unsigned int m = b & 0x7fffffu, de;
+  if (e == 0u) {
+    if (m == 0u) return __hiloint2double((int)sign, 0);
+    const int z = __clz((int)m);
+    m = (m << (z - 8)) & 0x7fffffu;
+    de = 905u - (unsigned int)z;
+  } else {
+    de = e == 255u ? 2047u : e + 896u;
+  }
+  return __hiloint2double((int)(sign | (de << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// FP64 test of the entropy bound at U + tP (Reading A30), run on few entries.
+// The row state is read here from the state array (field-major, n nodes, row
+// r) rather than passed in: with five doubles held live in the caller across
+// the limiter loop, ncu counted ~5 FP64-pipe conversions (F2F) per entry in
+// the loop, and the flux-limit kernel ran 19 % slower.
+__device__ __noinline__ bool psi_holds_fp64(const double* Ug, int64_t n, int64_t r, float p0, float p1, float p2,
+                                            float p3, float p4, float t, double phi_min) {
+  const double u0 = Ug[r], u1 = Ug[n + r], u2 = Ug[2 * n + r], u3 = Ug[3 * n + r], u4 = Ug[4 * n + r];
+  const double td = f2d_exact(t);
+  const double v0 = u0 + td * f2d_exact(p0), v1 = u1 + td * f2d_exact(p1), v2 = u2 + td * f2d_exact(p2);
+  const double v3 = u3 + td * f2d_exact(p3), v4 = u4 + td * f2d_exact(p4);
   const double re = v0 * v4 - 0.5 * (v1 * v1 + v2 * v2 + v3 * v3);
   const double pw = phi_min * pow_12_5(v0);
   return v0 > 0.0 && re - pw >= -1e-13 * (fabs(re) + fabs(pw));
 }
 
-// limiter.compute of Alg. 2 for the mixed path.  U (FP64) is the row state,
-// P (FP32) the direction.  Returns t in [0, 1].
-__device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor& A, const float* P, double phi_min,
+// limiter.compute of Alg. 2 for the mixed path.  The row state (FP64) is row
+// r of the state array Ug (field-major, n nodes), read only by the FP64 check;
+// P (FP32) is the direction.  Returns t in [0, 1].
+__device__ __forceinline__ float limiter_mixed(const double* Ug, int64_t n, int64_t r, const PsiAnchor& A,
+                                               const float* P, double phi_min,
                                                const LimiterParams& prm) {
   // density interval (Reading A12) against the row's FP64 gaps: the cut
   // t = |gap|/|rho(P)| is shrunk by 2^-22 to absorb the FP32 division, so
@@ -235,8 +262,7 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
       psiL = psi_at(A, L, tL, &dpsiL, &feL, &qL);
       haveL = true;
     }
-    const float tol = (float)prm.newton_tol * (A.psi0 + A.phi_pow0);
-    if (psiL <= tol) break;
+    if (psiL <= A.tol) break;
     const float scaling = 1.0f / (tR - tL + FLT_EPSILON);
     const float d12 = (psiR - psiL) * scaling;
     const float d112 = (d12 - dpsiL) * scaling;
@@ -267,7 +293,7 @@ __device__ __forceinline__ float limiter_mixed(const double* U, const PsiAnchor&
   // guarantee it: psiAtL >= 0 means Psi(t) >= margin - error, so the check is
   // needed only when the rounding bound reaches the margin
   if (tL > 0.0f && (psiAtL < 0.0f || psi_error_bound(A, L, tL, feL, qL) >= A.margin) &&
-      !psi_holds_fp64(U[0], U[1], U[2], U[3], U[4], P[0], P[1], P[2], P[3], P[4], tL, phi_min))
+      !psi_holds_fp64(Ug, n, r, P[0], P[1], P[2], P[3], P[4], tL, phi_min))
     tL = 0.0f;
   return tL;
 }
@@ -517,7 +543,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
   load5(R, n, r, ri);
   load5(UL, n, r, ul);
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
-  const PsiAnchor anchor = make_anchor(ul, rmin, rmax, pmin);
+  const PsiAnchor anchor = make_anchor(ul, rmin, rmax, pmin, C.lim.newton_tol);
   const float a_i = alpha[r];
   const float inv_mi = (float)G.inv_mi[r];
   const float scale = (float)(tau * G.inv_mi[r] * (double)(len - 1));
@@ -541,7 +567,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
       pij[f] = scale * fmaf(b_ij, R[f * n + j], fmaf(-b_ji, ri[f], dd * (Uf[f * n + j] - ui[f])));
       P[f * ns + p] = pij[f];
     }
-    l[p] = limiter_mixed(ul, anchor, pij, pmin, C.lim);
+    l[p] = limiter_mixed(UL, n, r, anchor, pij, pmin, C.lim);
   }
 }
 
@@ -581,7 +607,7 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
     Unext[f * n + r] = u[f];
   }
   const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
-  const PsiAnchor anchor = make_anchor(u, rmin, rmax, pmin);
+  const PsiAnchor anchor = make_anchor(u, rmin, rmax, pmin, C.lim.newton_tol);
   // Software pipeline: the loads of entry k + 1 are issued before the limiter
   // of entry k, so their latency overlaps its arithmetic (they read P and l_old
   // slots that iteration k does not write).
@@ -615,7 +641,7 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
       P[f * ns + p] = pij[f];
       zero &= pij[f] == 0.0f;
     }
-    lnew[p] = zero ? 1.0f : limiter_mixed(u, anchor, pij, pmin, C.lim);
+    lnew[p] = zero ? 1.0f : limiter_mixed(Unext, n, r, anchor, pij, pmin, C.lim);
   }
 }
 
