@@ -55,11 +55,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # of the same workloads (the full-size inputs are too large for an ncu replay)
 # and scaled by the number of matrix entries (profiles/ holds the captures):
 # FP64 at h = 1/80 (17,679,673 entries) -> h = 1/120;
-# FP32-mixed k_limiter_pass_m 1.976 GB at 96^3 (23,393,656 entries) -> 128^3.
+# FP32-mixed k_limiter_pass_m 2.002 GB at 96^3 (23,393,656 entries) -> 128^3.
 NCU_TRAFFIC_BYTES = {k: v * 59373973 / 17679673 for k, v in
                      {"edge": 1.583546e9, "flux_limit": 1.265060e9, "low_order": 1.210403e9,
                       "limiter_pass": 2.512997e9}.items()}
-NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 1.976342e9 * 55742968 / 23393656}
+NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 2.001756e9 * 55742968 / 23393656}
 
 
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
