@@ -69,11 +69,17 @@ typedef struct {
                                values instead of six per-entry floats (the matrices of Sec. 3.1,
                                precomputed once as Sec. 3.2 asks); 0: per-entry arrays.  Results are
                                bitwise the same either way. */
+  int adjoint_store_stages; /* 1 (default): idp_adjoint_record also reserves, when the device has the
+                               memory (112 B per stored entry and 200 B per node, for each of the
+                               3 x checkpoint_every stages of a segment, plus 4 GiB to spare), room
+                               for the traces of one checkpoint segment, so that idp_adjoint_backward
+                               evaluates each stage forward once instead of twice; 0: the traced
+                               stages are recomputed.  Gradients are bitwise the same either way. */
 } idp_config;
 
 /* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,
  * newton_tol 1e-10, newton_eps = DBL_EPSILON, FP64, schedule 0, no bound
- * relaxation, entry table on. */
+ * relaxation, entry table on, adjoint stage traces stored. */
 void idp_config_default(idp_config* cfg);
 
 /* Creates a context on the current CUDA device.  cuda_stream is a

@@ -55,6 +55,7 @@ struct idp_ctx {
   std::vector<void*> rec_allocs;
   int rec_steps = 0, rec_every = 0;
   double *rec_ckpt = nullptr, *rec_tau = nullptr, *rec_seg = nullptr;
+  double* rec_snap = nullptr;  // stage traces of one checkpoint segment (adjoint_store_stages), or nullptr
 };
 
 namespace {
@@ -105,7 +106,7 @@ void free_record(idp_ctx* ctx) {
   for (void* p : ctx->rec_allocs) cudaFree(p);
   ctx->rec_allocs.clear();
   ctx->rec_steps = ctx->rec_every = 0;
-  ctx->rec_ckpt = ctx->rec_tau = ctx->rec_seg = nullptr;
+  ctx->rec_ckpt = ctx->rec_tau = ctx->rec_seg = ctx->rec_snap = nullptr;
 }
 
 void free_all(idp_ctx* ctx) {
@@ -245,6 +246,47 @@ int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int 
                                 trace, s, prof, ctx->block, bar);
 }
 
+// Doubles of one stage's stored trace: per node the node quantities, alpha,
+// U^L, the bounds and U after the first pass; per slot d, 1/(2d), P' (after
+// the first pass), P and l of Step 4 and l of the first pass.
+size_t snapshot_doubles(const idp_ctx* ctx) {
+  const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
+  return (size_t)(idp::kNodeQ + 1 + 5 + 3 + 5) * n + (size_t)(1 + 1 + 5 + 5 + 1 + 1) * ns;
+}
+
+// The stage buffers of stored trace k: the stage's own node, d, 1/(2d),
+// alpha, U^L, bounds, P and trace arrays inside rec_snap, the rest (state
+// scratch, R, limiter values, status) shared with ctx->B.
+idp::StageBuffers snapshot_set(const idp_ctx* ctx, int k) {
+  idp::StageBuffers B = ctx->B;
+  const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
+  double* p = ctx->rec_snap + (size_t)k * snapshot_doubles(ctx);
+  auto take = [&](double** f, size_t count) {
+    *f = p;
+    p += count;
+  };
+  take(&B.node, (size_t)idp::kNodeQ * n);
+  take(&B.alpha, n);
+  take(&B.UL, 5 * n);
+  take(&B.bnd, 3 * n);
+  take(&B.tU5, 5 * n);
+  take(&B.d, ns);
+  take(&B.dinv, ns);
+  take(&B.P, 5 * ns);
+  take(&B.tP, 5 * ns);
+  take(&B.tl4, ns);
+  take(&B.tl5, ns);
+  return B;
+}
+
+// One traced FP64 euler_step on explicit stage buffers (the adjoint's stored
+// traces).
+int launch_traced(idp_ctx* ctx, const idp::StageBuffers& B, const double* Uin, double* Uout, const double* Un,
+                  int blend, int tau_mode, cudaStream_t s, idp::Profiler* prof) {
+  return idp::launch_euler_step(ctx->G, B, ctx->C, Uin, Uout, Un, blend, tau_mode, false, false, true, s, prof,
+                                ctx->block, nullptr);
+}
+
 // The three euler_steps of one SSP-RK3 step (eq. ssprk3) on stream s.
 int64_t launch_rk3(idp_ctx* ctx, cudaStream_t s, idp::Profiler* prof) {
   idp::StageBuffers& B = ctx->B;
@@ -295,6 +337,7 @@ void idp_config_default(idp_config* cfg) {
   cfg->schedule = 0;
   cfg->barrier_spin_limit = 1 << 26;
   cfg->entry_table = 1;
+  cfg->adjoint_store_stages = 1;
 }
 
 const char* idp_status_string(idp_status s) {
@@ -935,6 +978,22 @@ idp_status idp_adjoint_record(idp_ctx* ctx, int n_steps, int checkpoint_every) {
     free_record(ctx);
     return st;
   }
+  if (ctx->cfg.adjoint_store_stages) {
+    // traces of the segment's 3 x checkpoint_every stages, if they fit with 4 GiB to spare
+    const size_t want = sizeof(double) * snapshot_doubles(ctx) * (size_t)(3 * checkpoint_every);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b > want + ((size_t)4 << 30)) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, want) == cudaSuccess) {
+        ctx->rec_allocs.push_back(q);
+        ctx->rec_snap = static_cast<double*>(q);
+        // d and 1/(2d) of padding slots and of the diagonal are never written
+        IDP_CUDA(ctx, cudaMemsetAsync(q, 0, want, ctx->stream));
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   cudaStream_t s = ctx->stream;
   int64_t launches = 0;
   for (int q = 0; q < n_steps; ++q) {
@@ -973,12 +1032,23 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
   auto U2 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q + 2) * n5; };
   IDP_CUDA(ctx, cudaMemcpyAsync(g, gU_final, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   int64_t launches = 0;
+  const bool stored = ctx->rec_snap != nullptr;
   for (int c = n_ckpt - 1; c >= 0; --c) {
     const int first = c * every;
     const int len = n_steps - first < every ? n_steps - first : every;
-    // recompute the segment's step inputs and first two stage states
+    // recompute the segment's step inputs and first two stage states (with
+    // stored traces: every stage traced into its own buffers, once)
     IDP_CUDA(ctx, cudaMemcpyAsync(U0(0), ctx->rec_ckpt + (size_t)c * n5, bytes, cudaMemcpyDeviceToDevice, s));
     for (int q = 0; q < len; ++q) {
+      if (stored) {
+        launches += launch_traced(ctx, snapshot_set(ctx, 3 * q), U0(q), U1(q), U0(q), idp::kBlendNone, 0, s,
+                                  &ctx->prof);
+        launches += launch_traced(ctx, snapshot_set(ctx, 3 * q + 1), U1(q), U2(q), U0(q), idp::kBlendStage2, 1, s,
+                                  &ctx->prof);
+        launches += launch_traced(ctx, snapshot_set(ctx, 3 * q + 2), U2(q), q + 1 < len ? U0(q + 1) : scr, U0(q),
+                                  idp::kBlendStage3, 1, s, &ctx->prof);
+        continue;
+      }
       launches += launch(ctx, U0(q), U1(q), U0(q), idp::kBlendNone, 0, false, false, false, s, &ctx->prof);
       launches += launch(ctx, U1(q), U2(q), U0(q), idp::kBlendStage2, 1, false, false, false, s, &ctx->prof);
       if (q + 1 < len)
@@ -987,19 +1057,22 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
     for (int q = len - 1; q >= 0; --q) {
       IDP_CUDA(ctx, cudaMemcpyAsync(G.tau, ctx->rec_tau + first + q, sizeof(double), cudaMemcpyDeviceToDevice, s));
       IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
+      const idp::StageBuffers B1 = stored ? snapshot_set(ctx, 3 * q) : B;
+      const idp::StageBuffers B2 = stored ? snapshot_set(ctx, 3 * q + 1) : B;
+      const idp::StageBuffers B3 = stored ? snapshot_set(ctx, 3 * q + 2) : B;
       // stage 3: U^{n+1} = U^n/3 + 2/3 E(U2)
-      launches += launch(ctx, U2(q), scr, U2(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
+      if (!stored) launches += launch(ctx, U2(q), scr, U2(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
       idp::launch_axpby(gE, 2.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
       idp::launch_axpby(acc, 1.0 / 3.0, g, 0.0, nullptr, (int64_t)n5, s);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U2(q), gE, tmp, false, s, &ctx->prof);
+      launches += idp::launch_adjoint_stage(G, B3, ctx->A, ctx->C, U2(q), gE, tmp, false, s, &ctx->prof);
       // stage 2: U2 = 3/4 U^n + 1/4 E(U1)
-      launches += launch(ctx, U1(q), scr, U1(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
+      if (!stored) launches += launch(ctx, U1(q), scr, U1(q), idp::kBlendNone, 1, false, false, true, s, &ctx->prof);
       idp::launch_axpby(gE, 0.25, tmp, 0.0, nullptr, (int64_t)n5, s);
       idp::launch_axpby(acc, 0.75, tmp, 1.0, acc, (int64_t)n5, s);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U1(q), gE, tmp, false, s, &ctx->prof);
+      launches += idp::launch_adjoint_stage(G, B2, ctx->A, ctx->C, U1(q), gE, tmp, false, s, &ctx->prof);
       // stage 1: U1 = E(U^n), tau_n computed here
-      launches += launch(ctx, U0(q), scr, U0(q), idp::kBlendNone, 0, false, false, true, s, &ctx->prof);
-      launches += idp::launch_adjoint_stage(G, B, ctx->A, ctx->C, U0(q), tmp, gE, true, s, &ctx->prof);
+      if (!stored) launches += launch(ctx, U0(q), scr, U0(q), idp::kBlendNone, 0, false, false, true, s, &ctx->prof);
+      launches += idp::launch_adjoint_stage(G, B1, ctx->A, ctx->C, U0(q), tmp, gE, true, s, &ctx->prof);
       idp::launch_axpby(g, 1.0, gE, 1.0, acc, (int64_t)n5, s);
       launches += 5;  // the blends
     }
