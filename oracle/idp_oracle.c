@@ -12,7 +12,9 @@
  * "Reading A<k>" and listed in the design doc.
  *
  * Parity pins (tests/test_oracle_*.py): closed-form Q1 matrices on uniform
- * grids, linear reproduction on jittered meshes, equal-state wavespeeds and a
+ * grids (hexahedra and quadrilaterals; the quadrilateral matrices also against
+ * the hexahedral ones of the mesh extruded over a periodic axis), linear
+ * reproduction on jittered meshes, equal-state wavespeeds and a
  * brute-force check against an exact Riemann solver, alpha in [0,1], limiter
  * admissibility against bisection, conservation, positivity and local bounds,
  * free-stream preservation, exact Sod and vortex convergence.  Parity
