@@ -213,6 +213,33 @@ def test_deterministic():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
+def test_mesh_upload_rejects_invalid_meshes():
+    """Empty meshes, node ids out of range, a node in no cell and an inverted
+    cell are reported (IDP_ERR_ARG) at upload, for hexahedra and quadrilaterals."""
+    import copy
+    from paper_2007_00094_gb300.idp import IdpError
+    for base in (W.box_mesh((4, 3, 3), periodic=(False, False, False)), W.rect_mesh((4, 3), periodic=(False, False))):
+        bad = []
+        m = copy.deepcopy(base)
+        m.cells = m.cells[:0]
+        m.cell_xyz = m.cell_xyz[:0]
+        bad.append(m)
+        m = copy.deepcopy(base)
+        m.cells[0, 0] = m.n_nodes  # out of range
+        bad.append(m)
+        m = copy.deepcopy(base)
+        m.x = np.vstack([m.x, m.x[:1]])  # one more node that no cell uses
+        m.bc = np.append(m.bc, 0).astype(np.int32)
+        bad.append(m)
+        m = copy.deepcopy(base)
+        m.cell_xyz[0, :, 0] = -m.cell_xyz[0, :, 0]  # mirrored in x: negative Jacobian
+        bad.append(m)
+        for m in bad:
+            with pytest.raises(IdpError) as e:
+                _solver(m)
+            assert e.value.status == 1  # IDP_ERR_ARG
+
+
 def test_rejects_inadmissible_state():
     from paper_2007_00094_gb300.idp import IdpError
     mesh, U = _mesh("tiny3")
