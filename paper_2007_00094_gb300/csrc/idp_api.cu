@@ -536,7 +536,7 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
     const idp::HostEntriesF E{c_float(L.cx), c_float(L.cy), c_float(L.cz), to_float(L.mij), to_float(L.cn),
                               to_float(L.inv_cn)};
     float* fimi;
-    if ((st = upload(ctx, &fimi, to_float(L.inv_mi)))) return st;
+    if ((st = upload(ctx, &fimi, to_float(L.inv_mi))) != IDP_OK) return st;
     ctx->MG = idp::MixedGraph{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fimi, nullptr, nullptr};
     ctx->n_entry_values = 0;
     if (ctx->cfg.entry_table && (st = upload_entry_table(ctx, E))) return st;
@@ -562,7 +562,7 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   }
   B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
-  if ((st = alloc_instances(ctx, 1, std::vector<int32_t>()))) return st;
+  if ((st = alloc_instances(ctx, 1, std::vector<int32_t>())) != IDP_OK) return st;
   ctx->has_mesh = true;
   return IDP_OK;
 }
