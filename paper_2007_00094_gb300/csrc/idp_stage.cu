@@ -351,15 +351,32 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
   const double lam = G.lam[r];
   double u[kFields];
   load5(Ucur, n, r, u);
-  for (int k = 0; k < len; ++k) {
-    const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    // min of two limiter values in [0, 1] on their bit patterns (integer pipe)
-    const double la = lold[p], lb = lold[G.tpos[p]];
-    const double lk = min_k(la, lb);
-    const double w = lam * lk;
+  {
+    // loads of entry k + 1 issued before entry k's accumulation
+    bool dg_n = false;
+    double la_n = 0.0, lb_n = 0.0, p_n[kFields];
+    auto fetch1 = [&](int k) {
+      const int64_t q = base + 32 * (int64_t)k;
+      dg_n = G.col[q] == r;
+      la_n = lold[q];
+      lb_n = lold[G.tpos[q]];
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];
+      for (int f = 0; f < kFields; ++f) p_n[f] = P[f * ns + q];
+    };
+    if (len > 0) fetch1(0);
+    for (int k = 0; k < len; ++k) {
+      const bool dg = dg_n;
+      const double la = la_n, lb = lb_n;
+      double pk[kFields];
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) pk[f] = p_n[f];
+      if (k + 1 < len) fetch1(k + 1);
+      if (dg) continue;
+      // min of two limiter values in [0, 1] on their bit patterns (integer pipe)
+      const double w = lam * min_k(la, lb);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) u[f] += w * pk[f];
+    }
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) Unext[f * n + r] = u[f];
