@@ -75,6 +75,12 @@ typedef struct {
                                for the traces of one checkpoint segment, so that idp_adjoint_backward
                                evaluates each stage forward once instead of twice; 0: the traced
                                stages are recomputed.  Gradients are bitwise the same either way. */
+  int renumber;             /* 1: the library orders its rows by reverse Cuthill-McKee over the
+                               stencil graph (locality of the neighbour gathers for meshes whose nodes
+                               come in an arbitrary order); 0 (default): the caller's node order.
+                               States, fields, gradients, matrices and instance offsets stay in the
+                               caller's numbering at this interface, and results are bitwise the same
+                               either way (every row sum keeps the caller's column order). */
 } idp_config;
 
 /* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,

@@ -29,6 +29,11 @@ struct idp_ctx {
   idp::StageConfig C{};
   idp::MixedGraph MG{};
   int64_t n_entry_values = 0;  // size of the mixed stage's entry table (0: per-entry arrays)
+  // row order (idp_config.renumber): library row of each caller node and back,
+  // on the device, and a 5n buffer for reordering states at the interface
+  bool renumbered = false;
+  int64_t *d_perm = nullptr, *d_iperm = nullptr;
+  double* perm_buf = nullptr;
   idp::MixedBuffers MB{};
   bool mixed = false;
   std::vector<void*> allocations;
@@ -175,7 +180,10 @@ idp_status upload_relax(idp_ctx* ctx, const std::vector<int32_t>& inst) {
   int64_t n_inst = 1;
   for (int32_t k : inst) n_inst = k + 1 > n_inst ? k + 1 : n_inst;
   std::vector<double> vol((size_t)n_inst, 0.0), r((size_t)n);
-  for (int64_t i = 0; i < n; ++i) vol[inst.empty() ? 0 : inst[i]] += L.mi[i];
+  for (int64_t c = 0; c < n; ++c) {  // summed in the caller's node order
+    const int64_t i = L.perm[c];
+    vol[inst.empty() ? 0 : inst[i]] += L.mi[i];
+  }
   for (int64_t i = 0; i < n; ++i) r[i] = std::sqrt(L.mi[i] / vol[inst.empty() ? 0 : inst[i]]);
   if (!ctx->G.relax) {
     double* p = nullptr;
@@ -244,6 +252,52 @@ int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int 
                                         acc_time, skip_write_on_error, trace, s, prof, ctx->block, bar);
   return idp::launch_euler_step(ctx->G, ctx->B, ctx->C, Uin, Uout, Un, blend, tau_mode, acc_time, skip_write_on_error,
                                 trace, s, prof, ctx->block, bar);
+}
+
+// dst[c n + r] = src[c n + map[r]] for the 5 fields: states between the
+// caller's node order and the library's row order (idp_config.renumber).
+__global__ void k_gather_rows(int64_t n, const int64_t* __restrict__ map, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t i = map[r];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) dst[c * n + r] = src[c * n + i];
+}
+
+// A caller-order 5-field array (host or device) into library row order.
+idp_status copy_in(idp_ctx* ctx, double* dst_lib, const double* src, bool on_device) {
+  const int64_t n = ctx->G.n;
+  const size_t bytes = sizeof(double) * 5 * (size_t)n;
+  if (!ctx->renumbered) {
+    IDP_CUDA(ctx, cudaMemcpyAsync(dst_lib, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    return IDP_OK;
+  }
+  const double* from = src;
+  if (!on_device) {
+    IDP_CUDA(ctx, cudaMemcpyAsync(ctx->perm_buf, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    from = ctx->perm_buf;
+  }
+  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_iperm, from, dst_lib);
+  IDP_CUDA(ctx, cudaGetLastError());
+  return IDP_OK;
+}
+
+// A library-order 5-field array back into the caller's order (host or device).
+idp_status copy_out(idp_ctx* ctx, double* dst, const double* src_lib, bool on_device) {
+  const int64_t n = ctx->G.n;
+  const size_t bytes = sizeof(double) * 5 * (size_t)n;
+  if (!ctx->renumbered) {
+    IDP_CUDA(ctx, cudaMemcpyAsync(dst, src_lib, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    return IDP_OK;
+  }
+  double* to = on_device ? dst : ctx->perm_buf;
+  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_perm, src_lib, to);
+  IDP_CUDA(ctx, cudaGetLastError());
+  if (!on_device) IDP_CUDA(ctx, cudaMemcpyAsync(dst, ctx->perm_buf, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return IDP_OK;
 }
 
 // Doubles of one stage's stored trace: per node the node quantities, alpha,
@@ -462,7 +516,7 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
   ctx->M.bc.assign(node_bc ? node_bc : nullptr, node_bc ? node_bc + n_nodes : nullptr);
   if (!node_bc) ctx->M.bc.assign(n_nodes, 0);
-  msg = idp::build_sell(ctx->M, ctx->L);
+  msg = idp::build_sell(ctx->M, ctx->L, ctx->cfg.renumber != 0);
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
   for (int f = 0; f < 5; ++f) ctx->C.inflow[f] = inflow_state ? inflow_state[f] : 0.0;
 
@@ -503,6 +557,11 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   G.relax = nullptr;
   if (ctx->cfg.relax && (st = upload_relax(ctx, std::vector<int32_t>()))) return st;
 
+  ctx->renumbered = ctx->cfg.renumber != 0;
+  if (ctx->renumbered &&
+      ((st = upload(ctx, &ctx->d_perm, L.perm)) || (st = upload(ctx, &ctx->d_iperm, L.iperm)) ||
+       (st = dalloc(ctx, &ctx->perm_buf, (size_t)5 * L.n))))
+    return st;
   idp::StageBuffers& B = ctx->B;
   const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
   B = idp::StageBuffers{};
@@ -598,9 +657,8 @@ idp_status idp_get_matrices(idp_ctx* ctx, int64_t* rowptr, int64_t* col, double*
 idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device) {
   if (!ctx || !U) return fail(ctx, IDP_ERR_ARG, "null state");
   if (!ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
-  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
-  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->B.U, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                ctx->stream));
+  idp_status cst = copy_in(ctx, ctx->B.U, U, on_device != 0);
+  if (cst != IDP_OK) return cst;
   idp_bounds_report rep;
   ctx->has_state = true;
   idp_status st = idp_check_bounds(ctx, &rep);
@@ -615,9 +673,8 @@ idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device) {
 idp_status idp_get_state(idp_ctx* ctx, double* U, int on_device) {
   if (!ctx || !U) return fail(ctx, IDP_ERR_ARG, "null state");
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
-  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
-  IDP_CUDA(ctx, cudaMemcpyAsync(U, ctx->B.U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                ctx->stream));
+  idp_status st = copy_out(ctx, U, ctx->B.U, on_device != 0);
+  if (st != IDP_OK) return st;
   IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return IDP_OK;
 }
@@ -929,12 +986,9 @@ idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, con
   if (!ctx || !U || !gE || !gU) return fail(ctx, IDP_ERR_ARG, "null argument");
   idp_status st = adjoint_supported(ctx);
   if (st != IDP_OK || (st = ensure_adjoint(ctx)) != IDP_OK) return st;
-  const size_t bytes = sizeof(double) * 5 * ctx->G.n;
-  const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const cudaMemcpyKind out = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   cudaStream_t s = ctx->stream;
-  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->a_in, U, bytes, in, s));
-  IDP_CUDA(ctx, cudaMemcpyAsync(ctx->a_e, gE, bytes, in, s));
+  if ((st = copy_in(ctx, ctx->a_in, U, on_device != 0)) != IDP_OK || (st = copy_in(ctx, ctx->a_e, gE, on_device != 0)) != IDP_OK)
+    return st;
   if (tau > 0.0) IDP_CUDA(ctx, cudaMemcpyAsync(ctx->G.tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
   IDP_CUDA(ctx, cudaMemsetAsync(ctx->A.gtau, 0, 2 * sizeof(double), s));
   int64_t launches = launch(ctx, ctx->a_in, ctx->a_out, ctx->a_in, idp::kBlendNone, tau > 0.0 ? 1 : 0, false, false,
@@ -943,7 +997,7 @@ idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, con
                                         &ctx->prof);
   ctx->launches = launches;
   IDP_CUDA(ctx, cudaGetLastError());
-  IDP_CUDA(ctx, cudaMemcpyAsync(gU, ctx->a_tmp, bytes, out, s));
+  if ((st = copy_out(ctx, gU, ctx->a_tmp, on_device != 0)) != IDP_OK) return st;
   double gt = 0.0;
   IDP_CUDA(ctx, cudaMemcpyAsync(&gt, ctx->A.gtau, sizeof(double), cudaMemcpyDeviceToHost, s));
   st = device_status(ctx, true);  // synchronises the stream
@@ -1030,7 +1084,7 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
   auto U0 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q) * n5; };
   auto U1 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q + 1) * n5; };
   auto U2 = [&](int q) { return ctx->rec_seg + (size_t)(3 * q + 2) * n5; };
-  IDP_CUDA(ctx, cudaMemcpyAsync(g, gU_final, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if ((st = copy_in(ctx, g, gU_final, on_device != 0)) != IDP_OK) return st;
   int64_t launches = 0;
   const bool stored = ctx->rec_snap != nullptr;
   for (int c = n_ckpt - 1; c >= 0; --c) {
@@ -1079,7 +1133,7 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
   }
   IDP_CUDA(ctx, cudaMemcpyAsync(G.tau, ctx->rec_tau + n_steps - 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
   IDP_CUDA(ctx, cudaGetLastError());
-  IDP_CUDA(ctx, cudaMemcpyAsync(gU_initial, g, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if ((st = copy_out(ctx, gU_initial, g, on_device != 0)) != IDP_OK) return st;
   ctx->launches = launches;
   return device_status(ctx, true);
 }

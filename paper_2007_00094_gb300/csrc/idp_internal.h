@@ -54,6 +54,7 @@ struct SellLayout {
   std::vector<int64_t> slot_of_entry;   // caller CSR entry -> slot
 };
 
-std::string build_sell(const HostMatrices& M, SellLayout& L);
+// renumber: rows in reverse Cuthill-McKee order (else the caller's order).
+std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber = false);
 
 }  // namespace idp

@@ -267,12 +267,71 @@ std::string assemble_q1_2d(int64_t n, int64_t nc, const int64_t* cells, const do
   return assemble_impl<2>(n, nc, cells, xy, out);
 }
 
-std::string build_sell(const HostMatrices& M, SellLayout& L) {
+// Reverse Cuthill-McKee order of the stencil graph: per connected component
+// (taken in order of their smallest node id) a breadth-first order from a
+// pseudo-peripheral node (the lowest-degree node of the last level of a
+// breadth-first search from the component's smallest id), neighbours visited
+// by increasing degree, then id; the whole sequence reversed.  Returns the
+// caller node of each row.
+std::vector<int64_t> rcm_order(const HostMatrices& M) {
+  const int64_t n = M.n;
+  std::vector<int64_t> order, level(n, -1), queue;
+  order.reserve(n);
+  queue.reserve(n);
+  std::vector<char> done(n, 0);
+  auto deg = [&](int64_t i) { return M.rowptr[i + 1] - M.rowptr[i]; };
+  std::vector<int64_t> nb;
+  for (int64_t s0 = 0; s0 < n; ++s0) {
+    if (done[s0]) continue;
+    // breadth-first levels from s0 to find a pseudo-peripheral start
+    queue.clear();
+    queue.push_back(s0);
+    level[s0] = 0;
+    for (size_t h = 0; h < queue.size(); ++h) {
+      const int64_t u = queue[h];
+      for (int64_t e = M.rowptr[u]; e < M.rowptr[u + 1]; ++e) {
+        const int64_t v = M.col[e];
+        if (level[v] < 0) {
+          level[v] = level[u] + 1;
+          queue.push_back(v);
+        }
+      }
+    }
+    int64_t start = queue.back();
+    for (int64_t u : queue)
+      if (level[u] == level[queue.back()] && (deg(u) < deg(start) || (deg(u) == deg(start) && u < start))) start = u;
+    for (int64_t u : queue) level[u] = -1;
+    // Cuthill-McKee order of the component from start
+    const size_t first = order.size();
+    order.push_back(start);
+    done[start] = 1;
+    for (size_t h = first; h < order.size(); ++h) {
+      const int64_t u = order[h];
+      nb.clear();
+      for (int64_t e = M.rowptr[u]; e < M.rowptr[u + 1]; ++e)
+        if (!done[M.col[e]]) nb.push_back(M.col[e]);
+      std::sort(nb.begin(), nb.end(), [&](int64_t a, int64_t b) { return deg(a) != deg(b) ? deg(a) < deg(b) : a < b; });
+      for (int64_t v : nb) {
+        done[v] = 1;
+        order.push_back(v);
+      }
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
   const int64_t n = M.n;
   L.n = n;
   L.perm.resize(n);
   L.iperm.resize(n);
-  for (int64_t i = 0; i < n; ++i) L.perm[i] = L.iperm[i] = i;  // caller order keeps mesh locality
+  if (renumber) {
+    L.iperm = rcm_order(M);
+    for (int64_t r = 0; r < n; ++r) L.perm[L.iperm[r]] = r;
+  } else {
+    for (int64_t i = 0; i < n; ++i) L.perm[i] = L.iperm[i] = i;  // caller order keeps mesh locality
+  }
   L.n_slices = (n + kSlice - 1) / kSlice;
   L.slice_ptr.assign(L.n_slices + 1, 0);
   L.row_len.assign(n, 0);
@@ -344,7 +403,9 @@ std::string build_sell(const HostMatrices& M, SellLayout& L) {
       L.csz[r] += L.cz[p];
       uint8_t f = 0;
       if (j == r) f |= kEntryDiag;
-      if (j > r) f |= kEntryUpper;
+      // the row of the larger caller id evaluates the pair's wavespeed, so the
+      // orientation does not depend on the row order
+      if (M.col[e] > i) f |= kEntryUpper;
       L.flags[p] = f;
     }
   }

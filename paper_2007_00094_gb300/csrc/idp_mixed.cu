@@ -419,7 +419,7 @@ __device__ __forceinline__ double row_diag_m(const DeviceGraph& G, float* d, flo
     const int64_t j = G.col[p];
     if (j == r) continue;
     float v;
-    if (j < r) {
+    if (!(G.flags[p] & kEntryUpper)) {  // lower entry: copy from the owning row
       const int64_t pt = G.tpos[p];
       v = d[pt];
       d[p] = v;

@@ -170,7 +170,7 @@ __device__ __forceinline__ double row_diag(const DeviceGraph& G, double* d, doub
       continue;
     }
     double v;
-    if (j < r) {
+    if (!(G.flags[p] & kEntryUpper)) {  // lower entry: copy from the owning row
       const int64_t pt = G.tpos[p];
       v = d[pt];
       d[p] = v;

@@ -43,7 +43,7 @@ class IdpConfig(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter_passes", C.c_int), ("newton_max", C.c_int),
                 ("newton_tol", C.c_double), ("newton_eps", C.c_double), ("precision", C.c_int),
                 ("schedule", C.c_int), ("barrier_spin_limit", C.c_int64), ("relax", C.c_int),
-                ("entry_table", C.c_int), ("adjoint_store_stages", C.c_int)]
+                ("entry_table", C.c_int), ("adjoint_store_stages", C.c_int), ("renumber", C.c_int)]
 
 
 class BoundsReport(C.Structure):
