@@ -339,6 +339,39 @@ def pattern_q1_2d(stream, args):
     return out
 
 
+def pattern_renumber(stream, args):
+    """Row order: the step channel (h = 1/m) with its nodes in the generator's
+    lexicographic order, randomly shuffled (seeded) as given, and shuffled but
+    renumbered by the library (idp_config.renumber, reverse Cuthill-McKee);
+    FP64 and FP32-mixed ms per SSP-RK3 step."""
+    import numpy as np
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+
+    mesh = W.forward_step_mesh(m=args.m, jitter=0.2, seed=2007)
+    U0 = W.forward_step_state(mesh)
+    rng = np.random.default_rng(11)
+    p = rng.permutation(mesh.n_nodes)
+    inv = np.empty_like(p)
+    inv[p] = np.arange(mesh.n_nodes)
+    shuf = W.HexMesh(x=mesh.x[inv], cells=p[mesh.cells], cell_xyz=mesh.cell_xyz, bc=mesh.bc[inv], volume=mesh.volume,
+                     inflow=mesh.inflow, name="shuffled")
+    U_shuf = U0[:, inv]
+    out = {"config": {"workload": f"mach3_forward_facing_step_h1/{args.m}_nodes_shuffled_seed11", "nodes": mesh.n_nodes,
+                      "steps_timed": args.pattern_steps, "warmup": args.warmup}}
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+        row = {}
+        for label, m, u, ren in (("lexicographic", mesh, U0, 0), ("shuffled", shuf, U_shuf, 0),
+                                 ("shuffled_renumbered", shuf, U_shuf, 1)):
+            s = Solver(m, stream=stream, precision=prec, renumber=ren)
+            s.init_state(u)
+            row[label] = _time_steps(s, stream, args.pattern_steps, args.warmup, profile=False)[0]
+            s.close()
+        out[name] = {"ms_per_step": row}
+    return out
+
+
 def job_rate(local_ms, units_per_rank, dist=None, device="cpu"):
     """Whole-job rate of a weak-scaling run: the slowest rank's time (max over
     ranks) and all ranks' units divided by it.  Returns (ms_max, units/s)."""
@@ -510,7 +543,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=100)
     ap.add_argument("--adj-fd-directions", type=int, default=2)
     ap.add_argument("--m2d", type=int, default=1000, help="cells per unit length of the 2D channel mesh")
-    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation", "q1_2d"],
+    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation", "q1_2d", "renumber"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -534,7 +567,7 @@ def main():
     if args.only:
         build.build()
         run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
-               "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d}[args.only]
+               "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d, "renumber": pattern_renumber}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return
     dist = None
@@ -633,7 +666,8 @@ def main():
         if not args.no_patterns:
             line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
                                 "adjoint": pattern_adjoint(stream, args),
-                                "relaxation": pattern_relaxation(stream, args), "q1_2d": pattern_q1_2d(stream, args)}
+                                "relaxation": pattern_relaxation(stream, args), "q1_2d": pattern_q1_2d(stream, args),
+                                "renumber": pattern_renumber(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
 __global__ void __launch_bounds__(kB) ka_tau(DeviceGraph G, AdjointBuffers A, int add_carry) {
   __shared__ double part[kB];
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) s += A.gtau_part[i];
+  for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) s += A.gtau_part[G.row_of_node ? G.row_of_node[i] : i];
   part[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -594,7 +594,9 @@ __global__ void __launch_bounds__(kB) ka_cfl_arg(DeviceGraph G, const double* __
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const double c = cfl_candidate(G, d, r);
-  if ((unsigned long long)__double_as_longlong(c) == A.argmin[0]) atomicMin(&A.argmin[1], (unsigned long long)r);
+  // the first row in the caller's node order attaining the minimum
+  const int64_t key = G.node_of_row ? G.node_of_row[r] : r;
+  if ((unsigned long long)__double_as_longlong(c) == A.argmin[0]) atomicMin(&A.argmin[1], (unsigned long long)key);
 }
 
 // Step 2 reverse: d_ii = -sum_{j != i} d_ij; in the first RK stage also
@@ -610,7 +612,7 @@ __global__ void __launch_bounds__(kB) ka_diag(DeviceGraph G, StageConfig C, cons
     const int64_t p = base + 32 * (int64_t)k;
     if (G.col[p] != r) continue;
     gdii = A.gd[p];
-    if (tau_computed && (unsigned long long)r == A.argmin[1]) {
+    if (tau_computed && (unsigned long long)(G.node_of_row ? G.node_of_row[r] : r) == A.argmin[1]) {
       const double dii = d[p];
       gdii += A.gtau[1] * C.cfl * G.mi[r] / (2.0 * dii * dii);
     }

@@ -558,10 +558,14 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   if (ctx->cfg.relax && (st = upload_relax(ctx, std::vector<int32_t>()))) return st;
 
   ctx->renumbered = ctx->cfg.renumber != 0;
-  if (ctx->renumbered &&
-      ((st = upload(ctx, &ctx->d_perm, L.perm)) || (st = upload(ctx, &ctx->d_iperm, L.iperm)) ||
-       (st = dalloc(ctx, &ctx->perm_buf, (size_t)5 * L.n))))
-    return st;
+  G.node_of_row = G.row_of_node = nullptr;
+  if (ctx->renumbered) {
+    if ((st = upload(ctx, &ctx->d_perm, L.perm)) || (st = upload(ctx, &ctx->d_iperm, L.iperm)) ||
+        (st = dalloc(ctx, &ctx->perm_buf, (size_t)5 * L.n)))
+      return st;
+    G.node_of_row = ctx->d_iperm;
+    G.row_of_node = ctx->d_perm;
+  }
   idp::StageBuffers& B = ctx->B;
   const size_t n = (size_t)L.n, ns = (size_t)L.n_slots;
   B = idp::StageBuffers{};

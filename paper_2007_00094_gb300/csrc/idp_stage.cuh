@@ -33,6 +33,12 @@ struct DeviceGraph {
   const double* lam;
   const int32_t* bc;
   const double* relax;  // per-row bound relaxation r_i, or nullptr (off)
+  // Row order (idp_config.renumber): caller node of each row and row of each
+  // caller node, or nullptr for the caller's order.  Read where a result
+  // depends on the order of rows (the adjoint's fixed-order sum of the tau
+  // adjoint and its CFL arg-min tie rule), so that it is the same either way.
+  const int64_t* node_of_row;
+  const int64_t* row_of_node;
   // Independent instances (node ranges without entries between them): each
   // has its own tau_n and time.  inst[r] is the instance of row r (nullptr:
   // one instance).  The per-instance arrays below are device state written
