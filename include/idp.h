@@ -226,7 +226,7 @@ enum {
 idp_status idp_profile(idp_ctx* ctx, int enable);
 idp_status idp_profile_read(idp_ctx* ctx, double* ms, int64_t* launches);
 
-/* Many independent instances in one context (SURVEY batching pattern): the
+/* Many independent instances in one context (batches of small problems): the
  * uploaded mesh is the union of instance meshes whose nodes occupy the
  * contiguous ranges [node_offsets[k], node_offsets[k+1]) (n_instances + 1
  * host values, 0 first, n_nodes last) and share no matrix entry (else

@@ -8,8 +8,8 @@
  * rows i in index order, stencil entries j in increasing column order, one
  * floating-point operation at a time (build with -ffp-contract=off).
  *
- * Readings of passages that are silent, garbled or inconsistent are marked
- * "Reading A<k>" and listed in the design doc.
+ * Where the paper is silent, garbled or inconsistent the reading taken is
+ * marked "Reading A<k>" and stated at the place it is used.
  *
  * Parity pins (tests/test_oracle_*.py): closed-form Q1 matrices on uniform
  * grids (hexahedra and quadrilaterals; the quadrilateral matrices also against
@@ -305,7 +305,9 @@ void orc_node_quantities(const double* U, double gamma, double* out) {
 /* ------------------------------------------------------------------------ */
 
 static double positive_part(double x) { return 0.5 * (fabs(x) + x); }
-static double negative_part(double x) { return 0.5 * (fabs(x) - x); } /* Reading A3 */
+/* [x]_neg = (|x| - x)/2: the paper uses the negative part without defining
+ * its sign convention (Reading A3) */
+static double negative_part(double x) { return 0.5 * (fabs(x) - x); }
 
 typedef struct { double rho, u, p, c; } state1d;
 
@@ -558,7 +560,9 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
                  s_i * b[0];
     double N_i = fabs(num);
     double D_i = fabs(a);
-    for (int f = 0; f < NF; ++f) D_i += fabs(etap[f] - (f == 0 ? s_i : 0.0)) * fabs(b[f]); /* Reading A6 */
+    /* the denominator sums all five components (the printed range stops one
+     * short), which keeps alpha_i in [0, 1] (Reading A6) */
+    for (int f = 0; f < NF; ++f) D_i += fabs(etap[f] - (f == 0 ? s_i : 0.0)) * fabs(b[f]);
     alpha[i] = D_i > 0.0 ? N_i / D_i : 0.0;
   }
 
@@ -585,7 +589,7 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
   if (!fixed_tau) {
     *tau = prm->cfl * tau_max;
   } else if (*tau > tau_max) {
-    status = ORC_ERR_CFL; /* Reading A17 */
+    status = ORC_ERR_CFL; /* a given tau above this stage's bound is reported (Reading A17) */
   }
   const double dt = *tau;
 
@@ -616,7 +620,7 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
       contract(Fi, c, fi);
       const double dH = d[k] * (alpha[i] + alpha[j]) / 2.0;
       for (int f = 0; f < NF; ++f) r[f] += -fj[f] + dH * (uj[f] - ui[f]);
-      if (d[k] != 0.0) { /* Reading A19 */
+      if (d[k] != 0.0) { /* an entry with d_ij = 0 has no bar state and is skipped (Reading A19) */
         double ubar[NF];
         for (int f = 0; f < NF; ++f) ubar[f] = 0.5 * (ui[f] + uj[f]) - (fj[f] - fi[f]) / (2.0 * d[k]);
         const double coef = 2.0 * dt / M->mi[i] * d[k];
