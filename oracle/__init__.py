@@ -20,7 +20,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "idp_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "libidp_oracle.so")
+# IDP_ORACLE_LIB: load a prebuilt oracle library instead (the tests that plant
+# mistakes in a copy of the source point it at the mutant's build)
+_LIB_PATH = os.environ.get("IDP_ORACLE_LIB") or os.path.join(_HERE, "libidp_oracle.so")
 _lib = None
 
 _dp = C.POINTER(C.c_double)
