@@ -57,3 +57,31 @@ def test_config_defaults_and_argument_checks(lib):
 
 def test_sources_target_sm103a_only():
     assert "arch=compute_103a,code=sm_103a" in " ".join(B.ARCH)
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and field offsets of a struct of include/idp.h, from a C program."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    prog = tmp_path / "layout.c"
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "idp.h"', "int main(void) {",
+             f'  printf("%zu", sizeof({struct}));']
+    lines += [f'  printf(" %zu", offsetof({struct}, {f}));' for f in fields]
+    lines += ['  printf("\\n");', "  return 0;", "}"]
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)], check=True)
+    return [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """The binding's idp_config and idp_bounds_report have the C compiler's size
+    and field offsets (a field added on one side only would shift the rest)."""
+    from paper_2007_00094_gb300 import idp
+    for cls, name in ((idp.IdpConfig, "idp_config"), (idp.BoundsReport, "idp_bounds_report")):
+        fields = [f[0] for f in cls._fields_]
+        layout = _c_layout(name, fields, tmp_path)
+        assert layout[0] == ctypes.sizeof(cls), name
+        assert layout[1:] == [getattr(cls, f).offset for f in fields], name
