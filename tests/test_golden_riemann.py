@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def test_sod_star_region():
-    g = json.load(open(os.path.join(HERE, "golden", "sod_star_state.json")))
+    with open(os.path.join(HERE, "golden", "sod_star_state.json")) as fh:
+        g = json.load(fh)
     L = (g["left"]["rho"], g["left"]["u"], g["left"]["p"])
     R = (g["right"]["rho"], g["right"]["u"], g["right"]["p"])
     p, u = star_pressure(L, R, g["gamma"])

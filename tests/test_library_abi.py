@@ -17,7 +17,8 @@ def _declared_functions():
     for f in sorted(os.listdir(inc)):
         if not f.endswith(".h"):
             continue
-        text = open(os.path.join(inc, f)).read()
+        with open(os.path.join(inc, f)) as fh:
+            text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names += re.findall(r"\b(idp_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))

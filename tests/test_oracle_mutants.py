@@ -38,7 +38,8 @@ def test_planted_mistake_fails_a_pin(name, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
     old, new = MUTANTS[name]
-    src = open(SRC).read()
+    with open(SRC) as fh:
+        src = fh.read()
     assert src.count(old) == 1, name
     shutil.copy(os.path.join(ROOT, "oracle", "idp_oracle.h"), tmp_path)
     (tmp_path / "idp_oracle.c").write_text(src.replace(old, new))
