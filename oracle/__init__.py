@@ -33,15 +33,15 @@ _i32p = C.POINTER(C.c_int32)
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("limiter_passes", C.c_int),
                 ("newton_max", C.c_int), ("newton_tol", C.c_double), ("newton_eps", C.c_double),
-                ("n_threads", C.c_int), ("relax", C.c_int)]
+                ("n_threads", C.c_int), ("relax", C.c_int), ("psi_margin", C.c_double)]
 
 
 def default_params(**kw) -> Params:
     """gamma = 7/5 (Sec. 2), c_cfl = 0.5, two limiter passes (Reading A16),
     two Newton steps and tolerance 1e-10 (Reading A11), eps = DBL_EPSILON
-    (Reading A5)."""
+    (Reading A5), Psi margin 1e-13 (Reading A27)."""
     p = Params(gamma=1.4, cfl=0.5, limiter_passes=2, newton_max=2, newton_tol=1e-10,
-               newton_eps=float(np.finfo(np.float64).eps), n_threads=1, relax=0)
+               newton_eps=float(np.finfo(np.float64).eps), n_threads=1, relax=0, psi_margin=1e-13)
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -95,6 +95,10 @@ def lib():
                                      C.POINTER(_Trace)]
         L.orc_ssprk3_step.restype = C.c_int
         L.orc_ssprk3_step.argtypes = [C.POINTER(_Mesh), C.POINTER(Params), _dp, _dp]
+        L.orc_ssprk3_step_fixed.restype = C.c_int
+        L.orc_ssprk3_step_fixed.argtypes = [C.POINTER(_Mesh), C.POINTER(Params), _dp, C.c_double]
+        L.orc_limiter_many.restype = None
+        L.orc_limiter_many.argtypes = [C.c_int64, _dp, _dp, _dp, C.POINTER(Params), _dp, _i32p, _dp]
     return _lib
 
 
@@ -200,6 +204,15 @@ def ssprk3_step(om: OracleMesh, U, params=None):
     return U, t.value, st
 
 
+def ssprk3_step_fixed(om: OracleMesh, U, tau, params=None):
+    """One SSP-RK3 step (eq. ssprk3) with a given tau_n for all three stages;
+    returns ``(U_new, status)``."""
+    prm = params or default_params()
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    st = lib().orc_ssprk3_step_fixed(C.byref(om.struct()), C.byref(prm), _p(U), float(tau))
+    return U, st
+
+
 def run(om: OracleMesh, U, n_steps, params=None):
     """``n_steps`` SSP-RK3 steps; returns ``(U, t, taus)``."""
     t = 0.0
@@ -227,6 +240,25 @@ def limiter(U, P, rho_min, rho_max, phi_min, params=None) -> float:
     U = np.ascontiguousarray(U, dtype=np.float64)
     P = np.ascontiguousarray(P, dtype=np.float64)
     return lib().orc_limiter(_p(U), _p(P), rho_min, rho_max, phi_min, C.byref(prm))
+
+
+def limiter_many(U, P, bounds, params=None):
+    """limiter.compute of Alg. 2 for m independent calls: U, P of shape (5, m),
+    bounds (3, m) = (rho_min, rho_max, phi_min).  Returns ``(t, hits, worst)``:
+    the limiter values, the number of admissibility tests per call whose
+    outcome the Psi margin decided (Reading A27) and the largest |Psi| / scale
+    among them."""
+    prm = params or default_params()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    bounds = np.ascontiguousarray(bounds, dtype=np.float64)
+    m = U.shape[1]
+    assert U.shape == (5, m) and P.shape == (5, m) and bounds.shape == (3, m)
+    t = np.zeros(m)
+    hits = np.zeros(m, dtype=np.int32)
+    worst = np.zeros(m)
+    lib().orc_limiter_many(m, _p(U), _p(P), _p(bounds), C.byref(prm), _p(t), _p(hits, _i32p), _p(worst))
+    return t, hits, worst
 
 
 def psi(U, phi_min, gamma=1.4) -> float:

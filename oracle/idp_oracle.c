@@ -17,9 +17,12 @@
  * reproduction on jittered meshes, equal-state wavespeeds and a
  * brute-force check against an exact Riemann solver, alpha in [0,1], limiter
  * admissibility against bisection, conservation, positivity and local bounds,
- * free-stream preservation, exact Sod and vortex convergence.  Parity
- * unpinned: the lower bound of the limiter's t (it depends on the Newton
- * settings of Alg. 2, which the paper leaves open).
+ * free-stream preservation, exact Sod and vortex convergence, third-order
+ * temporal convergence of eq. (ssprk3), and the Psi margin of Reading A27
+ * (it changes only limiter calls in which some Psi lay within the margin,
+ * and it keeps rounding-level input perturbations from flipping limiter
+ * decisions).  Parity unpinned: the lower bound of the limiter's t (it
+ * depends on the Newton settings of Alg. 2, which the paper leaves open).
  */
 #include "idp_oracle.h"
 
@@ -371,15 +374,26 @@ static double dpsi_dt(const double* V, const double* P, double phi_min, double g
   return drho_eps - phi_min * (gamma + 1.0) * pow(V[0], gamma) * P[0];
 }
 
-/* Psi(V) >= 0 up to a relative margin of 1e-13 of its two terms: they
- * nearly cancel where phi is close to phi_min (isentropic flow), so the sign
- * of a Psi that small is decided by rounding.  The margin sits well above the
- * rounding error (~1e-15) so the decision does not depend on it, and well
- * below the tolerance of the invariant checks (Reading A10). */
-static int psi_admissible(const double* V, double phi_min, double gamma) {
+/* Admissibility test Psi(V) >= 0 of Alg. 2, taken with a relative margin
+ * (Reading A27): Psi(V) >= -margin (|rho eps| + |phi_min rho^(gamma+1)|).
+ * The caption of Alg. 3 states that an implementation must add safeguards
+ * against round-off; this is one of them.  Where phi is close to phi_min
+ * (isentropic flow) the two terms of Psi nearly cancel and the sign of a Psi
+ * that small depends on the rounding of its inputs, which differ between any
+ * two implementations of the stage at the 1e-13 level.  margin = 0 gives the
+ * strict test.  When the outcome was decided by the margin (-slack <= Psi <
+ * 0), *hits is incremented and *worst raised to |Psi| / scale. */
+static int psi_admissible(const double* V, double phi_min, double gamma, double margin, int* hits,
+                          double* worst) {
   const double rho_eps = V[0] * V[4] - 0.5 * (V[1] * V[1] + V[2] * V[2] + V[3] * V[3]);
-  const double slack = 1e-13 * (fabs(rho_eps) + fabs(phi_min * pow(V[0], gamma + 1.0)));
-  return orc_psi(V, phi_min, gamma) >= -slack;
+  const double scale = fabs(rho_eps) + fabs(phi_min * pow(V[0], gamma + 1.0));
+  const double psi = orc_psi(V, phi_min, gamma);
+  const int ok = psi >= -margin * scale;
+  if (ok && psi < 0.0) {
+    ++*hits;
+    if (-psi / scale > *worst) *worst = -psi / scale;
+  }
+  return ok;
 }
 
 static void axpy_state(const double* U, double t, const double* P, double* out) {
@@ -413,10 +427,16 @@ static void quadratic_newton_step(double* tL, double* tR, double PsiL, double Ps
 
 /* limiter.compute(U, P, bounds) of Alg. 2: the largest t in [0,1] found by
  * the density interval and the quadratic Newton iteration such that U + t P
- * keeps rho in [rho_min, rho_max] and Psi >= 0.  Readings A9-A12. */
-double orc_limiter(const double* U, const double* P, double rho_min, double rho_max, double phi_min,
-                   const orc_params* prm) {
+ * keeps rho in [rho_min, rho_max] and Psi >= 0.  Readings A9-A12, A26, A27.
+ * margin_hits / margin_worst (may be NULL) receive the number of
+ * admissibility tests whose outcome the Psi margin decided and the largest
+ * |Psi| / scale among them. */
+double orc_limiter_ex(const double* U, const double* P, double rho_min, double rho_max, double phi_min,
+                      const orc_params* prm, int* margin_hits, double* margin_worst) {
   const double gamma = prm->gamma;
+  const double margin = prm->psi_margin;
+  int hits = 0;
+  double worst = 0.0;
   double tL = 0.0, tR = 1.0;
   const double rhoU = U[0], rhoP = P[0];
   /* density interval (Reading A12) */
@@ -428,7 +448,7 @@ double orc_limiter(const double* U, const double* P, double rho_min, double rho_
   for (int step = 0; step < prm->newton_max; ++step) {
     axpy_state(U, tR, P, V);
     const double PsiR = orc_psi(V, phi_min, gamma);
-    if (psi_admissible(V, phi_min, gamma)) { /* t_R is admissible: close the interval */
+    if (psi_admissible(V, phi_min, gamma, margin, &hits, &worst)) { /* t_R admissible: close the interval */
       tL = tR;
       break;
     }
@@ -445,12 +465,19 @@ double orc_limiter(const double* U, const double* P, double rho_min, double rho_
      * lands on the root within rounding must not fall back to the old t_L) */
     nL = clamp(nL, tL, tR);
     axpy_state(U, nL, P, V);
-    if (!psi_admissible(V, phi_min, gamma)) nL = tL;
+    if (!psi_admissible(V, phi_min, gamma, margin, &hits, &worst)) nL = tL;
     nR = clamp(nR, nL, tR);
     tL = nL;
     tR = nR;
   }
+  if (margin_hits) *margin_hits = hits;
+  if (margin_worst) *margin_worst = worst;
   return tL;
+}
+
+double orc_limiter(const double* U, const double* P, double rho_min, double rho_max, double phi_min,
+                   const orc_params* prm) {
+  return orc_limiter_ex(U, P, rho_min, rho_max, phi_min, prm, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -745,24 +772,55 @@ int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, do
 /* ------------------------------------------------------------------------ */
 /* SSP-RK3, Sec. 3.6 eq. (ssprk3): tau fixed by the first stage               */
 /* ------------------------------------------------------------------------ */
-int orc_ssprk3_step(const orc_mesh* M, const orc_params* prm, double* U, double* tau_out) {
+/* One step of eq. (ssprk3).  fixed_tau = 0: tau_n comes from the CFL rule of
+ * the first stage and is written to *tau; fixed_tau != 0: *tau is used by all
+ * three stages (each checks it against its own bound, Reading A17). */
+static int ssprk3(const orc_mesh* M, const orc_params* prm, double* U, double* tau, int fixed_tau) {
   const int64_t n = M->n;
   const size_t sz = sizeof(double) * NF * (size_t)n;
   double* U1 = (double*)malloc(sz);
   double* U2 = (double*)malloc(sz);
   double* E = (double*)malloc(sz);
-  double tau = 0.0;
-  int st = orc_euler_step(M, prm, U, &tau, 0, U1, NULL);
-  if (st == ORC_OK) st = orc_euler_step(M, prm, U1, &tau, 1, E, NULL);
+  int st = orc_euler_step(M, prm, U, tau, fixed_tau, U1, NULL);
+  if (st == ORC_OK) st = orc_euler_step(M, prm, U1, tau, 1, E, NULL);
   if (st == ORC_OK) {
     for (int64_t q = 0; q < NF * n; ++q) U2[q] = 0.75 * U[q] + 0.25 * E[q];
-    st = orc_euler_step(M, prm, U2, &tau, 1, E, NULL);
+    st = orc_euler_step(M, prm, U2, tau, 1, E, NULL);
   }
   if (st == ORC_OK)
     for (int64_t q = 0; q < NF * n; ++q) U[q] = 1.0 / 3.0 * U[q] + 2.0 / 3.0 * E[q];
-  if (tau_out) *tau_out = tau;
   free(U1);
   free(U2);
   free(E);
   return st;
+}
+
+int orc_ssprk3_step_fixed(const orc_mesh* M, const orc_params* prm, double* U, double tau) {
+  return ssprk3(M, prm, U, &tau, 1);
+}
+
+int orc_ssprk3_step(const orc_mesh* M, const orc_params* prm, double* U, double* tau_out) {
+  double tau = 0.0;
+  const int st = ssprk3(M, prm, U, &tau, 0);
+  if (tau_out) *tau_out = tau;
+  return st;
+}
+
+/* limiter.compute of Alg. 2 for m independent calls: U, P (5 x m), bounds
+ * (3 x m: rho_min, rho_max, phi_min), all field-major; t, hits and worst as
+ * in orc_limiter_ex (hits and worst may be NULL). */
+void orc_limiter_many(int64_t m, const double* U, const double* P, const double* bounds, const orc_params* prm,
+                      double* t, int* hits, double* worst) {
+  for (int64_t q = 0; q < m; ++q) {
+    double u[NF], p[NF];
+    for (int f = 0; f < NF; ++f) {
+      u[f] = U[f * m + q];
+      p[f] = P[f * m + q];
+    }
+    int h = 0;
+    double w = 0.0;
+    t[q] = orc_limiter_ex(u, p, bounds[q], bounds[m + q], bounds[2 * m + q], prm, &h, &w);
+    if (hits) hits[q] = h;
+    if (worst) worst[q] = w;
+  }
 }

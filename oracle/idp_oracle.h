@@ -29,6 +29,8 @@ typedef struct {
   double newton_eps;  /* eps of Alg. 3 */
   int n_threads;      /* OpenMP threads over rows (results do not depend on it) */
   int relax;          /* != 0: relax the local bounds (Sec. 3.9 remark; Reading A14) */
+  double psi_margin;  /* Psi >= -psi_margin (|rho eps| + |phi_min rho^(gamma+1)|) counts as admissible in
+                         Alg. 2 (Reading A27, the round-off safeguard of Alg. 3's caption); 0: strict */
 } orc_params;
 
 typedef struct {
@@ -75,11 +77,19 @@ double orc_lambda_max(const double* n, const double* Ui, const double* Uj, doubl
 double orc_limiter(const double* U, const double* P, double rho_min, double rho_max, double phi_min,
                    const orc_params* prm);
 double orc_psi(const double* U, double phi_min, double gamma);
+/* orc_limiter, also reporting the admissibility tests decided by the Psi
+ * margin (count, and the largest |Psi| / scale among them); either may be NULL */
+double orc_limiter_ex(const double* U, const double* P, double rho_min, double rho_max, double phi_min,
+                      const orc_params* prm, int* margin_hits, double* margin_worst);
+void orc_limiter_many(int64_t m, const double* U, const double* P, const double* bounds, const orc_params* prm,
+                      double* t, int* hits, double* worst);
 
 /* ---- one euler_step (Alg. 1) and one SSP-RK3 step (eq. "ssprk3") ---- */
 int orc_euler_step(const orc_mesh* M, const orc_params* prm, const double* U, double* tau, int fixed_tau,
                    double* U_out, orc_trace* tr);
 int orc_ssprk3_step(const orc_mesh* M, const orc_params* prm, double* U, double* tau_out);
+/* eq. "ssprk3" with a given tau_n for all three stages */
+int orc_ssprk3_step_fixed(const orc_mesh* M, const orc_params* prm, double* U, double tau);
 
 #ifdef __cplusplus
 }
