@@ -121,6 +121,29 @@ idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, c
 idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
                                 const double* cell_xy, const int32_t* node_bc, const double* inflow_state);
 
+/* Uploads pre-assembled matrices instead of a mesh.  The scheme needs only
+ * the matrices of Sec. 3.1 eq. (matrices), precomputed once (Sec. 3.2):
+ * callers that assemble them themselves (other element types, their own
+ * quadrature) pass them here in CSR form, in their own node numbering.
+ *   n_nodes      : number of nodes (rows)
+ *   rowptr       : host, n_nodes+1 offsets, rowptr[0] = 0, nnz = rowptr[n_nodes]
+ *   col          : host, nnz column ids, strictly increasing within each row;
+ *                  every row holds its diagonal and at least one neighbour, and
+ *                  the pattern is structurally symmetric (entry (j,i) exists
+ *                  for every entry (i,j)), else IDP_ERR_ARG
+ *   mij          : host, nnz consistent masses m_ij
+ *   cij          : host, 3*nnz, c_ij component-major (x row, y row, z row;
+ *                  a zero z row for d = 2)
+ *   mi           : host, n_nodes lumped masses m_i > 0, or NULL for the row
+ *                  sums of m_ij (equal to int phi_i by partition of unity)
+ *   node_bc, inflow_state : as for idp_upload_mesh_hex
+ * Entries must be finite (else IDP_ERR_ARG).  Pairs with c_ji = -c_ij
+ * bitwise share one wavespeed evaluation; all others evaluate both
+ * orientations (Sec. 3.3).  The buffers are copied during the call. */
+idp_status idp_upload_sparsity(idp_ctx* ctx, int64_t n_nodes, const int64_t* rowptr, const int64_t* col,
+                               const double* mij, const double* cij, const double* mi, const int32_t* node_bc,
+                               const double* inflow_state);
+
 /* Number of nodes and of stored matrix entries (the stencil sizes I(i) of
  * Sec. 3.1 summed over i). */
 idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz);
@@ -182,17 +205,50 @@ enum {
 };
 idp_status idp_get_field(idp_ctx* ctx, int which, double* out);
 
-/* Invariant check of the current state (Sec. 3.3, Sec. 3.9): counts nodes
- * with rho <= 0, epsilon <= 0 or a non-finite value.  Synchronises.  Returns
- * IDP_ERR_BOUNDS when any count is non-zero. */
+/* Invariant checks (Sec. 3.3: the admissible set; Sec. 3.9: the local
+ * bounds that the limiter enforces).
+ *
+ * idp_check_bounds checks
+ *  (a) the current state: counts of nodes with rho <= 0, epsilon <= 0 or a
+ *      non-finite value, and the smallest rho and epsilon;
+ *  (b) the output of the last euler_step the context ran on the current state
+ *      (idp_step, idp_euler_step, or a forward evaluation inside the
+ *      idp_adjoint_* calls), after its last limiter pass and before boundary
+ *      values and the SSP-RK3 blend, against that stage's own bounds
+ *      rho_min_i <= rho_i <= rho_max_i and phi(U_i) >= phi_min_i.  The
+ *      entropy bound is tested as the limiter tests it (Alg. 2):
+ *      Psi = rho eps - phi_min rho^(gamma+1) >= -slack_phi (|rho eps| +
+ *      phi_min rho^(gamma+1)); the density bounds with a relative slack
+ *      slack_rho.  Slacks: FP64 1e-13 (rho) and 2e-13 (Psi: the limiter
+ *      accepts Psi down to -1e-13 of this scale, plus rounding of the row
+ *      sum); FP32-mixed 1e-7 and 1e-6 (increments summed in FP32).  Before
+ *      any stage has run on the state, n_bound_rows is 0 and (b) is skipped.
+ * Synchronises.  Returns IDP_ERR_BOUNDS when any count is non-zero.
+ *
+ * idp_check_local_bounds runs the same two checks on a caller-given state U
+ * (5 x n, caller order) against caller-given bounds (3 x n: rho_min,
+ * rho_max, phi_min, caller order, the layout of IDP_FIELD_BOUNDS); host
+ * pointers, or device pointers with on_device != 0.  It uses stage scratch
+ * buffers of the context and leaves its state untouched. */
 typedef struct {
-  int64_t n_rho_nonpositive;
+  int64_t n_rho_nonpositive;  /* (a) */
   int64_t n_eps_nonpositive;
   int64_t n_nonfinite;
   double rho_min;
   double eps_min;
+  int64_t n_bound_rows;       /* (b): rows checked, 0 when skipped */
+  int64_t n_rho_below_min;    /* rho < rho_min - slack_rho |rho_min| (or NaN) */
+  int64_t n_rho_above_max;    /* rho > rho_max + slack_rho |rho_max| (or NaN) */
+  int64_t n_phi_below_min;    /* Psi below -slack_phi of its scale (or NaN) */
+  double rho_min_violation;   /* max_i (rho_min_i - rho_i) / |rho_min_i|; <= 0: the bound holds everywhere */
+  double rho_max_violation;   /* max_i (rho_i - rho_max_i) / |rho_max_i| */
+  double phi_min_violation;   /* max_i -Psi_i / (|rho eps| + phi_min rho^(gamma+1))_i */
+  double slack_rho;           /* the relative slacks the counts use */
+  double slack_phi;
 } idp_bounds_report;
 idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out);
+idp_status idp_check_local_bounds(idp_ctx* ctx, const double* U, const double* bounds, int on_device,
+                                  idp_bounds_report* out);
 
 /* Number of kernel launches the last idp_step/idp_euler_step enqueued. */
 int64_t idp_launch_count(const idp_ctx* ctx);
@@ -300,12 +356,23 @@ idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, con
 idp_status idp_adjoint_record(idp_ctx* ctx, int n_steps, int checkpoint_every);
 idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU_initial, int on_device);
 
+/* FP64 fused multiply-add rate of the current GPU, for the roofline of the
+ * FP64 stage (its heavy kernels are bound by the FP64 pipe; the paper has no
+ * counterpart, it measures CPU peaks instead, Sec. 5, Table 1).  Runs one
+ * launch of independent FMA chains on a full grid of the current device, on
+ * cuda_stream (may be NULL), fma_per_thread (>= 16) FMAs per thread, and
+ * writes the rate in TFLOP/s (2 flops per FMA) and, if ms is not NULL, the
+ * launch's CUDA-event time.  Synchronises the stream; allocates nothing. */
+idp_status idp_probe_fp64_peak(void* cuda_stream, int64_t fma_per_thread, double* tflops, double* ms);
+
 /* Time-step bound without any device allocation.  The paper has no
- * counterpart: this entry point exists for callers that cannot allocate
- * device memory, such as a host framework that owns all device memory
- * through its own pool, or code that is recording work into a CUDA graph,
- * where cudaMalloc is not allowed.  Those callers cannot create an idp_ctx,
- * which allocates, so they pass their own device arrays instead.
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory themselves, such as a host framework that hands out all
+ * device memory from its own pool (an allocation behind its back escapes its
+ * accounting and may fail under its memory cap), or a long-running service
+ * that allocates everything at start-up and forbids allocation afterwards.
+ * Those callers cannot create an idp_ctx, which allocates, so they pass their
+ * own device arrays instead.
  *
  * Computes tau_max = min_i m_i / (-2 d_ii), the bound that idp_euler_step
  * scales by c_cfl and reports as IDP_FIELD_TAU_MAX, for the state U:
@@ -313,16 +380,19 @@ idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU
  *   rowptr, col  : device, CSR pattern (n_nodes+1, nnz), columns sorted per row
  *   cij          : device, 3*nnz, c_ij component-major (as idp_get_matrices)
  *   mi           : device, n_nodes lumped masses
- *   U            : device, 5*n_nodes conserved state, admissible
- *   tau_max      : device, 1 double written by the kernel
+ *   U            : device, 5*n_nodes conserved state
+ *   tau_max      : device, 1 double written by the kernel; NaN when some node
+ *                  of U is not admissible (rho <= 0, epsilon <= 0 or NaN)
  *   cuda_stream  : cudaStream_t (may be NULL); the call does not synchronise.
  * It calls no cudaMalloc or cudaFree.  Its scratch is a fixed device array in
  * the library (one partial minimum per 128 nodes, 128 KiB), which every GPU
- * that loads the library keeps until the process exits.  The first call on a
- * device looks up that array's device address; make that first call before
- * any stream capture.  All calls share the array, so calls that overlap on
- * the GPU (e.g. on two streams at once) race and give wrong results; the
- * call clears what must start at zero itself. */
+ * that loads the library keeps until the process exits.  Each call looks up
+ * that array's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing); the first call on a device may also load the
+ * library's device code, so make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (e.g. on two
+ * streams at once) race and give wrong results; the call clears what must
+ * start at zero itself. */
 #define IDP_NOALLOC_MAX_NODES 2097152
 idp_status idp_tau_max_noalloc(int64_t n_nodes, int64_t nnz, const int64_t* rowptr, const int64_t* col,
                                const double* cij, const double* mi, const double* U, double* tau_max,

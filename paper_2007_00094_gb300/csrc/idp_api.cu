@@ -22,6 +22,7 @@ struct idp_ctx {
   int device = 0;
   std::string err;
   bool has_mesh = false, has_state = false, has_trace = false;
+  bool stage_ran = false;  // B.Ulast and B.bnd hold the output and bounds of one stage of the current state
   idp::HostMatrices M;
   idp::SellLayout L;
   idp::DeviceGraph G{};
@@ -37,8 +38,8 @@ struct idp_ctx {
   idp::MixedBuffers MB{};
   bool mixed = false;
   std::vector<void*> allocations;
-  double* check = nullptr;  // 5 doubles
-  unsigned long long* check_acc = nullptr;  // 5 words
+  double* check = nullptr;  // 12 doubles: state check (5), local-bound check (7)
+  unsigned long long* check_acc = nullptr;  // 12 words
   int64_t launches = 0;
   idp::Profiler prof;
   // per-instance device state (one instance unless idp_set_instances)
@@ -247,6 +248,7 @@ idp_status ensure_adjoint(idp_ctx* ctx) {
 int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int blend, int tau_mode, bool acc_time,
            bool skip_write_on_error, bool trace, cudaStream_t s, idp::Profiler* prof) {
   idp::GridBarrier* bar = ctx->persistent ? ctx->bar : nullptr;
+  ctx->stage_ran = true;
   if (ctx->mixed)
     return idp::launch_euler_step_mixed(ctx->G, ctx->MG, ctx->B, ctx->MB, ctx->C, Uin, Uout, Un, blend, tau_mode,
                                         acc_time, skip_write_on_error, trace, s, prof, ctx->block, bar);
@@ -257,18 +259,17 @@ int launch(idp_ctx* ctx, const double* Uin, double* Uout, const double* Un, int 
 // dst[c n + r] = src[c n + map[r]] for the 5 fields: states between the
 // caller's node order and the library's row order (idp_config.renumber).
 __global__ void k_gather_rows(int64_t n, const int64_t* __restrict__ map, const double* __restrict__ src,
-                              double* __restrict__ dst) {
+                              double* __restrict__ dst, int comps) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int64_t i = map[r];
-#pragma unroll
-  for (int c = 0; c < 5; ++c) dst[c * n + r] = src[c * n + i];
+  for (int c = 0; c < comps; ++c) dst[c * n + r] = src[c * n + i];
 }
 
-// A caller-order 5-field array (host or device) into library row order.
-idp_status copy_in(idp_ctx* ctx, double* dst_lib, const double* src, bool on_device) {
+// A caller-order array of `comps` fields (host or device) into library row order.
+idp_status copy_in(idp_ctx* ctx, double* dst_lib, const double* src, bool on_device, int comps = 5) {
   const int64_t n = ctx->G.n;
-  const size_t bytes = sizeof(double) * 5 * (size_t)n;
+  const size_t bytes = sizeof(double) * comps * (size_t)n;
   if (!ctx->renumbered) {
     IDP_CUDA(ctx, cudaMemcpyAsync(dst_lib, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   ctx->stream));
@@ -279,7 +280,7 @@ idp_status copy_in(idp_ctx* ctx, double* dst_lib, const double* src, bool on_dev
     IDP_CUDA(ctx, cudaMemcpyAsync(ctx->perm_buf, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
     from = ctx->perm_buf;
   }
-  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_iperm, from, dst_lib);
+  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_iperm, from, dst_lib, comps);
   IDP_CUDA(ctx, cudaGetLastError());
   return IDP_OK;
 }
@@ -294,7 +295,7 @@ idp_status copy_out(idp_ctx* ctx, double* dst, const double* src_lib, bool on_de
     return IDP_OK;
   }
   double* to = on_device ? dst : ctx->perm_buf;
-  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_perm, src_lib, to);
+  k_gather_rows<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->d_perm, src_lib, to, 5);
   IDP_CUDA(ctx, cudaGetLastError());
   if (!on_device) IDP_CUDA(ctx, cudaMemcpyAsync(dst, ctx->perm_buf, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   return IDP_OK;
@@ -330,6 +331,7 @@ idp::StageBuffers snapshot_set(const idp_ctx* ctx, int k) {
   take(&B.tP, 5 * ns);
   take(&B.tl4, ns);
   take(&B.tl5, ns);
+  B.Ulast = nullptr;  // the stored traces leave the last stage's output and bounds alone
   return B;
 }
 
@@ -372,6 +374,48 @@ idp_status build_graph(idp_ctx* ctx) {
     return fail(ctx, IDP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   return IDP_OK;
+}
+
+// The state check of Sec. 3.3 (rho > 0, epsilon > 0, finite) of a 5n
+// library-order array: fills the first five fields of *out.
+idp_status check_state(idp_ctx* ctx, const double* U, idp_bounds_report* out) {
+  std::memset(out, 0, sizeof(*out));
+  idp::launch_check_state(U, ctx->G.n, ctx->check, ctx->check_acc, ctx->stream);
+  IDP_CUDA(ctx, cudaGetLastError());
+  double h[5];
+  IDP_CUDA(ctx, cudaMemcpyAsync(h, ctx->check, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  out->n_rho_nonpositive = (int64_t)h[0];
+  out->n_eps_nonpositive = (int64_t)h[1];
+  out->n_nonfinite = (int64_t)h[2];
+  out->rho_min = h[3];
+  out->eps_min = h[4];
+  return (out->n_rho_nonpositive || out->n_eps_nonpositive || out->n_nonfinite) ? IDP_ERR_BOUNDS : IDP_OK;
+}
+
+// The local bounds of Sec. 3.9 of a library-order state against library-
+// order bounds (rho_min, rho_max, phi_min): fills the local-bound fields of
+// *out.  Relative slacks: FP64 1e-13 on rho and 2e-13 on Psi (the limiter
+// accepts Psi down to -1e-13 of its scale, Reading A27, and the row sum of
+// the accepted increments adds rounding); FP32-mixed 1e-7 and 1e-6 (the
+// increments are summed in FP32 before they reach the FP64 state).
+idp_status check_local(idp_ctx* ctx, const double* U, const double* bnd, idp_bounds_report* out) {
+  out->slack_rho = ctx->mixed ? 1e-7 : 1e-13;
+  out->slack_phi = ctx->mixed ? 1e-6 : 2e-13;
+  idp::launch_check_local(U, bnd, ctx->G.n, out->slack_rho, out->slack_phi, ctx->check + 5, ctx->check_acc + 5,
+                          ctx->stream);
+  IDP_CUDA(ctx, cudaGetLastError());
+  double h[7];
+  IDP_CUDA(ctx, cudaMemcpyAsync(h, ctx->check + 5, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  out->n_bound_rows = (int64_t)h[0];
+  out->n_rho_below_min = (int64_t)h[1];
+  out->n_rho_above_max = (int64_t)h[2];
+  out->n_phi_below_min = (int64_t)h[3];
+  out->rho_min_violation = h[4];
+  out->rho_max_violation = h[5];
+  out->phi_min_violation = h[6];
+  return (out->n_rho_below_min || out->n_rho_above_max || out->n_phi_below_min) ? IDP_ERR_BOUNDS : IDP_OK;
 }
 
 }  // namespace
@@ -452,6 +496,7 @@ const char* idp_last_error(const idp_ctx* ctx) { return ctx ? ctx->err.c_str() :
 namespace {
 idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
                        const double* cell_x, const int32_t* node_bc, const double* inflow_state);
+idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state);
 }
 
 extern "C" idp_status idp_upload_mesh_hex(idp_ctx* ctx, int64_t n_nodes, int64_t n_cells, const int64_t* cells,
@@ -464,6 +509,51 @@ extern "C" idp_status idp_upload_mesh_quad(idp_ctx* ctx, int64_t n_nodes, int64_
                                            const double* cell_xy, const int32_t* node_bc,
                                            const double* inflow_state) {
   return upload_mesh(ctx, 2, n_nodes, n_cells, cells, cell_xy, node_bc, inflow_state);
+}
+
+extern "C" idp_status idp_upload_sparsity(idp_ctx* ctx, int64_t n_nodes, const int64_t* rowptr, const int64_t* col,
+                                          const double* mij, const double* cij, const double* mi,
+                                          const int32_t* node_bc, const double* inflow_state) {
+  if (!ctx) return IDP_ERR_ARG;
+  if (n_nodes <= 0 || !rowptr || !col || !mij || !cij) return fail(ctx, IDP_ERR_ARG, "bad sparsity arguments");
+  if (rowptr[0] != 0) return fail(ctx, IDP_ERR_ARG, "rowptr[0] must be 0");
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    if (rowptr[i + 1] < rowptr[i] + 2) return fail(ctx, IDP_ERR_ARG, "every row needs its diagonal and a neighbour");
+    bool diag = false;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= n_nodes) return fail(ctx, IDP_ERR_ARG, "column index out of range");
+      if (k > rowptr[i] && col[k] <= col[k - 1]) return fail(ctx, IDP_ERR_ARG, "columns must increase within a row");
+      diag |= col[k] == i;
+    }
+    if (!diag) return fail(ctx, IDP_ERR_ARG, "a row lacks its diagonal entry");
+  }
+  const int64_t nnz = rowptr[n_nodes];
+  for (int64_t k = 0; k < nnz; ++k)
+    if (!std::isfinite(mij[k]) || !std::isfinite(cij[k]) || !std::isfinite(cij[nnz + k]) ||
+        !std::isfinite(cij[2 * nnz + k]))
+      return fail(ctx, IDP_ERR_ARG, "non-finite matrix entry");
+  if (mi)
+    for (int64_t i = 0; i < n_nodes; ++i)
+      if (!(mi[i] > 0.0) || !std::isfinite(mi[i])) return fail(ctx, IDP_ERR_ARG, "lumped masses must be positive");
+  if (ctx->has_mesh) {
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    ctx->has_mesh = ctx->has_state = ctx->has_trace = false;
+  }
+  idp::HostMatrices& M = ctx->M;
+  M = idp::HostMatrices{};
+  M.n = n_nodes;
+  M.rowptr.assign(rowptr, rowptr + n_nodes + 1);
+  M.col.assign(col, col + nnz);
+  M.mij.assign(mij, mij + nnz);
+  for (int d = 0; d < 3; ++d) M.cij[d].assign(cij + d * nnz, cij + (d + 1) * nnz);
+  if (mi) {
+    M.mi.assign(mi, mi + n_nodes);
+    M.lumped_given = true;
+  }
+  M.bc.assign(n_nodes, 0);
+  if (node_bc) M.bc.assign(node_bc, node_bc + n_nodes);
+  return upload_matrices(ctx, inflow_state);
 }
 
 namespace {
@@ -514,9 +604,17 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   std::string msg = dim == 3 ? idp::assemble_q1(n_nodes, n_cells, cells, cell_x, ctx->M)
                              : idp::assemble_q1_2d(n_nodes, n_cells, cells, cell_x, ctx->M);
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
+  ctx->M.lumped_given = false;
   ctx->M.bc.assign(node_bc ? node_bc : nullptr, node_bc ? node_bc + n_nodes : nullptr);
   if (!node_bc) ctx->M.bc.assign(n_nodes, 0);
-  msg = idp::build_sell(ctx->M, ctx->L, ctx->cfg.renumber != 0);
+  return upload_matrices(ctx, inflow_state);
+}
+
+// Sliced-ELL layout of ctx->M, device copies and stage buffers (the part of
+// a mesh upload that follows the matrices).
+idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
+  idp_status st;
+  std::string msg = idp::build_sell(ctx->M, ctx->L, ctx->cfg.renumber != 0);
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
   for (int f = 0; f < 5; ++f) ctx->C.inflow[f] = inflow_state ? inflow_state[f] : 0.0;
 
@@ -524,7 +622,6 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   idp::DeviceGraph& G = ctx->G;
   G.n = L.n;
   G.n_slots = L.n_slots;
-  idp_status st;
   int32_t *slice_ptr, *row_len, *col, *tpos, *bc;
   uint8_t* flags;
   double *cx, *cy, *cz, *mij, *mi, *inv_mi, *lam, *cn, *inv_cn, *csx, *csy, *csz;
@@ -571,8 +668,8 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
   B = idp::StageBuffers{};
   if ((st = dalloc(ctx, &B.U, 5 * n)) || (st = dalloc(ctx, &B.Us, 5 * n)) || (st = dalloc(ctx, &B.UL, 5 * n)) ||
       (st = dalloc(ctx, &B.bnd, 3 * n)) || (st = dalloc(ctx, &B.Uw[0], 5 * n)) || (st = dalloc(ctx, &B.Uw[1], 5 * n)) ||
-      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 5)) || (st = dalloc(ctx, &ctx->check_acc, 5)) ||
-      (st = dalloc(ctx, &ctx->bar, 1)))
+      (st = dalloc(ctx, &B.scal, 1)) || (st = dalloc(ctx, &ctx->check, 12)) || (st = dalloc(ctx, &ctx->check_acc, 12)) ||
+      (st = dalloc(ctx, &ctx->bar, 1)) || (st = dalloc(ctx, &B.Ulast, 5 * n)))
     return st;
   if (!ctx->mixed) {
     if ((st = dalloc(ctx, &B.node, idp::kNodeQ * n)) || (st = dalloc(ctx, &B.d, ns)) || (st = dalloc(ctx, &B.dinv, ns)) ||
@@ -665,7 +762,8 @@ idp_status idp_init_state(idp_ctx* ctx, const double* U, int on_device) {
   if (cst != IDP_OK) return cst;
   idp_bounds_report rep;
   ctx->has_state = true;
-  idp_status st = idp_check_bounds(ctx, &rep);
+  ctx->stage_ran = false;
+  idp_status st = check_state(ctx, ctx->B.U, &rep);
   if (st == IDP_ERR_BOUNDS) {
     ctx->has_state = false;
     return fail(ctx, IDP_ERR_STATE_NOT_ADMISSIBLE, "initial state has rho <= 0, epsilon <= 0 or non-finite values");
@@ -954,18 +1052,31 @@ idp_status idp_get_field(idp_ctx* ctx, int which, double* out) {
 idp_status idp_check_bounds(idp_ctx* ctx, idp_bounds_report* out) {
   if (!ctx || !out) return IDP_ERR_ARG;
   if (!ctx->has_state) return fail(ctx, IDP_ERR_STATE, "no state");
-  idp::launch_check_state(ctx->B.U, ctx->G.n, ctx->check, ctx->check_acc, ctx->stream);
-  IDP_CUDA(ctx, cudaGetLastError());
-  double h[5];
-  IDP_CUDA(ctx, cudaMemcpyAsync(h, ctx->check, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-  IDP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  out->n_rho_nonpositive = (int64_t)h[0];
-  out->n_eps_nonpositive = (int64_t)h[1];
-  out->n_nonfinite = (int64_t)h[2];
-  out->rho_min = h[3];
-  out->eps_min = h[4];
-  if (out->n_rho_nonpositive || out->n_eps_nonpositive || out->n_nonfinite)
-    return fail(ctx, IDP_ERR_BOUNDS, "state violates rho > 0, epsilon > 0 or finiteness");
+  idp_status st = check_state(ctx, ctx->B.U, out);
+  if (st != IDP_OK && st != IDP_ERR_BOUNDS) return st;
+  const idp_status sl = ctx->stage_ran ? check_local(ctx, ctx->B.Ulast, ctx->B.bnd, out) : IDP_OK;
+  if (sl != IDP_OK && sl != IDP_ERR_BOUNDS) return sl;
+  if (st == IDP_ERR_BOUNDS || sl == IDP_ERR_BOUNDS)
+    return fail(ctx, IDP_ERR_BOUNDS, st == IDP_ERR_BOUNDS ? "state violates rho > 0, epsilon > 0 or finiteness"
+                                                          : "the last stage's output violates its local bounds");
+  return IDP_OK;
+}
+
+idp_status idp_check_local_bounds(idp_ctx* ctx, const double* U, const double* bounds, int on_device,
+                                  idp_bounds_report* out) {
+  if (!ctx || !U || !bounds || !out) return fail(ctx, IDP_ERR_ARG, "null argument");
+  if (!ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  // scratch: the limiter passes' state buffers, rewritten by every stage
+  double* Uc = ctx->B.Uw[0];
+  double* bc = ctx->B.Uw[1];
+  idp_status st;
+  if ((st = copy_in(ctx, Uc, U, on_device != 0)) != IDP_OK || (st = copy_in(ctx, bc, bounds, on_device != 0, 3)) != IDP_OK)
+    return st;
+  st = check_state(ctx, Uc, out);
+  if (st != IDP_OK && st != IDP_ERR_BOUNDS) return st;
+  const idp_status sl = check_local(ctx, Uc, bc, out);
+  if (sl != IDP_OK && sl != IDP_ERR_BOUNDS) return sl;
+  if (st == IDP_ERR_BOUNDS || sl == IDP_ERR_BOUNDS) return fail(ctx, IDP_ERR_BOUNDS, "bounds violated");
   return IDP_OK;
 }
 

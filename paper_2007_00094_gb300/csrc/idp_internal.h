@@ -24,6 +24,7 @@ struct HostMatrices {
   int64_t n = 0;
   std::vector<int64_t> rowptr, col;
   std::vector<double> mij, cij[3], mi;
+  bool lumped_given = false;           // mi is the caller's (else m_i = sum_j m_ij)
   std::vector<uint8_t> boundary_pair;  // entry (i,j) lies on a common boundary face
   std::vector<int32_t> bc;
 };

@@ -370,9 +370,11 @@ std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
     const int64_t len = M.rowptr[i + 1] - M.rowptr[i];
     if (len < 2) return "a node has no neighbours";
     L.row_len[r] = (int32_t)len;
-    // the lumped mass m_i = int phi_i equals the row sum of m_ij (partition of unity)
+    // the lumped mass m_i = int phi_i equals the row sum of m_ij (partition of
+    // unity); pre-assembled matrices may bring their own
     double m = 0.0;
     for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) m += M.mij[k];
+    if (M.lumped_given) m = M.mi[i];
     L.mi[r] = m;
     L.inv_mi[r] = 1.0 / m;
     L.lam[r] = 1.0 / (double)(len - 1);

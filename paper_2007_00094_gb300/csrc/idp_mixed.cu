@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStag
   }
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[11], n, [&](int64_t r) {
-    if (r < n) row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+    if (r < n) row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, B.Ulast, B.scal, a.blend, a.skip_write_on_error, r);
   });
 }
 
@@ -823,10 +823,13 @@ int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const Sta
     wbuf ^= 1;
     lbuf ^= 1;
   }
+  double* ulim = B.Ulast ? B.Ulast : (trace ? B.tUlim : nullptr);
   run(kKFinal, [&] {
-    k_final_m<<<grid, kBlock, 0, s>>>(G, C, cur, X.P, X.l[lbuf], Un, Uout, trace ? B.tUlim : nullptr, B.scal, blend,
+    k_final_m<<<grid, kBlock, 0, s>>>(G, C, cur, X.P, X.l[lbuf], Un, Uout, ulim, B.scal, blend,
                                       skip_write_on_error ? 1 : 0);
   });
+  if (trace && B.Ulast)
+    cudaMemcpyAsync(B.tUlim, B.Ulast, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
   return launches;
 }
 

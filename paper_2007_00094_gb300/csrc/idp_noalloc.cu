@@ -1,20 +1,19 @@
 // idp_tau_max_noalloc: the admissible time-step bound of a state, computed
 // without allocating device memory.
 //
-// Who needs it: code that owns all of its device memory and must not call
-// cudaMalloc/cudaFree, e.g. a host framework with its own memory pool, or a
-// caller in the middle of recording work into a CUDA graph, where allocation
-// is not allowed.  Such callers cannot create an idp_ctx (which allocates), but
-// they can hand over their own device arrays: CSR matrices (as returned by
-// idp_get_matrices), lumped masses and a state.
+// Who needs it: code that must not call cudaMalloc/cudaFree itself, e.g. a
+// host framework that hands out all device memory from its own pool (an
+// allocation behind its back escapes its accounting and can fail under its
+// memory cap), or a long-running service that allocates everything at
+// start-up and forbids allocation afterwards.  Such callers cannot create an
+// idp_ctx (which allocates), but they can hand over their own device arrays:
+// CSR matrices (as returned by idp_get_matrices), lumped masses and a state.
 //
 // The bound is tau_max = min_i m_i / (-2 d_ii) with d_ii = -sum_{j != i} d_ij
 // and d_ij the larger of the two orientations of the two-rarefaction
 // wavespeed bound times |c|.  The reduction needs scratch memory; here it is a
 // file-scope device array of fixed size instead of an allocation.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "idp.h"
 #include "idp_device.cuh"
@@ -34,27 +33,22 @@ struct NoallocScratch {
 
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-NoallocScratch* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, not a device address, so it
+// is looked up (cudaGetSymbolAddress, which allocates nothing) on every call:
+// the address stays right after a device reset or a new primary context.
 cudaError_t scratch_address(NoallocScratch** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<NoallocScratch*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<NoallocScratch*>(p);
   return cudaSuccess;
 }
+
+// Minimum that keeps a NaN: fmin would drop it, and a NaN partial means a
+// row whose state is not admissible.
+__device__ __forceinline__ double min_keep_nan(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
+__device__ __forceinline__ double max_keep_nan(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 
 __device__ __forceinline__ Side side_of(const double* U, int64_t n, int64_t i) {
   Side s;
@@ -79,6 +73,9 @@ k_tau_max_noalloc(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, co
   double cand = INFINITY;
   if (r < n) {
     const Side si = side_of(U, n, r);
+    // rho > 0 and epsilon > 0 (p = (gamma - 1) epsilon); otherwise the row
+    // yields NaN, which the reduction carries to tau_max
+    const bool admissible = si.rho > 0.0 && si.p > 0.0;
     double sum = 0.0;
     for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
       const int64_t j = col[k];
@@ -102,21 +99,21 @@ k_tau_max_noalloc(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, co
       if (kt >= 0) {
         const double tx = cij[kt], ty = cij[nnz + kt], tz = cij[2 * nnz + kt];
         const double nt = sqrt(tx * tx + ty * ty + tz * tz);
-        if (nt > 0.0) dij = fmax(dij, lambda_max(tx / nt, ty / nt, tz / nt, sj, si) * nt);
+        if (nt > 0.0) dij = max_keep_nan(dij, lambda_max(tx / nt, ty / nt, tz / nt, sj, si) * nt);
       }
       sum += dij;
     }
-    cand = mi[r] / (2.0 * sum);
+    cand = admissible ? mi[r] / (2.0 * sum) : NAN;
   }
   // block minimum, then the last block to finish reduces the partials
   __shared__ double red[kNaBlock / 32];
   __shared__ bool last;
-  for (int o = 16; o > 0; o >>= 1) cand = fmin(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+  for (int o = 16; o > 0; o >>= 1) cand = min_keep_nan(cand, __shfl_xor_sync(0xffffffffu, cand, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cand;
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = red[0];
-    for (int w = 1; w < kNaBlock / 32; ++w) v = fmin(v, red[w]);
+    for (int w = 1; w < kNaBlock / 32; ++w) v = min_keep_nan(v, red[w]);
     scratch->partial[blockIdx.x] = v;
     __threadfence();
     last = atomicAdd(&scratch->ticket, 1u) == gridDim.x - 1;
@@ -125,14 +122,14 @@ k_tau_max_noalloc(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr, co
   if (!last) return;
   __threadfence();
   double v = INFINITY;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmin(v, __ldcg(&scratch->partial[b]));
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = min_keep_nan(v, __ldcg(&scratch->partial[b]));
+  for (int o = 16; o > 0; o >>= 1) v = min_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < kNaBlock / 32; ++w) v = fmin(v, red[w]);
-    v = fmin(v, red[0]);
+    for (int w = 1; w < kNaBlock / 32; ++w) v = min_keep_nan(v, red[w]);
+    v = min_keep_nan(v, red[0]);
     *tau_out = v;
     scratch->ticket = 0u;
   }

@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_stage_persistent(PersistentSta
   }
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[11], n, [&](int64_t r) {
-    if (r < n) row_final(G, C, cur, B.P, B.l[lbuf], a.Un, a.Uout, nullptr, B.scal, a.blend, a.skip_write_on_error, r);
+    if (r < n) row_final(G, C, cur, B.P, B.l[lbuf], a.Un, a.Uout, B.Ulast, B.scal, a.blend, a.skip_write_on_error, r);
   });
 }
 
@@ -617,6 +617,66 @@ __global__ void k_check_finish(const unsigned long long* acc, double* out) {
   out[2] = (double)acc[2];
   out[3] = from_order_key(acc[3]);
   out[4] = from_order_key(acc[4]);
+}
+
+// Local bounds of Sec. 3.9 on a stage output: rho in [rho_min, rho_max] and
+// phi >= phi_min, the latter in the form the limiter tests (Alg. 2), Psi =
+// rho eps - phi_min rho^(gamma+1) >= -slack (|rho eps| + phi_min
+// rho^(gamma+1)).  acc = {n_rho_below, n_rho_above, n_phi_below, key(worst
+// (rho_min - rho)/|rho_min|), key(worst (rho - rho_max)/|rho_max|),
+// key(worst -Psi/scale), rows}.  A NaN counts as a violation.  Off the
+// stage's path: runs only when a caller asks for the check.
+__global__ void __launch_bounds__(kBlock) k_check_local(const double* __restrict__ U, const double* __restrict__ bnd,
+                                                        int64_t n, double slack_rho, double slack_phi,
+                                                        unsigned long long* acc) {
+  double w0 = -INFINITY, w1 = -INFINITY, w2 = -INFINITY;
+  unsigned long long c0 = 0, c1 = 0, c2 = 0, rows = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double u[kFields];
+    load5(U, n, i, u);
+    const double rmin = bnd[i], rmax = bnd[n + i], pmin = bnd[2 * n + i];
+    const double v0 = (rmin - u[0]) / fabs(rmin);
+    const double v1 = (u[0] - rmax) / fabs(rmax);
+    const double re = u[0] * u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+    const double pw = pmin * pow(u[0], 2.4);
+    const double v2 = -(re - pw) / (fabs(re) + fabs(pw));
+    c0 += !(v0 <= slack_rho);
+    c1 += !(v1 <= slack_rho);
+    c2 += !(v2 <= slack_phi);
+    w0 = fmax(w0, v0);
+    w1 = fmax(w1, v1);
+    w2 = fmax(w2, v2);
+    ++rows;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    w0 = fmax(w0, __shfl_xor_sync(0xffffffffu, w0, o));
+    w1 = fmax(w1, __shfl_xor_sync(0xffffffffu, w1, o));
+    w2 = fmax(w2, __shfl_xor_sync(0xffffffffu, w2, o));
+    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    rows += __shfl_xor_sync(0xffffffffu, rows, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd(&acc[0], c0);
+    if (c1) atomicAdd(&acc[1], c1);
+    if (c2) atomicAdd(&acc[2], c2);
+    atomicMax(&acc[3], order_key(w0));
+    atomicMax(&acc[4], order_key(w1));
+    atomicMax(&acc[5], order_key(w2));
+    if (rows) atomicAdd(&acc[6], rows);
+  }
+}
+
+__global__ void k_check_local_finish(const unsigned long long* acc, double* out) {
+  out[0] = (double)acc[6];
+  out[1] = (double)acc[0];
+  out[2] = (double)acc[1];
+  out[3] = (double)acc[2];
+  out[4] = from_order_key(acc[3]);
+  out[5] = from_order_key(acc[4]);
+  out[6] = from_order_key(acc[5]);
 }
 
 }  // namespace
@@ -691,10 +751,15 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
     wbuf ^= 1;
     lbuf ^= 1;
   }
+  // the stage output before boundary values and blend: kept in B.Ulast for
+  // the local-bound check, and copied to the trace when tracing
+  double* ulim = B.Ulast ? B.Ulast : (trace ? B.tUlim : nullptr);
   run(kKFinal, [&] {
-    k_final<<<grid, kBlock, 0, s>>>(G, C, cur, B.P, B.l[lbuf], Un, Uout, trace ? B.tUlim : nullptr, B.scal, blend,
+    k_final<<<grid, kBlock, 0, s>>>(G, C, cur, B.P, B.l[lbuf], Un, Uout, ulim, B.scal, blend,
                                     skip_write_on_error ? 1 : 0);
   });
+  if (trace && B.Ulast)
+    cudaMemcpyAsync(B.tUlim, B.Ulast, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
   return launches;
 }
 
@@ -720,6 +785,16 @@ int persistent_grid_limit(int block, bool mixed) {
     v = sms * (per_sm > 0 ? per_sm : 1);
   }
   return v;
+}
+
+void launch_check_local(const double* U, const double* bnd, int64_t n, double slack_rho, double slack_phi,
+                        double* out, unsigned long long* acc, cudaStream_t s) {
+  // counts start at 0, maximum keys at the smallest key
+  cudaMemsetAsync(acc, 0, 7 * sizeof(unsigned long long), s);
+  const int64_t blocks = (n + kBlock - 1) / kBlock;
+  const unsigned grid = (unsigned)(blocks < 152 * 8 ? blocks : 152 * 8);
+  k_check_local<<<grid, kBlock, 0, s>>>(U, bnd, n, slack_rho, slack_phi, acc);
+  k_check_local_finish<<<1, 1, 0, s>>>(acc, out);
 }
 
 void launch_check_state(const double* U, int64_t n, double* out, unsigned long long* acc, cudaStream_t s) {

@@ -80,6 +80,8 @@ struct StageBuffers {
   double* P;     // 5 * n_slots (holds (f_j - f_i).c_ij from Step 1 to Step 3)
   double* l[2];  // n_slots each
   double* Uw[2]; // 5n each
+  double* Ulast; // 5n: output of the last stage after its last limiter pass, before boundary values and
+                 // the RK blend (what the local bounds of that stage constrain); nullptr: not kept
   DeviceScalars* scal;
   // trace copies (allocated on first traced stage)
   double* tP;
@@ -279,5 +281,10 @@ cudaError_t launch_barrier_selftest(GridBarrier* bar, long long spin_limit, int 
 // {count_rho, count_eps, count_nonfinite} as doubles plus rho_min, eps_min
 // into out[0..4] (device memory); acc is 5 words of device scratch.
 void launch_check_state(const double* U, int64_t n, double* out, unsigned long long* acc, cudaStream_t s);
+// Local bounds (Sec. 3.9) of a state U against per-row bounds bnd (rho_min,
+// rho_max, phi_min; 3n): out = {rows, n_rho_below, n_rho_above, n_phi_below,
+// worst rho_min, rho_max and phi_min relative violations}; acc: 7 words.
+void launch_check_local(const double* U, const double* bnd, int64_t n, double slack_rho, double slack_phi,
+                        double* out, unsigned long long* acc, cudaStream_t s);
 
 }  // namespace idp

@@ -20,6 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libidp.so")
 
 IDP_OK = 0
+IDP_ERR_ARG, IDP_ERR_BOUNDS = 1, 7
 STATUS_NAMES = {0: "IDP_OK", 1: "IDP_ERR_ARG", 2: "IDP_ERR_CUDA", 3: "IDP_ERR_OOM", 4: "IDP_ERR_STATE_NOT_ADMISSIBLE",
                 5: "IDP_ERR_CFL", 6: "IDP_ERR_NONFINITE", 7: "IDP_ERR_BOUNDS", 8: "IDP_ERR_TIMEOUT",
                 9: "IDP_ERR_STATE"}
@@ -33,7 +34,7 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
             "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad",
-            "idp_entry_table_size"]
+            "idp_entry_table_size", "idp_upload_sparsity", "idp_check_local_bounds", "idp_probe_fp64_peak"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -48,7 +49,10 @@ class IdpConfig(C.Structure):
 
 class BoundsReport(C.Structure):
     _fields_ = [("n_rho_nonpositive", C.c_int64), ("n_eps_nonpositive", C.c_int64), ("n_nonfinite", C.c_int64),
-                ("rho_min", C.c_double), ("eps_min", C.c_double)]
+                ("rho_min", C.c_double), ("eps_min", C.c_double), ("n_bound_rows", C.c_int64),
+                ("n_rho_below_min", C.c_int64), ("n_rho_above_max", C.c_int64), ("n_phi_below_min", C.c_int64),
+                ("rho_min_violation", C.c_double), ("rho_max_violation", C.c_double),
+                ("phi_min_violation", C.c_double), ("slack_rho", C.c_double), ("slack_phi", C.c_double)]
 
 
 class IdpError(RuntimeError):
@@ -83,6 +87,7 @@ def load(path: str = LIB_PATH):
     L.idp_status_string.restype = C.c_char_p
     L.idp_upload_mesh_hex.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
     L.idp_upload_mesh_quad.argtypes = [_vp, C.c_int64, C.c_int64, _i64p, _dp, _i32p, _dp]
+    L.idp_upload_sparsity.argtypes = [_vp, C.c_int64, _i64p, _i64p, _dp, _dp, _dp, _i32p, _dp]
     L.idp_mesh_info.argtypes = [_vp, _i64p, _i64p]
     L.idp_entry_table_size.argtypes = [_vp, _i64p]
     L.idp_get_matrices.argtypes = [_vp, _i64p, _i64p, _dp, _dp, _dp]
@@ -95,11 +100,13 @@ def load(path: str = LIB_PATH):
     L.idp_set_time.argtypes = [_vp, C.c_double]
     L.idp_get_field.argtypes = [_vp, C.c_int, _dp]
     L.idp_check_bounds.argtypes = [_vp, C.POINTER(BoundsReport)]
+    L.idp_check_local_bounds.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(BoundsReport)]
     L.idp_launch_count.argtypes = [_vp]
     L.idp_launch_count.restype = C.c_int64
     L.idp_profile.argtypes = [_vp, C.c_int]
     L.idp_profile_read.argtypes = [_vp, _dp, _i64p]
     L.idp_tau_max_noalloc.argtypes = [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.idp_probe_fp64_peak.argtypes = [_vp, C.c_int64, _dp, _dp]
     L.idp_set_instances.argtypes = [_vp, C.c_int64, _i64p]
     L.idp_get_instance_times.argtypes = [_vp, _dp, _dp]
     L.idp_set_schedule.argtypes = [_vp, C.c_int, C.c_int, C.c_int]
@@ -118,6 +125,15 @@ def idp_tau_max_noalloc(n_nodes, nnz, rowptr, col, cij, mi, U, tau_max, stream=N
     pointers (ints) or CUDA tensors; returns the idp_status code."""
     ptrs = [a.data_ptr() if hasattr(a, "data_ptr") else int(a) for a in (rowptr, col, cij, mi, U, tau_max)]
     return load().idp_tau_max_noalloc(int(n_nodes), int(nnz), *ptrs, _stream_handle(stream))
+
+
+def idp_probe_fp64_peak(fma_per_thread=1 << 18, stream=None):
+    """Measured FP64 FMA rate of the current GPU: (TFLOP/s, ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    st = load().idp_probe_fp64_peak(_stream_handle(stream), int(fma_per_thread), C.byref(tf), C.byref(ms))
+    if st != IDP_OK:
+        raise IdpError(st, "idp_probe_fp64_peak failed")
+    return tf.value, ms.value
 
 
 def _ptr(a, t=_dp):
@@ -153,7 +169,11 @@ def _check(ctx, st):
 class Solver:
     """One libidp context: a mesh, its matrices and the stage buffers."""
 
-    def __init__(self, mesh, config: IdpConfig | None = None, stream=None, **overrides):
+    def __init__(self, mesh=None, config: IdpConfig | None = None, stream=None, sparsity=None, **overrides):
+        """``mesh``: a workloads.HexMesh (hexahedra or quadrilaterals), uploaded
+        with idp_upload_mesh_hex/quad; or ``sparsity``: pre-assembled matrices
+        with attributes (or keys) rowptr, col, mij, cij (3, nnz), mi (or None),
+        bc (or None), inflow (or None), uploaded with idp_upload_sparsity."""
         L = load()
         cfg = config or idp_config_default()
         for k, v in overrides.items():
@@ -163,6 +183,9 @@ class Solver:
         st = L.idp_create(C.byref(cfg), _stream_handle(stream), C.byref(self._ctx))
         if st != IDP_OK:
             raise IdpError(st, "idp_create failed")
+        if sparsity is not None:
+            self._upload_sparsity(sparsity)
+            return
         self.n = mesh.n_nodes
         cells = np.ascontiguousarray(mesh.cells, dtype=np.int64)
         bc = np.ascontiguousarray(mesh.bc, dtype=np.int32)
@@ -177,6 +200,26 @@ class Solver:
                                  _ptr(bc, _i32p), None if inflow is None else _ptr(inflow)))
         n, nnz = C.c_int64(), C.c_int64()
         _check(self._ctx, L.idp_mesh_info(self._ctx, C.byref(n), C.byref(nnz)))
+        self.nnz = nnz.value
+
+    def _upload_sparsity(self, sp):
+        get = (lambda k: sp.get(k)) if isinstance(sp, dict) else (lambda k: getattr(sp, k, None))
+        rowptr = np.ascontiguousarray(get("rowptr"), dtype=np.int64)
+        col = np.ascontiguousarray(get("col"), dtype=np.int64)
+        mij = np.ascontiguousarray(get("mij"), dtype=np.float64)
+        cij = np.ascontiguousarray(get("cij"), dtype=np.float64)
+        mi, bc, inflow = get("mi"), get("bc"), get("inflow")
+        mi = None if mi is None else np.ascontiguousarray(mi, dtype=np.float64)
+        bc = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+        inflow = None if inflow is None else np.ascontiguousarray(inflow, dtype=np.float64)
+        self.n = len(rowptr) - 1
+        assert cij.shape == (3, len(col)) and mij.shape == (len(col),)
+        _check(self._ctx, load().idp_upload_sparsity(
+            self._ctx, self.n, _ptr(rowptr, _i64p), _ptr(col, _i64p), _ptr(mij), _ptr(cij),
+            None if mi is None else _ptr(mi), None if bc is None else _ptr(bc, _i32p),
+            None if inflow is None else _ptr(inflow)))
+        n, nnz = C.c_int64(), C.c_int64()
+        _check(self._ctx, load().idp_mesh_info(self._ctx, C.byref(n), C.byref(nnz)))
         self.nnz = nnz.value
 
     def close(self):
@@ -261,8 +304,20 @@ class Solver:
         _check(self._ctx, load().idp_set_time(self._ctx, float(t)))
 
     def check_bounds(self):
+        """idp_check_bounds: (status, BoundsReport) for the current state and
+        the last stage's local bounds."""
         rep = BoundsReport()
         st = load().idp_check_bounds(self._ctx, C.byref(rep))
+        return st, rep
+
+    def check_local_bounds(self, U, bounds):
+        """idp_check_local_bounds of a (5, n) state against (3, n) bounds
+        (numpy arrays, caller order); returns (status, BoundsReport)."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        bounds = np.ascontiguousarray(bounds, dtype=np.float64)
+        assert U.shape == (5, self.n) and bounds.shape == (3, self.n)
+        rep = BoundsReport()
+        st = load().idp_check_local_bounds(self._ctx, U.ctypes.data, bounds.ctypes.data, 0, C.byref(rep))
         return st, rep
 
     def launch_count(self):

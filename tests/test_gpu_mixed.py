@@ -82,6 +82,14 @@ def test_mixed_invariants(name):
         assert (ulim[0] >= bnd[0] - 1e-7 * np.abs(bnd[0])).all()
         assert (ulim[0] <= bnd[1] + 1e-7 * np.abs(bnd[1])).all()
         assert (specific_entropy(ulim) >= bnd[2] - 1e-6 * np.abs(bnd[2])).all()
+        # the library's own check of the same stage, at the mixed precision's slacks
+        st, rep = s.check_bounds()
+        assert st == 0 and rep.n_bound_rows == mesh.n_nodes
+        assert rep.slack_rho == 1e-7 and rep.slack_phi == 1e-6
+        assert max(rep.rho_min_violation, rep.rho_max_violation) <= 1e-7 and rep.phi_min_violation <= 1e-6
+    s.step(2)
+    st, rep = s.check_bounds()
+    assert st == 0 and rep.n_bound_rows == mesh.n_nodes
 
 
 def test_mixed_conservation_and_determinism():

@@ -1,19 +1,25 @@
 """Parity of the CUDA stage (through the C ABI) with the FP64 oracle.
 
-Tolerances: per field, 1e-12 relative in the 2-norm for one euler_step and
-one SSP-RK3 step, and 1e-12 in the max-norm as well except on the isentropic
-vortex (1e-11 there, see gpu_common.ISENTROPIC_MAX_TOL); 1e-9 in the max-norm
-after 100 SSP-RK3 steps on smooth data; intermediate fields within
-1e-13..1e-12 on the state scale.  The GPU
-evaluates the same formulas in a different rounding order (FMA contraction,
-reciprocal multiplies, Newton-refined powers), so bitwise equality is not
-expected; the invariant checks hold exactly.
+Tolerances: per field, 1e-12 relative in the 2-norm and the max-norm for one
+euler_step and one SSP-RK3 step; 1e-9 in the max-norm after 100 SSP-RK3
+steps on smooth data; intermediate fields within 1e-13..1e-12 on the state
+scale.  The GPU evaluates the same formulas in a different rounding order
+(FMA contraction, reciprocal multiplies, Newton-refined powers), so bitwise
+equality is not expected; the invariant checks hold exactly.
+
+On the isentropic vortex the stage is ill-conditioned (the entropy limiter's
+root, see gpu_common.oracle_sensitivity): the oracle itself moves by up to a
+few 1e-12 when its input is perturbed by 1e-16..1e-15.  There every output
+entry must meet 1e-12 plus three times the oracle's own spread under eight
+seeded 1e-15 perturbations at that entry; entries where the oracle is stable
+therefore meet 1e-12, and the test reports how many entries needed the
+allowance.
 """
 import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import ISENTROPIC_MAX_TOL, rel_field_err, rel_field_err_l2, require_gpu
+from gpu_common import field_scales, oracle_sensitivity, rel_field_err, rel_field_err_l2, require_gpu
 from helpers import csr_rows, internal_energy, specific_entropy
 from paper_2007_00094_gb300 import workloads as W
 
@@ -65,6 +71,19 @@ def _isentropic(name):
     return name.startswith("vortex")
 
 
+def _assert_state_close(got, ref, spread=None, tol=1e-12, what=""):
+    """Max-norm per field: |got - ref| <= tol * scale_f, plus 3 x the
+    oracle's own spread at each entry when one is given."""
+    sc = field_scales(ref)[:, None]
+    err = np.abs(got - ref)
+    allow = tol * sc + (3.0 * spread if spread is not None else 0.0)
+    bad = err > allow
+    assert not bad.any(), (what, int(bad.sum()), float((err / sc).max()))
+    if spread is not None:
+        return int((err > tol * sc).sum())
+    return 0
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _gpu():
     require_gpu()
@@ -111,11 +130,20 @@ def test_euler_step_trace_parity(name, n_threads):
     np.maximum.at(var, rows, np.abs(U[:, om.col] - U[:, rows]).max(axis=0) / Umax)
     assert (np.abs(s.field("alpha") - tr["alpha"]) * var).max() <= 1e-12
     # state-sized quantities against the state scale
-    max_tol = ISENTROPIC_MAX_TOL if _isentropic(name) else 1e-12
-    for key, tol in (("UL", 1e-13), ("bounds", 1e-13), ("U5", max_tol), ("Ulim", max_tol)):
+    for key in ("UL", "bounds"):
         err = rel_field_err(s.field(key), tr[key])
-        assert err.max() <= tol, (key, err)
+        assert err.max() <= 1e-13, (key, err)
+    spread = {}
+    if _isentropic(name):
+        def run(Up):
+            o, _, st_p, t = O.euler_step(om, Up, tau=tau_ref, params=O.default_params(n_threads=n_threads),
+                                         trace=True)
+            assert st_p == 0
+            return {"U5": t["U5"], "Ulim": t["Ulim"], "out": o, "l4": t["l4"], "l5": t["l5"]}
+        _, spread = oracle_sensitivity(run, U)
+    allowed = {}
     for key in ("U5", "Ulim"):
+        allowed[key] = _assert_state_close(s.field(key), tr[key], spread.get(key), what=key)
         assert rel_field_err_l2(s.field(key), tr[key]).max() <= 1e-12, key
     # R enters the update as tau R_i / m_i, P_ij as lambda l_ij P_ij: both are
     # state increments and are compared on the state scale
@@ -128,11 +156,14 @@ def test_euler_step_trace_parity(name, n_threads):
     # values are admissible; compare l_ij weighted by the size of P_ij
     Pn = np.abs(P).max(axis=0) / Umax
     for key in ("l4", "l5"):
-        dl = np.abs(s.field(key) - tr[key])[off]
-        assert (dl * Pn[off]).max() <= (1e-9 if _isentropic(name) else 1e-11), key
+        dl = np.abs(s.field(key) - tr[key])
+        allow = 1e-11 + (3.0 * spread[key] * Pn if key in spread else 0.0)
+        assert ((dl * Pn)[off] <= np.broadcast_to(allow, dl.shape)[off]).all(), (key, (dl * Pn)[off].max())
     out = s.get_state()
-    assert rel_field_err(out, ref).max() <= max_tol
+    allowed["out"] = _assert_state_close(out, ref, spread.get("out"), what="out")
     assert rel_field_err_l2(out, ref).max() <= 1e-12
+    if spread:  # the allowance is needed on a minority of entries only
+        assert max(allowed.values()) <= 0.25 * out.size, allowed
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -142,14 +173,24 @@ def test_rk3_step_parity_and_invariants(name, n_threads):
     prm = O.default_params(n_threads=n_threads)
     s = _solver(mesh)
     s.init_state(U)
-    ref = U
-    for _ in range(3):
-        ref, tau, st = O.ssprk3_step(om, ref, prm)
-        assert st == 0
+
+    def run(U0):
+        r = U0
+        for _ in range(3):
+            r, _, st_p = O.ssprk3_step(om, r, prm)
+            assert st_p == 0
+        return {"out": r}
+
+    if _isentropic(name):
+        base, spread = oracle_sensitivity(run, U)
+        ref, spread = base["out"], spread["out"]
+    else:
+        ref, spread = run(U)["out"], None
     s.step(3)
     s.synchronize()
     out = s.get_state()
-    assert rel_field_err(out, ref).max() <= (ISENTROPIC_MAX_TOL if _isentropic(name) else 1e-12)
+    n_allowed = _assert_state_close(out, ref, spread, what="3 RK3 steps")
+    assert n_allowed <= 0.25 * out.size, n_allowed
     assert rel_field_err_l2(out, ref).max() <= 1e-12
     assert (out[0] > 0).all() and (internal_energy(out) > 0).all()
     st, rep = s.check_bounds()
@@ -158,17 +199,140 @@ def test_rk3_step_parity_and_invariants(name, n_threads):
         assert not out[3].any()
 
 
-def test_local_bounds_hold_on_gpu():
-    mesh, U = _mesh("sod_jitter")
+@pytest.mark.parametrize("name", ["sod_jitter", "vortex17", "ffs10", "wallrect_jitter"])
+def test_local_bounds_hold_on_gpu(name):
+    """rho in [rho_min, rho_max] to 1e-13 relative and phi >= phi_min to
+    3e-13 relative (the limiter's Psi margin of 1e-13 of rho eps +
+    phi_min rho^(gamma+1) ~ 2 phi_min rho^(gamma+1), plus rounding), checked
+    here on the traced fields and by the library's own idp_check_bounds."""
+    mesh, U = _mesh(name)
     s = _solver(mesh)
     s.init_state(U)
+    st, rep = s.check_bounds()
+    assert st == 0 and rep.n_bound_rows == 0  # no stage has run on this state yet
     for _ in range(5):
         s.euler_step(trace=True)
         ulim, bnd = s.field("Ulim"), s.field("bounds")
-        slack = 1e-12
-        assert (ulim[0] >= bnd[0] - slack * np.abs(bnd[0])).all()
-        assert (ulim[0] <= bnd[1] + slack * np.abs(bnd[1])).all()
-        assert (specific_entropy(ulim) >= bnd[2] - slack * np.abs(bnd[2])).all()
+        assert (ulim[0] >= bnd[0] - 1e-13 * np.abs(bnd[0])).all()
+        assert (ulim[0] <= bnd[1] + 1e-13 * np.abs(bnd[1])).all()
+        assert (specific_entropy(ulim) >= bnd[2] - 3e-13 * np.abs(bnd[2])).all()
+        st, rep = s.check_bounds()
+        assert st == 0, (rep.n_rho_below_min, rep.n_rho_above_max, rep.n_phi_below_min)
+        assert rep.n_bound_rows == mesh.n_nodes
+        assert rep.rho_min_violation <= 1e-13 and rep.rho_max_violation <= 1e-13
+        assert rep.phi_min_violation <= 2e-13
+        assert rep.slack_rho == 1e-13 and rep.slack_phi == 2e-13
+    # after whole SSP-RK3 steps the check covers the last stage of the last step
+    s.step(3)
+    st, rep = s.check_bounds()
+    assert st == 0 and rep.n_bound_rows == mesh.n_nodes
+
+
+def test_check_local_bounds_reports_planted_violations():
+    """idp_check_local_bounds on a traced stage output and its bounds: clean as
+    computed; each violation planted on the host (density below rho_min or
+    above rho_max, energy lowered so that phi < phi_min, a non-positive
+    density) is counted once, with the planted relative size as the worst
+    violation."""
+    from paper_2007_00094_gb300.idp import IDP_ERR_BOUNDS
+    mesh, U = _mesh("sod_jitter")
+    s = _solver(mesh)
+    s.init_state(U)
+    s.euler_step(trace=True)
+    ulim, bnd = s.field("Ulim"), s.field("bounds")
+    st, rep = s.check_local_bounds(ulim, bnd)
+    assert st == 0 and rep.n_bound_rows == mesh.n_nodes
+    k = 17
+    bad = ulim.copy()
+    bad[0, k] = bnd[0, k] * (1.0 - 1e-9)
+    st, rep = s.check_local_bounds(bad, bnd)
+    assert st == IDP_ERR_BOUNDS and rep.n_rho_below_min == 1 and rep.n_rho_above_max == 0
+    assert rep.rho_min_violation == pytest.approx(1e-9, rel=1e-3)
+    bad = ulim.copy()
+    bad[0, k] = bnd[1, k] * (1.0 + 1e-9)
+    st, rep = s.check_local_bounds(bad, bnd)
+    assert st == IDP_ERR_BOUNDS and rep.n_rho_above_max == 1 and rep.n_rho_below_min == 0
+    assert rep.rho_max_violation == pytest.approx(1e-9, rel=1e-3)
+    bad = ulim.copy()
+    kin = 0.5 * (bad[1:4, k] ** 2).sum() / bad[0, k]
+    eps = bnd[2, k] * bad[0, k] ** 1.4 * (1.0 - 1e-6)  # specific internal energy with phi 1e-6 below phi_min
+    bad[4, k] = kin + bad[0, k] * eps
+    st, rep = s.check_local_bounds(bad, bnd)
+    assert st == IDP_ERR_BOUNDS and rep.n_phi_below_min == 1 and rep.n_rho_below_min == 0
+    assert 4e-7 < rep.phi_min_violation < 6e-7  # -Psi / (rho eps + phi_min rho^2.4) ~ 1e-6 / 2
+    bad = ulim.copy()
+    bad[0, k] = -1.0
+    st, rep = s.check_local_bounds(bad, bnd)
+    assert st == IDP_ERR_BOUNDS and rep.n_rho_nonpositive == 1 and rep.n_rho_below_min == 1
+    # the context's own state and its last stage are untouched
+    st, rep = s.check_bounds()
+    assert st == 0 and rep.n_bound_rows == mesh.n_nodes
+
+
+@pytest.mark.parametrize("name", ["wallbox_jitter", "ffs10", "sod_jitter", "bumpy2d_jitter", "ffs2d_10"])
+def test_sparsity_upload_parity(name, n_threads):
+    """idp_upload_sparsity with the oracle's own matrices (rowptr, col, m_ij,
+    c_ij, m_i, boundary flags, inflow state): the library returns them
+    unchanged and one traced euler_step and one SSP-RK3 step meet the same
+    tolerances as with its own assembly."""
+    mesh, U = _mesh(name)
+    om = O.assemble(mesh)
+    s = _solver(None, sparsity=om)
+    assert s.n == om.n and s.nnz == om.nnz
+    rowptr, col, mij, cij, mi = s.matrices()
+    np.testing.assert_array_equal(rowptr, om.rowptr)
+    np.testing.assert_array_equal(col, om.col)
+    np.testing.assert_array_equal(mij, om.mij)
+    np.testing.assert_array_equal(cij, om.cij)
+    np.testing.assert_array_equal(mi, om.mi)
+    prm = O.default_params(n_threads=n_threads)
+    ref, tau_ref, st, tr = O.euler_step(om, U, params=prm, trace=True)
+    assert st == 0
+    s.init_state(U)
+    tau = s.euler_step(trace=True)
+    assert abs(tau - tau_ref) <= 1e-14 * tau_ref
+    assert np.abs(s.field("d") - tr["d"]).max() <= 1e-13 * np.abs(tr["d"]).max()
+    for key in ("UL", "bounds"):
+        assert rel_field_err(s.field(key), tr[key]).max() <= 1e-13, key
+    out = s.get_state()
+    assert rel_field_err(out, ref).max() <= 1e-12
+    assert rel_field_err_l2(out, ref).max() <= 1e-12
+    ref3, _, st = O.ssprk3_step(om, U, prm)
+    s.init_state(U)
+    s.step(1)
+    s.synchronize()
+    assert rel_field_err(s.get_state(), ref3).max() <= 1e-12
+
+
+def test_sparsity_upload_rejects_invalid_patterns():
+    from paper_2007_00094_gb300.idp import IdpError
+    mesh, _ = _mesh("tiny3")
+    om = O.assemble(mesh)
+    base = dict(rowptr=om.rowptr, col=om.col, mij=om.mij, cij=om.cij, mi=om.mi, bc=om.bc, inflow=None)
+    bads = []
+    c = om.col.copy()
+    c[[om.rowptr[1], om.rowptr[1] + 1]] = c[[om.rowptr[1] + 1, om.rowptr[1]]]  # unsorted row
+    bads.append(dict(base, col=c))
+    c = om.col.copy()
+    c[0] = om.n  # out of range
+    bads.append(dict(base, col=c))
+    mi = om.mi.copy()
+    mi[3] = 0.0  # non-positive lumped mass
+    bads.append(dict(base, mi=mi))
+    mij = om.mij.copy()
+    mij[5] = np.nan
+    bads.append(dict(base, mij=mij))
+    # drop one off-diagonal entry of row 0: no longer structurally symmetric
+    k = om.rowptr[0] + (1 if om.col[om.rowptr[0]] == 0 else 0)
+    keep = np.ones(om.nnz, bool)
+    keep[k] = False
+    rp = om.rowptr.copy()
+    rp[1:] -= 1
+    bads.append(dict(base, rowptr=rp, col=om.col[keep], mij=om.mij[keep], cij=om.cij[:, keep]))
+    for b in bads:
+        with pytest.raises(IdpError) as e:
+            _solver(None, sparsity=b)
+        assert e.value.status == 1  # IDP_ERR_ARG
 
 
 def test_hundred_steps_smooth_vortex(n_threads):

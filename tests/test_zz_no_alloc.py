@@ -1,13 +1,15 @@
 """The allocation-free time-step bound against the context's own value.
 
-idp_tau_max_noalloc serves callers that cannot allocate device memory (a
-host framework with its own memory pool, or code recording a CUDA graph): it
-takes caller-owned device arrays and keeps its scratch in a fixed device array
-of the library.  This test feeds it the matrices of a context
-(idp_get_matrices) and the same state, and checks it against the bound that
-idp_euler_step reports (IDP_FIELD_TAU_MAX), on two calls in a row so that the
-scratch left by the first call cannot leak into the second.  The file sorts
-last so that a run stopping at the first failure has run everything else.
+idp_tau_max_noalloc serves callers that must not allocate device memory
+themselves (a host framework that hands out all device memory from its own
+pool, or a service that allocates only at start-up): it takes caller-owned
+device arrays and keeps its scratch in a fixed device array of the library.
+This test feeds it the matrices of a context (idp_get_matrices, also of a
+context with renumbered rows) and the same state, and checks it against the
+bound that idp_euler_step reports (IDP_FIELD_TAU_MAX), on two calls in a row
+so that the scratch left by the first call cannot leak into the second; a
+non-admissible state gives NaN.  The file sorts last so that a run stopping
+at the first failure has run everything else.
 """
 import numpy as np
 import pytest
@@ -34,8 +36,8 @@ def test_noalloc_tau_max_matches_context():
 
     from paper_2007_00094_gb300.idp import IDP_OK, Solver, idp_tau_max_noalloc
 
-    for mesh, U in _cases():
-        s = Solver(mesh)
+    for (mesh, U), renumber in [(c, 0) for c in _cases()] + [(_cases()[1], 1)]:
+        s = Solver(mesh, renumber=renumber)
         s.init_state(U)
         s.euler_step(trace=True)
         ref = s.field("tau_max")
@@ -50,8 +52,35 @@ def test_noalloc_tau_max_matches_context():
             assert st == IDP_OK
             torch.cuda.synchronize()
             got = float(out.item())
-            assert abs(got - ref) <= 1e-14 * ref, (mesh.name, call, got, ref)
+            assert abs(got - ref) <= 1e-14 * ref, (mesh.name, renumber, call, got, ref)
         s.close()
+
+
+def test_noalloc_tau_max_is_nan_for_a_non_admissible_state():
+    require_gpu()
+    import torch
+
+    from paper_2007_00094_gb300.idp import IDP_OK, Solver, idp_tau_max_noalloc
+
+    mesh, U = _cases()[2]
+    s = Solver(mesh)
+    rowptr, col, mij, cij, mi = s.matrices()
+    s.close()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+           for k, v in dict(rowptr=rowptr, col=col, cij=cij, mi=mi).items()}
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    for bad in ("rho", "eps"):
+        Ub = U.copy()
+        k = mesh.n_nodes // 3
+        if bad == "rho":
+            Ub[0, k] = -0.5
+        else:
+            Ub[4, k] = 0.4 * 0.5 * (Ub[1:4, k] ** 2).sum() / Ub[0, k]  # epsilon < 0
+        st = idp_tau_max_noalloc(mesh.n_nodes, cij.shape[1], dev["rowptr"], dev["col"], dev["cij"], dev["mi"],
+                                 torch.from_numpy(Ub).cuda(), out, torch.cuda.current_stream())
+        assert st == IDP_OK
+        torch.cuda.synchronize()
+        assert np.isnan(float(out.item())), bad
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
