@@ -47,8 +47,9 @@ FP64_FLOP_PER_NNZ_EXECUTED = {"edge": 74.1, "low_order": 51.0, "flux_limit": 48.
 # the same capture: the pipe also issues compares, conversions and min/max.
 FP64_PIPE_BUSY_NCU = {"edge": 0.868, "low_order": 0.892, "flux_limit": 0.878, "limiter_pass": 0.664}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
-# FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s; a dependent-free DFMA
-# stream measured 1.197 TFLOP/s at 1.97 GHz on this machine).
+# FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s).  The roofline uses the
+# rate the library's own FMA-stream probe measures in the same run
+# (idp_probe_fp64_peak); this figure is its fallback.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # for the workloads of this file, keyed by kernel.  Captured on smaller meshes
@@ -76,6 +77,37 @@ def _hbm_peak():
         return float(json.load(open(path))["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+_PEAK64 = {}
+
+
+def fp64_peak(stream, bus_id=None):
+    """Measured FP64 FMA rate of this GPU (idp_probe_fp64_peak, best of three
+    launches) with the SM clocks sampled while it runs; falls back to the
+    unit-count figure if the probe fails.  Measured once per process."""
+    if "v" not in _PEAK64:
+        _PEAK64["v"] = _measure_fp64_peak(stream, bus_id)
+    return _PEAK64["v"]
+
+
+def _measure_fp64_peak(stream, bus_id):
+    from paper_2007_00094_gb300.idp import IdpError, idp_probe_fp64_peak
+
+    sampler = ClockSampler(bus_id=bus_id)
+    sampler.start()
+    try:
+        best = 0.0
+        for _ in range(3):
+            best = max(best, idp_probe_fp64_peak(1 << 20, stream)[0])
+    except IdpError:
+        best = None
+    clocks = sampler.stop()
+    if best is None:
+        return FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe failed)", clocks
+    mhz = clocks["sm_mhz"] if clocks else None
+    return best, (f"measured: FP64 FMA stream of libidp (idp_probe_fp64_peak), best of 3 launches, "
+                  f"median SM clock {mhz} MHz"), clocks
 
 
 def _time_steps(solver, stream, steps, warmup, profile=True):
@@ -318,8 +350,9 @@ def pattern_q1_2d(stream, args):
         per_launch_s = dom_ms / dom_n * 1e-3
         if prec == 0:
             achieved = FP64_FLOP_PER_NNZ_EXECUTED[dom] * s.nnz / per_launch_s / 1e12
-            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            peak64, peak64_src, _ = fp64_peak(stream)
+            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                    "frac": achieved / peak64, "traffic": None, "peak_source": peak64_src,
                     "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, 3D step channel) x "
                             f"{s.nnz} nnz per launch"}
         else:
@@ -447,63 +480,88 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _oracle_sample(cpu_m):
-    """The bounded CPU sample of the workload: the same channel, inflow state,
-    boundary conditions and jitter at h = 1/cpu_m, assembled by the oracle."""
+def _oracle_mesh(mesh):
+    """The oracle's own assembly of a workloads mesh, and its wall time."""
     import oracle as O
-    from paper_2007_00094_gb300 import workloads as W
 
     O.build()
-    mesh = W.forward_step_mesh(m=cpu_m, jitter=0.2, seed=2007)
     t0 = time.perf_counter()
     om = O.assemble(mesh)
-    return mesh, om, W.forward_step_state(mesh), time.perf_counter() - t0
+    return om, time.perf_counter() - t0
 
 
-def cpu_baseline(cpu_m, seconds_budget=20.0):
-    """The FP64 oracle, as it stands, on the host cores (OpenMP over rows, all
-    cores): euler_steps on the sample mesh until about seconds_budget."""
+def _oracle_rate(om, U, n_threads, seconds_budget, max_stages):
+    """euler_steps of the oracle from U until about seconds_budget (at least
+    one): node-stage updates/s and the stages run."""
     import oracle as O
 
-    mesh, om, U, t_asm = _oracle_sample(cpu_m)
-    cores = os.cpu_count() or 1
-    prm = O.default_params(n_threads=cores)
+    prm = O.default_params(n_threads=n_threads)
     stages, elapsed, V = 0, 0.0, U
-    while elapsed < seconds_budget and stages < 500:
+    while stages < 1 or (elapsed < seconds_budget and stages < max_stages):
         t0 = time.perf_counter()
         V, tau, st, _ = O.euler_step(om, V, params=prm)
         elapsed += time.perf_counter() - t0
         stages += 1
         if st != 0:
             break
-    value = mesh.n_nodes * stages / elapsed
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{stages} euler_steps of the FP64 oracle on the same channel at h = 1/{cpu_m} "
-                      f"({mesh.n_nodes} nodes), {elapsed:.1f} s; oracle assembly {t_asm:.1f} s untimed"}
+    return om.n * stages / elapsed, stages, elapsed
+
+
+def cpu_baseline(mesh, U, seconds_budget=15.0):
+    """The FP64 oracle, as it stands, on the host cores, on the benchmark's own
+    channel mesh (assembled by the oracle, untimed): OpenMP over rows on all
+    cores for about seconds_budget, and single-threaded for one euler_step
+    (results are bitwise the same; the j-loop order does not change).  Also the
+    17^3 periodic vortex run in full (20 SSP-RK3 steps) in both modes."""
+    import oracle as O
+    from paper_2007_00094_gb300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    om, t_asm = _oracle_mesh(mesh)
+    v_omp, n_omp, s_omp = _oracle_rate(om, U, cores, seconds_budget, 200)
+    v_one, n_one, s_one = _oracle_rate(om, U, 1, 0.0, 1)
+    del om
+    vm = W.vortex_mesh(17)
+    vom, _ = _oracle_mesh(vm)
+    c1 = {}
+    for label, nt in (("openmp", cores), ("single_thread", 1)):
+        t0 = time.perf_counter()
+        O.run(vom, W.vortex_state(vm), 20, O.default_params(n_threads=nt))
+        dt = time.perf_counter() - t0
+        c1[label] = {"value": vm.n_nodes * 3 * 20 / dt, "seconds": dt, "threads": nt}
+    return {"value": v_omp, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_omp} euler_steps of the FP64 oracle on the benchmark mesh itself ({mesh.n_nodes} nodes), "
+                      f"{s_omp:.1f} s on {cores} threads; oracle assembly {t_asm:.1f} s untimed",
+            "modes": {"openmp": {"value": v_omp, "threads": cores, "stages": n_omp, "seconds": s_omp},
+                      "single_thread": {"value": v_one, "threads": 1, "stages": n_one, "seconds": s_one}},
+            "vortex_17^3_20_steps_in_full": c1}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores;
-    each step is one euler_step over the sample mesh of the workload."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on all host cores
+    (OpenMP over rows), on the benchmark's own channel mesh; each step is one
+    SSP-RK3 step (three euler_steps) over every node, as in the GPU arm."""
     import oracle as O
+    from paper_2007_00094_gb300 import workloads as W
 
-    mesh, om, U, _ = _oracle_sample(args.cpu_m)
+    mesh = W.forward_step_mesh(m=args.m, jitter=0.2, seed=2007)
+    om, _ = _oracle_mesh(mesh)
+    V = W.forward_step_state(mesh)
     cores = os.cpu_count() or 1
     prm = O.default_params(n_threads=cores)
-    V = U
     for _ in range(args.warmup):
-        V, _, _, _ = O.euler_step(om, V, params=prm)
+        V, _, _ = O.ssprk3_step(om, V, prm)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        V, _, st, _ = O.euler_step(om, V, params=prm)
+        V, _, st = O.ssprk3_step(om, V, prm)
     dt = time.perf_counter() - t0
-    value = mesh.n_nodes * args.steps / dt
-    sample = (f"each step = one euler_step of the FP64 oracle on the same channel at h = 1/{args.cpu_m} "
-              f"({mesh.n_nodes} nodes)")
+    value = mesh.n_nodes * 3 * args.steps / dt
+    sample = (f"each step = one SSP-RK3 step (3 euler_steps) of the FP64 oracle on the benchmark mesh itself "
+              f"({mesh.n_nodes} nodes, {om.nnz} entries), {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(args.m, _channel_nodes(args.m), None, args),
+            "config": _config(args.m, mesh.n_nodes, om.nnz, args),
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -530,8 +588,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=120, help="cells per unit length of the channel mesh")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--cpu-m", type=int, default=60, help="mesh of the CPU oracle sample (h = 1/cpu_m)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patterns", action="store_true", help="skip the FP32-mixed / batched / adjoint lines")
     ap.add_argument("--pattern-steps", type=int, default=5)
@@ -639,6 +696,7 @@ def main():
     state_bytes = 5 * N * 8
 
     if rank == 0:
+        peak64, peak64_src, peak64_clocks = fp64_peak(stream, str(bus) if bus is not None else None)
         dom = max(prof, key=lambda k: prof[k][0])
         dom_ms, dom_n = prof[dom]
         per_launch_s = dom_ms / dom_n * 1e-3
@@ -652,9 +710,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "peak_source": "FP64 pipe from unit counts and max clock (nominal 1.25 TFLOP/s)",
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64,
+                         "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": traffic,
+                         "peak_source": peak64_src, "peak_clocks": peak64_clocks,
+                         "peak_derived_from_unit_counts": FP64_PEAK_TFLOPS,
                          "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, h = 1/80) x {nnz} "
                                  f"nnz per launch",
                          "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU.get(dom),
@@ -669,7 +728,7 @@ def main():
                                 "relaxation": pattern_relaxation(stream, args), "q1_2d": pattern_q1_2d(stream, args),
                                 "renumber": pattern_renumber(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_m, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(mesh, U0, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:

@@ -16,14 +16,17 @@ constexpr int kProbeBlock = 256;
 
 __device__ double g_probe_sink;
 
-__global__ void __launch_bounds__(kProbeBlock) k_fp64_fma_stream(int64_t iters, double seed) {
+// The trip counter is 32-bit and the loop unrolled: on this GPU 64-bit integer
+// compares issue on the FP64 pipe and would be counted against it.
+__global__ void __launch_bounds__(kProbeBlock) k_fp64_fma_stream(int iters, double seed) {
   double a[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) a[c] = seed + 1e-3 * (threadIdx.x + c);
   // x <- x * b + e with b slightly below 1 stays bounded: a fixed point near
   // e / (1 - b); nothing overflows or becomes subnormal
   const double b = 0.999999, e = 1e-6;
-  for (int64_t k = 0; k < iters; ++k) {
+#pragma unroll 4
+  for (int k = 0; k < iters; ++k) {
 #pragma unroll
     for (int c = 0; c < kChains; ++c) a[c] = fma(a[c], b, e);
   }
@@ -45,7 +48,8 @@ extern "C" idp_status idp_probe_fp64_peak(void* cuda_stream, int64_t fma_per_thr
     return IDP_ERR_CUDA;
   }
   const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
-  const int64_t iters = fma_per_thread / kChains;
+  if (fma_per_thread / kChains > (int64_t)1 << 30) return IDP_ERR_ARG;
+  const int iters = (int)(fma_per_thread / kChains);
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     cudaGetLastError();

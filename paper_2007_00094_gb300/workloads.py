@@ -427,6 +427,13 @@ def bumpy_vortex_state(mesh: HexMesh, n_bumps=8, amplitude=1e-2, width=0.1, seed
     return primitive_to_conserved(rho, u, p)
 
 
+def perturbation_directions(U, count, seed=16):
+    """Seeded directions v_k = xi_k |U| (xi_k standard normal, element-wise)
+    in the space of states, for directional-derivative checks."""
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal(U.shape) * np.abs(U) for _ in range(count)]
+
+
 def random_riemann_batch(n_instances=256, side_range=(8, 48), seed=4):
     """Independent 3D Riemann problems on slip-walled unit cubes of random size.
 
