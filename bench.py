@@ -153,7 +153,7 @@ def pattern_batched(stream, args):
         out[name] = {"value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                      "schedule": {"block": block, "cuda_graph": graph, "persistent": persistent,
                                   "autotune_ms_per_step": ms_tuned},
-                     "gpu_launches_per_step": 3 if persistent else 21}
+                     "gpu_launches_per_step": 3 if persistent else (21 if prec == 0 else 18)}
         # every schedule on the same batch, for the record
         sched = {}
         for pers in (False, True):
@@ -163,7 +163,15 @@ def pattern_batched(stream, args):
                 sched[f"{'persistent' if pers else 'per_step'}_{'graph' if g else 'stream'}"] = \
                     _time_steps(s, stream, 2, 3, profile=False)[0]
         out[name]["ms_per_step_by_schedule_at_block"] = sched
+        # per-kernel times (per-step kernels at the chosen block size) and per stored entry
+        s.set_schedule(block, False, False)
+        s.init_state(U0)
+        _, prof = _time_steps(s, stream, 2, 3, profile=True)
+        out[name]["kernels_ms_per_launch"] = {k: v[0] / v[1] for k, v in prof.items() if v[1]}
+        out[name]["kernels_ns_per_entry"] = {k: v[0] / v[1] * 1e6 / s.nnz for k, v in prof.items() if v[1]}
+        out["config"]["nnz"] = s.nnz
         s.close()
+    out["config"]["boundary_node_fraction"] = float((mesh.bc != 0).mean())
     return out
 
 
@@ -297,6 +305,78 @@ def pattern_adjoint(stream, args):
             / sum(v[0] for v in prof.values()),
             "fd_check": {"directions": args.adj_fd_directions,
                          "max_rel_err": {f"{e:.0e}": (max(v) if v else None) for e, v in fd_err.items()}}}
+
+
+def pattern_adjoint_fd(stream, args):
+    """Where the finite differences of the differentiation workload lose
+    against its derivative: central differences of J(U^N) along the seeded
+    directions for a range of eps against the CUDA adjoint's <dJ/dU^0, v>,
+    and, for the first args.adj_fd_trace_steps SSP-RK3 steps, the number of
+    limiter values whose branch (t = 0, 0 < t < 1, t = 1) differs between the
+    +eps and the -eps run (stages run one at a time with their traces, the
+    RK blend on the host)."""
+    import numpy as np
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import Solver
+    from paper_2007_00094_gb300.objectives import BoxPressure
+
+    mesh = W.vortex_mesh(args.adj_n)
+    U0 = W.bumpy_vortex_state(mesh)
+    N = args.adj_steps
+    s = Solver(mesh, stream=stream)
+    J = BoxPressure(mesh.x, s.matrices()[4])
+    s.init_state(U0)
+    s.adjoint_record(N, 10)
+    g = s.adjoint_backward(J.gradient(s.get_state()))
+    dirs = W.perturbation_directions(U0, args.adj_fd_directions, seed=16)
+
+    def run(V):
+        s.init_state(V)
+        s.step(N)
+        return J(s.get_state())
+
+    def branch(l):
+        return np.digitize(l, [1e-300, 1.0]).astype(np.uint8)
+
+    def classes(V, steps):
+        out = []
+        U = V
+        for _ in range(steps):
+            s.init_state(U)
+            tau = s.euler_step(trace=True)
+            out.append([branch(s.field("l4")), branch(s.field("l5"))])
+            E1 = s.get_state()
+            s.euler_step(tau=tau, trace=True)
+            out.append([branch(s.field("l4")), branch(s.field("l5"))])
+            U2 = 0.75 * U + 0.25 * s.get_state()
+            s.init_state(U2)
+            s.euler_step(tau=tau, trace=True)
+            out.append([branch(s.field("l4")), branch(s.field("l5"))])
+            U = 1.0 / 3.0 * U + 2.0 / 3.0 * s.get_state()
+            del E1
+        return out
+
+    eps_list = [1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10]
+    rows = []
+    for k, v in enumerate(dirs):
+        ad = float((g * v).sum())
+        row = {"adjoint": ad, "fd_rel_err": {}, "limiter_branch_changes_first_steps": {}}
+        for eps in eps_list:
+            fd = (run(U0 + eps * v) - run(U0 - eps * v)) / (2 * eps)
+            row["fd_rel_err"][f"{eps:.0e}"] = abs(fd - ad) / abs(ad)
+        if k == 0:
+            for eps in (1e-6, 1e-8):
+                cp = classes(U0 + eps * v, args.adj_fd_trace_steps)
+                cm = classes(U0 - eps * v, args.adj_fd_trace_steps)
+                row["limiter_branch_changes_first_steps"][f"{eps:.0e}"] = [
+                    int(sum((a != b).sum() for a, b in zip(x, y))) for x, y in zip(cp, cm)]
+        rows.append(row)
+    s.close()
+    return {"config": {"workload": f"bumpy_vortex_{args.adj_n}^3_periodic_8_bumps_seed5", "steps": N,
+                       "directions_seed": 16, "traced_steps": args.adj_fd_trace_steps,
+                       "entries": int(mesh.n_nodes * 27)},
+            "directions": rows}
 
 
 def pattern_relaxation(stream, args):
@@ -599,8 +679,10 @@ def main():
     ap.add_argument("--adj-n", type=int, default=64, help="nodes per axis of the adjoint workload")
     ap.add_argument("--adj-steps", type=int, default=100)
     ap.add_argument("--adj-fd-directions", type=int, default=2)
+    ap.add_argument("--adj-fd-trace-steps", type=int, default=10)
     ap.add_argument("--m2d", type=int, default=1000, help="cells per unit length of the 2D channel mesh")
-    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "relaxation", "q1_2d", "renumber"],
+    ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "adjoint_fd", "relaxation", "q1_2d",
+                                       "renumber"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -624,6 +706,7 @@ def main():
     if args.only:
         build.build()
         run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
+               "adjoint_fd": pattern_adjoint_fd,
                "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d, "renumber": pattern_renumber}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return

@@ -74,97 +74,124 @@ __global__ void __launch_bounds__(kMaxBlock) k_node(int64_t n, const double* __r
   if (i < n) row_node(n, U, Q, scal, i);
 }
 
-// Step 1: d^L_ij for the edges this row owns (j > i), stored with 1/(2 d_ij),
-// and the indicator alpha_i (Sec. 3.8) over all j in I(i).  The flux
-// differences (f_j - f_i).c_ij computed for the indicator are stored (in the
-// P buffer, free until Step 4) for the bar states and R_i of Step 3.
+// Step 1: for every unordered pair {i, j} that this row owns (kEntryUpper),
+// d^L_ij with 1/(2 d_ij), and the flux differences (f_j - f_i).c_ij with
+// m_j.c_ij, stored at both of the pair's slots.  For a bitwise skew pair
+// (c_ji = -c_ij) the transposed slot's values are bitwise those its own row
+// would compute, (f_i - f_j).c_ji = (f_j - f_i).c_ij and m_i.c_ji = -m_i.c_ij,
+// because every product and difference is rounded alike on both sides;
+// boundary pairs evaluate the transposed orientation separately.  The
+// indicator alpha_i (Sec. 3.8), which sums these over all j in I(i), is
+// formed in Step 2, and Step 3 reuses the differences for the bar states and
+// R_i.
+__device__ __forceinline__ void flux_diff(const Side& si, const Side& sj, double vxi, double vyi, double vzi,
+                                          double vxj, double vyj, double vzj, double hi, double hj, double cx,
+                                          double cy, double cz, double* df, double* mcj_out, double* mci_out) {
+  // (f_j - f_i).c_ij formed from m.c of both sides and the pressure
+  // difference: every term is rounded alike on both sides, so equal states
+  // still give exact zeros, with fewer FP64 operations than two fluxes
+  const double mcj = m_dot_c(sj.mx, sj.my, sj.mz, cx, cy, cz);
+  const double mci = m_dot_c(si.mx, si.my, si.mz, cx, cy, cz);
+  const double dp = sj.p - si.p;
+  df[0] = mcj - mci;
+  df[1] = fma(dp, cx, __dmul_rn(vxj, mcj) - __dmul_rn(vxi, mci));
+  df[2] = fma(dp, cy, __dmul_rn(vyj, mcj) - __dmul_rn(vyi, mci));
+  df[3] = fma(dp, cz, __dmul_rn(vzj, mcj) - __dmul_rn(vzi, mci));
+  df[4] = __dmul_rn(hj, mcj) - __dmul_rn(hi, mci);
+  *mcj_out = mcj;
+  *mci_out = mci;
+}
+
 __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
                                          const double* Q, double* d,
-                                         double* dinv, double* dF,
-                                         double* alpha, int64_t r) {
+                                         double* dinv, double* dF, double* mc, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
   const Side si = load_side(U, Q, n, r);
-  const double Ei = U[4 * n + r];
-  const double s_i = Q[kQS * n + r], h_i = Q[kQH * n + r];
+  const double h_i = Q[kQH * n + r];
   const double vxi = Q[kQVx * n + r], vyi = Q[kQVy * n + r], vzi = Q[kQVz * n + r];
-  double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0, b4 = 0.0;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
     const uint8_t fl = G.flags[p];
+    if (fl & kEntryDiag) {  // (f_i - f_i).c_ii = 0; the diagonal's m_i.c_ii is not used
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) dF[f * ns + p] = 0.0;
+      mc[p] = 0.0;
+      continue;
+    }
+    if (!(fl & kEntryUpper)) continue;  // written by the pair's owner
+    const int64_t j = G.col[p];
+    const int64_t pt = G.tpos[p];
     const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
     const Side sj = load_side(U, Q, n, j);
-    const double s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
-    // (f_j - f_i).c_ij formed from m.c of both sides and the pressure
-    // difference: every term is rounded alike on both sides, so equal states
-    // still give exact zeros, with fewer FP64 operations than two fluxes
-    const double mcj = m_dot_c(sj.mx, sj.my, sj.mz, cx, cy, cz);
-    const double mci = m_dot_c(si.mx, si.my, si.mz, cx, cy, cz);
-    const double dp = sj.p - si.p;
-    double df[kFields];
-    df[0] = mcj - mci;
-    df[1] = fma(dp, cx, __dmul_rn(Q[kQVx * n + j], mcj) - __dmul_rn(vxi, mci));
-    df[2] = fma(dp, cy, __dmul_rn(Q[kQVy * n + j], mcj) - __dmul_rn(vyi, mci));
-    df[3] = fma(dp, cz, __dmul_rn(Q[kQVz * n + j], mcj) - __dmul_rn(vzi, mci));
-    df[4] = __dmul_rn(h_j, mcj) - __dmul_rn(h_i, mci);
-    a += (s_j - s_i) * mcj;
+    const double h_j = Q[kQH * n + j];
+    const double vxj = Q[kQVx * n + j], vyj = Q[kQVy * n + j], vzj = Q[kQVz * n + j];
+    double df[kFields], mcj, mci;
+    flux_diff(si, sj, vxi, vyi, vzi, vxj, vyj, vzj, h_i, h_j, cx, cy, cz, df, &mcj, &mci);
 #pragma unroll
     for (int f = 0; f < kFields; ++f) dF[f * ns + p] = df[f];
-    b0 += df[0];
-    b1 += df[1];
-    b2 += df[2];
-    b3 += df[3];
-    b4 += df[4];
-    if (fl & kEntryUpper) {
-      const double nc = G.cn[p];
-      double dij = 0.0;
-      if (positive_k(nc)) {
-        const double inv = G.inv_cn[p];
-        dij = lambda_max_u(normal_speed(mci, si.inv_rho, inv), normal_speed(mcj, sj.inv_rho, inv), si, sj) * nc;
-      }
-      if (!(fl & kEntrySkew)) {  // boundary pair: evaluate the transposed orientation too
-        const int64_t pt = G.tpos[p];
-        const double nt = G.cn[pt];
-        if (positive_k(nt)) {
-          const double inv = G.inv_cn[pt];
-          dij = fmax(dij, lambda_max(G.cx[pt] * inv, G.cy[pt] * inv, G.cz[pt] * inv, sj, si) * nt);
-        }
-      }
-      d[p] = dij;
-      dinv[p] = !dzero(dij) ? 0.5 / dij : 0.0;
+    mc[p] = mcj;
+    const double nc = G.cn[p];
+    double dij = 0.0;
+    if (positive_k(nc)) {
+      const double inv = G.inv_cn[p];
+      dij = lambda_max_u(normal_speed(mci, si.inv_rho, inv), normal_speed(mcj, sj.inv_rho, inv), si, sj) * nc;
     }
+    if (fl & kEntrySkew) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) dF[f * ns + pt] = df[f];
+      mc[pt] = -mci;
+    } else {  // boundary pair: the transposed orientation separately
+      const double tx = G.cx[pt], ty = G.cy[pt], tz = G.cz[pt];
+      double dft[kFields], mcjt, mcit;
+      flux_diff(sj, si, vxj, vyj, vzj, vxi, vyi, vzi, h_j, h_i, tx, ty, tz, dft, &mcjt, &mcit);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) dF[f * ns + pt] = dft[f];
+      mc[pt] = mcjt;
+      const double nt = G.cn[pt];
+      if (positive_k(nt)) {
+        const double inv = G.inv_cn[pt];
+        dij = fmax(dij, lambda_max(tx * inv, ty * inv, tz * inv, sj, si) * nt);
+      }
+    }
+    d[p] = dij;
+    dinv[p] = !dzero(dij) ? div_pos(0.5, dij) : 0.0;
   }
-  // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
-  const double sc = s_i * si.inv_p * (1.0 / 6.0);
-  const double e0 = sc * Ei, e1 = -sc * si.mx, e2 = -sc * si.my, e3 = -sc * si.mz, e4 = sc * si.rho;
-  const double num = a - (e0 * b0 + e1 * b1 + e2 * b2 + e3 * b3 + e4 * b4) + s_i * b0;
-  const double D = fabs(a) + fabs(e0 - s_i) * fabs(b0) + fabs(e1) * fabs(b1) + fabs(e2) * fabs(b2) +
-                   fabs(e3) * fabs(b3) + fabs(e4) * fabs(b4);
-  alpha[r] = positive_k(D) ? fabs(num) / D : 0.0;
 }
 
 __global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double* __restrict__ U,
                                                  const double* __restrict__ Q, double* __restrict__ d,
                                                  double* __restrict__ dinv, double* __restrict__ dF,
-                                                 double* __restrict__ alpha, DeviceScalars* scal) {
+                                                 double* __restrict__ mc, DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < G.n_inst) G.tau_min[r] = 0x7ff0000000000000ull;  // +inf, read by the next kernel
-  if (r < G.n) row_edge(G, U, Q, d, dinv, dF, alpha, r);
+  if (r < G.n) row_edge(G, U, Q, d, dinv, dF, mc, r);
 }
 
 // Step 2: d_ij = d_ji below the diagonal, d_ii = -sum_{j != i} d_ij and the
-// CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows).
-__device__ __forceinline__ double row_diag(const DeviceGraph& G, double* d, double* dinv,
+// CFL bound min_i m_i / (-2 d_ii) (a deterministic min over all rows); and the
+// indicator alpha_i = N_i / D_i of Sec. 3.8 from the flux differences and
+// m_j.c_ij of Step 1, summed over all j in I(i) in slot order.
+__device__ __forceinline__ double row_diag(const DeviceGraph& G, const double* U, const double* Q, double* d,
+                                           double* dinv, const double* dF, const double* mc, double* alpha,
                                            int64_t r) {
+  const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
+  const double s_i = Q[kQS * n + r];
   double sum = 0.0;
+  double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0, b4 = 0.0;
   int64_t pd = base;
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
+    a = fma(Q[kQS * n + j] - s_i, mc[p], a);
+    b0 += dF[p];
+    b1 += dF[ns + p];
+    b2 += dF[2 * ns + p];
+    b3 += dF[3 * ns + p];
+    b4 += dF[4 * ns + p];
     if (j == r) {
       pd = p;
       continue;
@@ -181,13 +208,24 @@ __device__ __forceinline__ double row_diag(const DeviceGraph& G, double* d, doub
     sum += v;
   }
   d[pd] = -sum;
+  // eta'(U_i) = (rho eps)^(-7/12)/(gamma+1) (E, -m, rho) = (eta/rho) / (6 p) (E, -m, rho)
+  const double rho = U[r], mx = U[n + r], my = U[2 * n + r], mz = U[3 * n + r], Ei = U[4 * n + r];
+  const double sc = s_i * Q[kQInvP * n + r] * (1.0 / 6.0);
+  const double e0 = sc * Ei, e1 = -sc * mx, e2 = -sc * my, e3 = -sc * mz, e4 = sc * rho;
+  const double num = a - (e0 * b0 + e1 * b1 + e2 * b2 + e3 * b3 + e4 * b4) + s_i * b0;
+  const double D = fabs(a) + fabs(e0 - s_i) * fabs(b0) + fabs(e1) * fabs(b1) + fabs(e2) * fabs(b2) +
+                   fabs(e3) * fabs(b3) + fabs(e4) * fabs(b4);
+  alpha[r] = positive_k(D) ? fabs(num) / D : 0.0;
   return G.mi[r] / (2.0 * sum);
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, double* __restrict__ d, double* __restrict__ dinv,
+__global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, const double* __restrict__ U,
+                                                 const double* __restrict__ Q, double* __restrict__ d,
+                                                 double* __restrict__ dinv, const double* __restrict__ dF,
+                                                 const double* __restrict__ mc, double* __restrict__ alpha,
                                                  DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, d, dinv, r) : INFINITY);
+  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, U, Q, d, dinv, dF, mc, alpha, r) : INFINITY);
 }
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
@@ -516,11 +554,11 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_stage_persistent(PersistentSta
   });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[1], n, [&](int64_t r) {
-    if (r < n) row_edge(G, a.Uin, B.node, B.d, B.dinv, B.P, B.alpha, r);
+    if (r < n) row_edge(G, a.Uin, B.node, B.d, B.dinv, B.P, B.l[1], r);
   });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[2], n, [&](int64_t r) {
-    reduce_tau_candidate(G, r, r < n ? row_diag(G, B.d, B.dinv, r) : INFINITY);
+    reduce_tau_candidate(G, r, r < n ? row_diag(G, a.Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, r) : INFINITY);
   });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[3], n, [&](int64_t r) {
@@ -724,8 +762,9 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
     ++launches;
   };
   run(kKNode, [&] { k_node<<<grid, kBlock, 0, s>>>(G.n, Uin, B.node, B.scal); });
-  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.scal); });
-  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, B.d, B.dinv, B.scal); });
+  // m_j.c_ij of Step 1 lives in l[1] until Step 2 (l[1] is next written by the first limiter pass)
+  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.scal); });
+  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, B.scal); });
   run(kKLowOrder, [&] {
     k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
                                         tau_mode, accumulate_time ? 1 : 0);

@@ -7,6 +7,10 @@ euler_step (Alg. 1-3) and of SSP-RK3 (Sec. 3.6, eq. ssprk3), whose forward
 values are pinned to the C oracle.  Forward mode carries one tangent through
 every step, so it needs no tape and gives dJ/dU^0 . v directly, including
 the dependence of tau_n on the state (tau_n = c_cfl min_i m_i/(-2 d_ii)).
+The vortex is z-invariant away from the bumps, so z-neighbours hold bitwise
+equal states and min/max decisions tie exactly; the restatement runs with
+ties="first", the derivative convention of Reading A33 (each tie goes to
+the first operand or entry), which the CUDA adjoint follows too.
 
 Workload: the n^3 periodic isentropic vortex with eight seeded Gaussian
 density bumps (amplitude 1e-2, width 0.1, seed 5; workloads.bumpy_vortex_state),
@@ -59,6 +63,7 @@ def main():
     rec = {"source": "forward-mode AD through oracle/torch_stage.py (make_adjoint_tangents.py)",
            "workload": f"bumpy vortex {args.n}^3 periodic, 8 bumps amplitude 1e-2 width 0.1 seed 5",
            "functional": "sum over x_i in [0.4,0.6]^3 of m_i p_i(U^N) (oracle lumped masses)",
+           "ties": "first (Reading A33)",
            "n": args.n, "steps": args.steps, "cfl": 0.5, "directions_seed": 16, "J": None, "dJ_dv": [],
            "seconds": []}
     for k, v in enumerate(dirs):
@@ -66,7 +71,7 @@ def main():
         with fwAD.dual_level():
             U = fwAD.make_dual(torch.as_tensor(U0), torch.as_tensor(v))
             for _ in range(args.steps):
-                U, _ = T.ssprk3_step(tm, U)
+                U, _ = T.ssprk3_step(tm, U, ties="first")
             J = (w * T.pressure(U)).sum()
             val, tan = fwAD.unpack_dual(J)
         rec["J"] = float(val)

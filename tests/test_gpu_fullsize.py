@@ -188,3 +188,35 @@ def test_full_size_adjoint_directional_derivatives():
         ad = float((g * v).sum())
         errs = [abs((run(U + eps * v) - run(U - eps * v)) / (2 * eps) - ad) for eps in (1e-7, 1e-8, 1e-9)]
         assert min(errs) <= 1e-2 * abs(ad), (errs, ad)
+
+
+@pytest.mark.parametrize("steps", [10, 100])
+def test_full_size_adjoint_against_tangent_reference(steps):
+    """C5 at full size: 64^3 periodic vortex with eight density bumps, J = sum
+    over x_i in [0.4,0.6]^3 of m_i p_i(U^N), checkpoints every 10 steps.  The
+    CUDA adjoint's directional derivatives <dJ/dU^0, v_k> along the two seeded
+    directions of workloads.perturbation_directions against the FP64 CPU
+    tangent-linear reference (forward-mode AD through oracle/torch_stage.py,
+    stored by tests/golden/make_adjoint_tangents.py), to 1e-8 relative."""
+    import json
+    import os
+
+    from paper_2007_00094_gb300.objectives import BoxPressure
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        f"adjoint_tangents_64_{steps}steps.json")
+    with open(path) as fh:
+        ref = json.load(fh)
+    assert ref["n"] == 64 and ref["steps"] == steps and ref["directions_seed"] == 16
+    mesh = W.vortex_mesh(64)
+    U = W.bumpy_vortex_state(mesh)
+    s = _solver(mesh)
+    J = BoxPressure(mesh.x, s.matrices()[4])
+    s.init_state(U)
+    s.adjoint_record(steps, checkpoint_every=10)
+    UN = s.get_state()
+    assert abs(J(UN) - ref["J"]) <= 1e-10 * abs(ref["J"])
+    g = s.adjoint_backward(J.gradient(UN))
+    dirs = W.perturbation_directions(U, len(ref["dJ_dv"]), seed=16)
+    for v, want in zip(dirs, ref["dJ_dv"]):
+        got = float((g * v).sum())
+        assert abs(got - want) <= 1e-8 * abs(want), (steps, got, want)
