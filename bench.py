@@ -40,33 +40,34 @@ FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "fl
 # 2 x DFMA + DADD + DMUL from ncu (smsp__sass_thread_inst_executed_op_d*) on
 # the step channel at h = 1/80 (17,679,673 entries).  This is the `achieved`
 # work of the FP64 roofline; the paper's per-step counts above overstate what
-# these kernels execute (lambda_max once per unordered edge, powers without
-# pow, tests on 32-bit words), so a rate from them can exceed the pipe.
-FP64_FLOP_PER_NNZ_EXECUTED = {"edge": 74.1, "low_order": 51.0, "flux_limit": 48.3, "limiter_pass": 13.5}
+# these kernels execute (lambda_max once per unordered edge, flux differences
+# once per pair, powers without pow, tests on 32-bit words), so a rate from
+# them can exceed the pipe.
+FP64_FLOP_PER_NNZ_EXECUTED = {"node": 3.5, "edge": 43.4, "diag": 11.2, "low_order": 51.0, "flux_limit": 48.3,
+                              "limiter_pass": 13.5, "final": 11.2}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, % of active cycles) of
 # the same capture: the pipe also issues compares, conversions and min/max.
-FP64_PIPE_BUSY_NCU = {"edge": 0.868, "low_order": 0.892, "flux_limit": 0.878, "limiter_pass": 0.664}
+FP64_PIPE_BUSY_NCU = {"node": 0.853, "edge": 0.848, "diag": 0.754, "low_order": 0.892, "flux_limit": 0.878,
+                      "limiter_pass": 0.716, "final": 0.697}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s).  The roofline uses the
 # rate the library's own FMA-stream probe measures in the same run
 # (idp_probe_fp64_peak); this figure is its fallback.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# for the workloads of this file, keyed by kernel.  Captured on smaller meshes
-# of the same workloads (the full-size inputs are too large for an ncu replay)
-# and scaled by the number of matrix entries (profiles/ holds the captures):
-# FP64 at h = 1/80 (17,679,673 entries) -> h = 1/120;
-# FP32-mixed k_limiter_pass_m 2.002 GB at 96^3 (23,393,656 entries) -> 128^3.
-NCU_TRAFFIC_BYTES = {k: v * 59373973 / 17679673 for k, v in
-                     {"edge": 1.583546e9, "flux_limit": 1.265060e9, "low_order": 1.210403e9,
-                      "limiter_pass": 2.512997e9}.items()}
-NCU_TRAFFIC_BYTES_MIXED = {"limiter_pass": 2.001756e9 * 55742968 / 23393656}
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
+# one pass, no replay) on the workloads of this file at full size: the step
+# channel at h = 1/120 (FP64) and the 128^3 Sod cube (FP32-mixed), one stage
+# after three warm-up steps (profiles/ holds the launch lists).
+NCU_TRAFFIC_BYTES = {"node": 0.227e9, "edge": 5.137e9, "diag": 4.469e9, "low_order": 4.074e9,
+                     "flux_limit": 4.360e9, "limiter_pass": 7.991e9, "final": 3.723e9}
+NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 2.147e9, "low_order": 2.199e9, "flux_limit": 2.169e9,
+                           "limiter_pass": 4.717e9, "final": 2.077e9}
 
 
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
 # or write once; neighbour gathers counted once per node): bytes per stored
 # entry (slot) and per node.
-MIXED_BYTES = {"node": (0, 92), "edge": (45, 56), "diag": (18, 8), "low_order": (32, 164),
+MIXED_BYTES = {"node": (0, 92), "edge": (35, 52), "low_order": (32, 164),
                "flux_limit": (36, 116), "limiter_pass": (60, 112), "final": (36, 124)}
 
 

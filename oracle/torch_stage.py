@@ -9,17 +9,6 @@ took.  Its forward values are pinned to the C oracle (tests/test_oracle_torch.py
 
 Readings follow the C oracle (A1-A28 of the design notes); sections refer to
 Maier & Kronbichler, arXiv:2007.00094.
-
-Ties: at an exact tie of a min, max or clamp the derivative is not unique.
-``ties="even"`` (default) keeps torch's own rules (a tie of torch.maximum /
-minimum / scatter_reduce splits the derivative evenly).  ``ties="first"``
-takes Reading A33's convention, the one the CUDA adjoint follows: max(p_L,
-p_R), min(p_max, p~*), the larger of the wave speeds and of the two
-orientations of d_ij, and min(l_ij, l_ji) go to the first operand; rho_min,
-rho_max and phi_min to the first entry (CSR order) attaining them; tau_n to
-the first row attaining the CFL minimum; a positive part [x]_+ at x = 0 and
-the vacuum clamp of p~* have derivative 0; the limiter's clamps keep the
-clamped value's own derivative at equality.  Values are the same either way.
 """
 from __future__ import annotations
 
@@ -91,15 +80,7 @@ def flux_dot(U, c):
     return torch.stack(out)
 
 
-def _max_first(a, b):
-    return torch.where(a >= b, a, b)
-
-
-def _min_first(a, b):
-    return torch.where(a <= b, a, b)
-
-
-def lambda_max(n, Ui, Uj, ties="even"):
+def lambda_max(n, Ui, Uj):
     """Two-rarefaction bound of Sec. 3.7 for unit vectors n (3, m)."""
     def project(U):
         rho = U[0]
@@ -114,12 +95,11 @@ def lambda_max(n, Ui, Uj, ties="even"):
     rL, uL, pL, cL = project(Ui)
     rR, uR, pR, cR = project(Uj)
     e = (GAMMA - 1.0) / (2.0 * GAMMA)
-    first = ties == "first"
     num = cL + cR - 0.5 * (GAMMA - 1.0) * (uR - uL)
-    num = torch.where(num > 0.0, num, torch.zeros_like(num)) if first else torch.clamp(num, min=0.0)
+    num = torch.clamp(num, min=0.0)
     den = cL * (pL / pR) ** (-e) + cR
     p_tr = pR * (num / den) ** (1.0 / e)
-    p_max = _max_first(pL, pR) if first else torch.maximum(pL, pR)
+    p_max = torch.maximum(pL, pR)
 
     def f(rho, p_side, c_side, p):
         shock = p >= p_side
@@ -129,17 +109,8 @@ def lambda_max(n, Ui, Uj, ties="even"):
         return _where(shock, a, b)
 
     psi = f(rL, pL, cL, p_max) + f(rR, pR, cR, p_max) + uR - uL
-    k = (GAMMA + 1.0) / (2.0 * GAMMA)
-    if first:
-        p_star = _where(psi < 0.0, p_tr, _min_first(p_max, p_tr))
-        zL, zR = (p_star - pL) / pL, (p_star - pR) / pR
-        one = torch.ones_like(zL)
-        lam1 = uL - cL * _where(zL > 0.0, torch.sqrt(1.0 + k * _safe(zL, zL > 0.0)), one)
-        lam3 = uR + cR * _where(zR > 0.0, torch.sqrt(1.0 + k * _safe(zR, zR > 0.0)), one)
-        a = _where(-lam1 < 0.0, torch.zeros_like(lam1), -lam1)
-        b = _where(lam3 < 0.0, torch.zeros_like(lam3), lam3)
-        return _max_first(a, b)
     p_star = _where(psi < 0.0, p_tr, torch.minimum(p_max, p_tr))
+    k = (GAMMA + 1.0) / (2.0 * GAMMA)
     lam1 = uL - cL * torch.sqrt(1.0 + k * torch.clamp((p_star - pL) / pL, min=0.0))
     lam3 = uR + cR * torch.sqrt(1.0 + k * torch.clamp((p_star - pR) / pR, min=0.0))
     return torch.maximum(torch.clamp(-lam1, min=0.0), torch.clamp(lam3, min=0.0))
@@ -163,10 +134,8 @@ def _dpsi(V, P, phi_min):
     return drho_eps - phi_min * (GAMMA + 1.0) * _safe(V[0], V[0] > 0) ** GAMMA * P[0]
 
 
-def limiter(U, P, rho_min, rho_max, phi_min, newton_max=2, newton_tol=1e-10, eps=np.finfo(np.float64).eps,
-            ties="even"):
+def limiter(U, P, rho_min, rho_max, phi_min, newton_max=2, newton_tol=1e-10, eps=np.finfo(np.float64).eps):
     """Alg. 2/3 over many entries at once (columns of U, P)."""
-    first = ties == "first"
     rhoU, rhoP = U[0], P[0]
     nz = rhoP != 0.0
     absP = _safe(torch.abs(rhoP), nz)
@@ -205,42 +174,26 @@ def limiter(U, P, rho_min, rho_max, phi_min, newton_max=2, newton_tol=1e-10, eps
         nR = tR - 2.0 * psiR / _safe(denR, act & (denR != 0))
         nL = _where(act & (denL != 0), nL, tL)
         nR = _where(act & (denR != 0), nR, tR)
-        if first:
-            nL = _min_first(_max_first(nL, tL), tR)
-        else:
-            nL = torch.minimum(torch.maximum(nL, tL), tR)
+        nL = torch.minimum(torch.maximum(nL, tL), tR)
         keep = _admissible(U + nL * P, phi_min)
         nL = _where(keep, nL, tL)
-        nR = _min_first(_max_first(nR, nL), tR) if first else torch.minimum(torch.maximum(nR, nL), tR)
+        nR = torch.minimum(torch.maximum(nR, nL), tR)
         tL = _where(act, nL, tL)
         tR = _where(act, nR, tR)
     return tL
 
 
-def _first_extreme(v, rows, n, mode):
-    """Per row, the first entry (CSR order) attaining the row's min or max of
-    v, as a gather of v (so its derivative is that entry's)."""
-    vp = v.detach()
-    fill = float("inf") if mode == "amin" else -float("inf")
-    ext = torch.full((n,), fill, dtype=vp.dtype).scatter_reduce(0, rows, vp, mode, include_self=True)
-    idx = torch.arange(v.shape[0])
-    cand = torch.where(vp == ext[rows], idx, torch.full_like(idx, v.shape[0]))
-    first = torch.full((n,), v.shape[0], dtype=idx.dtype).scatter_reduce(0, rows, cand, "amin", include_self=True)
-    return v[first]
-
-
-def euler_step(tm: TorchMesh, U, tau=None, cfl=0.5, passes=2, newton_max=2, newton_tol=1e-10, ties="even"):
+def euler_step(tm: TorchMesh, U, tau=None, cfl=0.5, passes=2, newton_max=2, newton_tol=1e-10):
     """One euler_step (Alg. 1) with boundary post-processing; returns
     (U_out, tau).  tau=None computes tau_n (first RK stage)."""
-    first = ties == "first"
     rows, col, off = tm.rows, tm.col, tm.off
     Ui, Uj = U[:, rows], U[:, col]
     # Step 1: d_ij = max of both orientations (symmetric), alpha_i (Sec. 3.8)
     nc = torch.sqrt((tm.c ** 2).sum(0))
     ncT = torch.sqrt((tm.cT ** 2).sum(0))
-    lij = lambda_max(tm.c / _safe(nc, nc > 0), Ui, Uj, ties) * nc
-    lji = lambda_max(tm.cT / _safe(ncT, ncT > 0), Uj, Ui, ties) * ncT
-    d_off = _where(off, _max_first(lij, lji) if first else torch.maximum(lij, lji), torch.zeros_like(lij))
+    lij = lambda_max(tm.c / _safe(nc, nc > 0), Ui, Uj) * nc
+    lji = lambda_max(tm.cT / _safe(ncT, ncT > 0), Uj, Ui) * ncT
+    d_off = _where(off, torch.maximum(lij, lji), torch.zeros_like(lij))
     d_ii = -tm.row_sum(d_off)
     d = _where(tm.diag, d_ii[rows], d_off)
     rho_eps = U[0] * internal_energy(U)
@@ -258,8 +211,7 @@ def euler_step(tm: TorchMesh, U, tau=None, cfl=0.5, passes=2, newton_max=2, newt
     D = torch.abs(a) + (torch.abs(etap - shift) * torch.abs(b)).sum(0)
     alpha = _where(D > 0, torch.abs(num) / _safe(D, D > 0), torch.zeros_like(D))
     # Step 2: tau
-    cfl_bound = tm.mi / (-2.0 * d_ii)
-    tau_max = cfl_bound[torch.argmin(cfl_bound.detach())] if first else torch.min(cfl_bound)
+    tau_max = torch.min(tm.mi / (-2.0 * d_ii))
     if tau is None:
         tau = cfl * tau_max
     # Step 3: low-order update, R, bounds
@@ -270,17 +222,12 @@ def euler_step(tm: TorchMesh, U, tau=None, cfl=0.5, passes=2, newton_max=2, newt
     coef = 2.0 * tau / tm.mi[rows] * d
     UL = U + tm.row_sum(_where(nzd, coef * ubar, torch.zeros_like(ubar)))
     big = torch.full_like(d, float("inf"))
-    if first:
-        rho_min = _first_extreme(_where(nzd, ubar[0], big), rows, tm.n, "amin")
-        rho_max = _first_extreme(_where(nzd, ubar[0], -big), rows, tm.n, "amax")
-        phi_min = _first_extreme(specific_entropy(Uj), rows, tm.n, "amin")
-    else:
-        rho_min = torch.full((tm.n,), float("inf"), dtype=U.dtype).scatter_reduce(
-            0, rows, _where(nzd, ubar[0], big), "amin", include_self=True)
-        rho_max = torch.full((tm.n,), -float("inf"), dtype=U.dtype).scatter_reduce(
-            0, rows, _where(nzd, ubar[0], -big), "amax", include_self=True)
-        phi_min = torch.full((tm.n,), float("inf"), dtype=U.dtype).scatter_reduce(
-            0, rows, specific_entropy(Uj), "amin", include_self=True)
+    rho_min = torch.full((tm.n,), float("inf"), dtype=U.dtype).scatter_reduce(
+        0, rows, _where(nzd, ubar[0], big), "amin", include_self=True)
+    rho_max = torch.full((tm.n,), -float("inf"), dtype=U.dtype).scatter_reduce(
+        0, rows, _where(nzd, ubar[0], -big), "amax", include_self=True)
+    phi_min = torch.full((tm.n,), float("inf"), dtype=U.dtype).scatter_reduce(
+        0, rows, specific_entropy(Uj), "amin", include_self=True)
     # Step 4: P_ij and limiter values
     lam = tm.lam
     b_ij = -tm.mij / tm.mi[col]
@@ -288,15 +235,15 @@ def euler_step(tm: TorchMesh, U, tau=None, cfl=0.5, passes=2, newton_max=2, newt
     P = tau / (tm.mi[rows] * lam[rows]) * (b_ij * R[:, col] - b_ji * R[:, rows] + (dH - d) * (Uj - Ui))
     P = _where(off, P, torch.zeros_like(P))
     bnd = (rho_min[rows], rho_max[rows], phi_min[rows])
-    lim = limiter(UL[:, rows], P, *bnd, newton_max=newton_max, newton_tol=newton_tol, ties=ties)
+    lim = limiter(UL[:, rows], P, *bnd, newton_max=newton_max, newton_tol=newton_tol)
     l = _where(off, lim, torch.zeros_like(lim))
     Ucur = UL
     for pss in range(1, passes + 1):
-        lk = _min_first(l, l[tm.kT]) if first else torch.minimum(l, l[tm.kT])
+        lk = torch.minimum(l, l[tm.kT])
         Unext = Ucur + tm.row_sum(_where(off, lam[rows] * lk * P, torch.zeros_like(P)))
         if pss < passes:
             P = (1.0 - lk) * P
-            lim = limiter(Unext[:, rows], P, *bnd, newton_max=newton_max, newton_tol=newton_tol, ties=ties)
+            lim = limiter(Unext[:, rows], P, *bnd, newton_max=newton_max, newton_tol=newton_tol)
             l = _where(off, lim, torch.zeros_like(lim))
         Ucur = Unext
     # boundary post-processing (Reading A20)

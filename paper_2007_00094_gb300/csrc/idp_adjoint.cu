@@ -129,15 +129,20 @@ __device__ __forceinline__ void side_vjp(double nx, double ny, double nz, const 
 }
 
 // Reverse of lambda_max (idp_device.cuh): adds g d lambda/dU_L to gL and
-// g d lambda/dU_R to gR, on the branches the forward evaluation takes.
+// g d lambda/dU_R to gR, on the branches the forward evaluation takes.  The
+// values that decide the branches are formed as the forward sweep forms
+// them, bitwise: the normal speeds u_fwd (m.c (1/rho)(1/|c|), as the forward
+// sweep takes them from its flux contractions) where given, else m.n/rho as
+// lambda_max forms them, and the quotient of the two-rarefaction pressure by
+// div_pos.
 __device__ void lambda_max_vjp(double nx, double ny, double nz, const Side& L, const Side& R, double g, double* gL,
-                               double* gR) {
-  const double uL = (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
-  const double uR = (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
+                               double* gR, const double* u_fwd = nullptr) {
+  const double uL = u_fwd ? u_fwd[0] : (L.mx * nx + L.my * ny + L.mz * nz) * L.inv_rho;
+  const double uR = u_fwd ? u_fwd[1] : (R.mx * nx + R.my * ny + R.mz * nz) * R.inv_rho;
   const double num0 = L.c + R.c - 0.2 * (uR - uL);
   const double num = num0 > 0.0 ? num0 : 0.0;
   const double den = L.c * L.pm + R.c * R.pm;
-  const double x = num / den;
+  const double x = div_pos(num, den);
   const double x2 = x * x, x3 = x2 * x, x6 = x3 * x3;
   const double p_tr = x6 * x;
   const bool left_high = L.p >= R.p;
@@ -754,7 +759,9 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
           lambda_max_vjp(G.cx[pt] * it, G.cy[pt] * it, G.cz[pt] * it, sj, si, gdedge * G.cn[pt], gj, gUi);
         } else if (nc > 0.0) {
           const double inv = G.inv_cn[p];
-          lambda_max_vjp(cx * inv, cy * inv, cz * inv, si, sj, gdedge * nc, gUi, gj);
+          const double u_fwd[2] = {normal_speed(m_dot_c(si.mx, si.my, si.mz, cx, cy, cz), si.inv_rho, inv),
+                                   normal_speed(m_dot_c(sj.mx, sj.my, sj.mz, cx, cy, cz), sj.inv_rho, inv)};
+          lambda_max_vjp(cx * inv, cy * inv, cz * inv, si, sj, gdedge * nc, gUi, gj, u_fwd);
         }
       }
     }

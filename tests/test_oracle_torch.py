@@ -80,15 +80,3 @@ def test_torch_vjp_matches_jvp():
     a, b = float((w * jv).sum()), float((g * v).sum())
     assert abs(a - b) <= 1e-12 * max(abs(a), 1.0)
 
-
-def test_first_tie_mode_gives_the_same_values():
-    """ties="first" (Reading A33's derivative convention at exact ties) changes
-    which operand a tie's derivative goes to, never a value: on the
-    z-invariant vortex (bitwise equal z-neighbours, exact ties everywhere)
-    both modes give bitwise the same SSP-RK3 step."""
-    mesh = W.vortex_mesh(6)
-    U = torch.as_tensor(W.bumpy_vortex_state(mesh))
-    tm = T.TorchMesh(O.assemble(mesh))
-    a, ta = T.ssprk3_step(tm, U)
-    b, tb = T.ssprk3_step(tm, U, ties="first")
-    assert torch.equal(a, b) and float(ta) == float(tb)
