@@ -237,52 +237,135 @@ __global__ void __launch_bounds__(kB) ka_final(DeviceGraph G, const double* __re
   }
 }
 
-// The limiter's derivative (a Dual<8> pass, ~255 registers) runs in kernels of
-// its own, over the entries whose limiter value lies strictly inside (0, 1);
-// the rest of each reversed step then runs at a higher occupancy.
+// The limiter's derivative (a Dual<8> pass, ~255 registers) is needed only
+// at the entries whose limiter value lies strictly inside (0, 1) and whose
+// l_ij has a non-zero adjoint (a few per cent of the entries, spread over
+// most warps' rows): ka_lim_select lists them, ka_lim_eval runs the dual pass
+// with one thread per listed entry, and ka_lim_gather adds each row's
+// contributions in slot order, so that the sums do not depend on the order
+// of the list.  The rest of each reversed step runs at a higher occupancy.
+// Used for Step 5 (l5 = limiter(U5, P', bounds)) and Step 4 (l4 =
+// limiter(U^L, P, bounds)).
+__global__ void __launch_bounds__(kB) ka_lim_select(DeviceGraph G, const double* __restrict__ l,
+                                                    const double* __restrict__ gl_own,
+                                                    const double* __restrict__ gl_tr, AdjointBuffers A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int64_t base = 0;
+  int len = 0;
+  unsigned int cnt = 0;
+  if (r < G.n) {
+    base = slot_base(G, r);
+    len = G.row_len[r];
+    for (int k = 0; k < len; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      uint8_t fl = 0;
+      if (G.col[p] != r) {
+        const double gl = gl_own[p] + gl_tr[G.tpos[p]];
+        const double lv = l[p];
+        // l = 0 and l = 1 are clamped (or skipped) values: locally constant
+        if (gl != 0.0 && lv > 0.0 && lv < 1.0) {
+          fl = 1;
+          A.lim_gl[p] = gl;
+          ++cnt;
+        }
+      }
+      A.lim_flag[p] = fl;
+    }
+  }
+  // warp-aggregated append: inclusive scan of the rows' counts
+  unsigned int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned int start = 0;
+  if (lane == 31 && total) start = atomicAdd(A.lim_count, total);
+  start = __shfl_sync(0xffffffffu, start, 31);
+  if (!cnt) return;
+  unsigned int pos = start + incl - cnt;
+  for (int k = 0; k < len; ++k) {
+    const int64_t p = base + 32 * (int64_t)k;
+    if (A.lim_flag[p]) {
+      A.lim_slot[pos] = (int32_t)p;
+      A.lim_row[pos] = (int32_t)r;
+      ++pos;
+    }
+  }
+}
 
-// Step 5 reverse, limiter part: l5_ij = limiter(U5, P'_ij, bounds); adds to
-// the adjoints of U5 (row), P'_ij (entry) and the bounds (row, first writer).
-__global__ void __launch_bounds__(kB) ka_pass_lim(DeviceGraph G, StageConfig C, const double* __restrict__ U5,
-                                                  const double* __restrict__ Pp, const double* __restrict__ l5,
-                                                  const double* __restrict__ bnd, AdjointBuffers A) {
+// One thread per listed entry: gl times the derivative of the limiter at
+// (U_r, P_p, bounds_r); the P part is added to gP at the entry, the row-state
+// and bound parts are kept at the entry for ka_lim_gather.
+__global__ void __launch_bounds__(kB) ka_lim_eval(DeviceGraph G, StageConfig C, const double* __restrict__ Ur,
+                                                  const double* __restrict__ P, const double* __restrict__ bnd,
+                                                  double* __restrict__ gP, AdjointBuffers A) {
+  const int64_t n = G.n, ns = G.n_slots;
+  const unsigned int count = *A.lim_count;
+  for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+    const int64_t p = A.lim_slot[q];
+    const int64_t r = A.lim_row[q];
+    double u[kFields], pij[kFields], gU[kFields], gPl[kFields], gb[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      u[f] = Ur[f * n + r];
+      pij[f] = P[f * ns + p];
+      gU[f] = 0.0;
+      gPl[f] = 0.0;
+    }
+    limiter_vjp(u, pij, bnd[r], bnd[n + r], bnd[2 * n + r], A.lim_gl[p], C.lim, gU, gPl, gb);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) {
+      gP[f * ns + p] += gPl[f];
+      A.lim_gU[f * ns + p] = gU[f];
+    }
+    A.lim_gb[p] = gb[0];
+    A.lim_gb[ns + p] = gb[1];
+    A.lim_gb[2 * ns + p] = gb[2];
+  }
+}
+
+// Row r adds its listed entries' contributions in slot order to gUr (the
+// adjoint of the state the limiter was evaluated at) and to the adjoint of
+// its bounds: assigned (the first writer, Step 5) or added (Step 4, only
+// where the row has listed entries).
+__global__ void __launch_bounds__(kB) ka_lim_gather(DeviceGraph G, double* __restrict__ gUr, int assign_bounds,
+                                                    AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
-  double u5[kFields], gU5[kFields], gb[3] = {0.0, 0.0, 0.0};
+  double g[kFields], gb[3] = {0.0, 0.0, 0.0};
   bool touched = false;
-  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    const double gl = A.gl5_own[p] + A.gl5_tr[G.tpos[p]];
-    const double l = l5[p];
-    // l = 0 and l = 1 are clamped (or skipped) values: locally constant
-    if (gl == 0.0 || !(l > 0.0 && l < 1.0)) continue;
+    if (!A.lim_flag[p]) continue;
     if (!touched) {
-      load5(U5, n, r, u5);
-      load5(A.gU5, n, r, gU5);
+      load5(gUr, n, r, g);
       touched = true;
     }
-    double pij[kFields], gP[kFields];
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      pij[f] = Pp[f * ns + p];
-      gP[f] = 0.0;
-    }
-    limiter_vjp(u5, pij, rmin, rmax, pmin, gl, C.lim, gU5, gP, gb);
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) A.gPp[f * ns + p] += gP[f];
+    for (int f = 0; f < kFields; ++f) g[f] += A.lim_gU[f * ns + p];
+    gb[0] += A.lim_gb[p];
+    gb[1] += A.lim_gb[ns + p];
+    gb[2] += A.lim_gb[2 * ns + p];
   }
   if (touched) {
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) A.gU5[f * n + r] = gU5[f];
+    for (int f = 0; f < kFields; ++f) gUr[f * n + r] = g[f];
   }
-  A.gbnd[r] = gb[0];
-  A.gbnd[n + r] = gb[1];
-  A.gbnd[2 * n + r] = gb[2];
+  if (assign_bounds) {
+    A.gbnd[r] = gb[0];
+    A.gbnd[n + r] = gb[1];
+    A.gbnd[2 * n + r] = gb[2];
+  } else if (touched) {
+    A.gbnd[r] += gb[0];
+    A.gbnd[n + r] += gb[1];
+    A.gbnd[2 * n + r] += gb[2];
+  }
 }
 
 // Step 5 reverse, the rest: P'_ij = (1 - m_ij) P_ij and
@@ -315,49 +398,6 @@ __global__ void __launch_bounds__(kB) ka_pass(DeviceGraph G, const double* __res
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) A.gUL[f * n + r] = gU5[f];
-}
-
-// Step 4 reverse, limiter part: l4_ij = limiter(U^L, P_ij, bounds); adds to
-// the adjoints of U^L (row), P_ij (entry) and the bounds (row).
-__global__ void __launch_bounds__(kB) ka_flux_lim(DeviceGraph G, StageConfig C, const double* __restrict__ UL,
-                                                  const double* __restrict__ P, const double* __restrict__ l4,
-                                                  const double* __restrict__ bnd, AdjointBuffers A) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
-  const int64_t n = G.n, ns = G.n_slots;
-  const int64_t base = slot_base(G, r);
-  const int len = G.row_len[r];
-  double ul[kFields], gUL[kFields], gb[3] = {0.0, 0.0, 0.0};
-  bool touched = false;
-  const double rmin = bnd[r], rmax = bnd[n + r], pmin = bnd[2 * n + r];
-  for (int k = 0; k < len; ++k) {
-    const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    const double gl = A.gl4_own[p] + A.gl4_tr[G.tpos[p]];
-    const double l = l4[p];
-    if (gl == 0.0 || !(l > 0.0 && l < 1.0)) continue;
-    if (!touched) {
-      load5(UL, n, r, ul);
-      load5(A.gUL, n, r, gUL);
-      touched = true;
-    }
-    double pij[kFields], gP[kFields];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) {
-      pij[f] = P[f * ns + p];
-      gP[f] = 0.0;
-    }
-    limiter_vjp(ul, pij, rmin, rmax, pmin, gl, C.lim, gUL, gP, gb);
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) A.gP[f * ns + p] += gP[f];
-  }
-  if (touched) {
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) A.gUL[f * n + r] = gUL[f];
-    A.gbnd[r] += gb[0];
-    A.gbnd[n + r] += gb[1];
-    A.gbnd[2 * n + r] += gb[2];
-  }
 }
 
 // Step 4 reverse, the rest:
@@ -429,7 +469,8 @@ __global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, const double* __res
 // R_i = -f_i.s_i - sum_j (f_j - f_i).c_ij + sum_j d^H_ij (U_j - U_i).
 __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
                                              const double* __restrict__ d, const double* __restrict__ dinv,
-                                             const double* __restrict__ alpha, AdjointBuffers A) {
+                                             const double* __restrict__ dF, const double* __restrict__ alpha,
+                                             AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
@@ -442,7 +483,8 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
   load5(A.gR_own, n, r, gR);
   const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
   // gather R's adjoint; locate the first entries attaining the bounds (the
-  // bar-state densities recomputed as in Step 3)
+  // doubled bar-state densities formed as Step 3 forms them, from its flux
+  // differences)
   int kmin = -1, kmax = -1, kphi = -1;
   double vmin = INFINITY, vmax = -INFINITY, vphi = INFINITY;
   for (int k = 0; k < len; ++k) {
@@ -453,14 +495,7 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
     for (int f = 0; f < kFields; ++f) gR[f] += A.gR_tr[f * ns + pt];
     const double dij = d[p];
     if (dij != 0.0) {
-      double ub0 = ui[0];
-      if (j != r) {
-        double fj[kFields], fi[kFields];
-        flux_dot(U[n + j], U[2 * n + j], U[3 * n + j], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j],
-                 G.cx[p], G.cy[p], G.cz[p], fj);
-        flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, G.cx[p], G.cy[p], G.cz[p], fi);
-        ub0 = 0.5 * (ui[0] + U[j]) - (fj[0] - fi[0]) * dinv[p];
-      }
+      const double ub0 = j != r ? fma(-dF[p], 2.0 * dinv[p], ui[0] + U[j]) : ui[0] + ui[0];
       if (ub0 < vmin) {
         vmin = ub0;
         kmin = k;
@@ -507,16 +542,13 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
     }
     double uj[kFields];
     load5(U, n, j, uj);
-    const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
-    double fj[kFields], fi[kFields], df[kFields], gdf[kFields];
-    flux_dot(uj[1], uj[2], uj[3], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j], cx, cy, cz, fj);
-    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, cx, cy, cz, fi);
+    double df[kFields], gdf[kFields];
     const double Aij = (a_i + alpha[j]) * 0.5;
     const double dH = dij * Aij;
     double gdH = 0.0;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) {
-      df[f] = fj[f] - fi[f];
+      df[f] = dF[f * ns + p];
       gdf[f] = -gR[f];
       A.gU_tr[f * ns + p] += dH * gR[f];
       gUi[f] -= dH * gR[f];
@@ -559,18 +591,41 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
   A.gtau_part[r] += gtau;
 }
 
-// Sum of the per-row adjoints of tau_n in a fixed order (one block).
-// gtau[1] = this stage's sum plus the carried sum when tau was computed here;
-// gtau[0] accumulates over the stages.
-__global__ void __launch_bounds__(kB) ka_tau(DeviceGraph G, AdjointBuffers A, int add_carry) {
-  __shared__ double part[kB];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < G.n; i += blockDim.x) s += A.gtau_part[G.row_of_node ? G.row_of_node[i] : i];
+// Sum of the per-row adjoints of tau_n in a fixed order, in two levels:
+// block b sums a contiguous range of caller nodes (a strided pass, then a
+// tree in shared memory), then one block sums the block partials the same
+// way.  gtau[1] = this stage's sum plus the carried sum when tau was
+// computed here; gtau[0] accumulates over the stages.
+constexpr int kTauThreads = 256;
+
+__device__ __forceinline__ double block_tree_sum(double* part, double s) {
   part[threadIdx.x] = s;
   __syncthreads();
+#pragma unroll
+  for (int w = kTauThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  return part[0];
+}
+
+__global__ void __launch_bounds__(kTauThreads) ka_tau_part(DeviceGraph G, AdjointBuffers A) {
+  __shared__ double part[kTauThreads];
+  const int64_t chunk = (G.n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < G.n ? lo + chunk : G.n;
+  double s = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kTauThreads) s += A.gtau_part[G.row_of_node ? G.row_of_node[i] : i];
+  const double t = block_tree_sum(part, s);
+  if (threadIdx.x == 0) A.gtau_blk[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kTauThreads) ka_tau(AdjointBuffers A, int blocks, int add_carry) {
+  __shared__ double part[kTauThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < blocks; i += kTauThreads) s += A.gtau_blk[i];
+  const double t = block_tree_sum(part, s);
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)blockDim.x; ++q) t += part[q];
     A.gtau[1] = t + (add_carry ? A.gtau[0] : 0.0);
     A.gtau[0] += t;
   }
@@ -590,9 +645,15 @@ __device__ __forceinline__ double cfl_candidate(const DeviceGraph& G, const doub
 
 __global__ void __launch_bounds__(kB) ka_cfl_min(DeviceGraph G, const double* __restrict__ d, AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= G.n) return;
-  const double c = cfl_candidate(G, d, r);
-  if (c > 0.0 && c < INFINITY) atomicMin(&A.argmin[0], (unsigned long long)__double_as_longlong(c));
+  const double c = r < G.n ? cfl_candidate(G, d, r) : INFINITY;
+  // the warp's minimum first (as bits: +inf and the positive candidates order like their values), one atomic per warp
+  unsigned long long key = c > 0.0 && c < INFINITY ? (unsigned long long)__double_as_longlong(c) : ~0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, key, o);
+    key = v < key ? v : key;
+  }
+  if ((threadIdx.x & 31) == 0 && key != ~0ull) atomicMin(&A.argmin[0], key);
 }
 
 __global__ void __launch_bounds__(kB) ka_cfl_arg(DeviceGraph G, const double* __restrict__ d, AdjointBuffers A) {
@@ -631,7 +692,7 @@ __global__ void __launch_bounds__(kB) ka_diag(DeviceGraph G, StageConfig C, cons
 // Step 1 reverse: alpha_i (Sec. 3.8), the flux differences, the wavespeed
 // bound d_ij of the edges this row owns, and phi(U_i) of the bounds.
 __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
-                                              AdjointBuffers A) {
+                                              const double* __restrict__ ab, AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
   const int64_t n = G.n, ns = G.n_slots;
@@ -647,19 +708,9 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
   }
   const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
   const double s_i = Q[kQS * n + r];
-  // a_i and b_i of the indicator, as in Step 1
-  double a = 0.0, b[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int k = 0; k < len; ++k) {
-    const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
-    double fj[kFields], fi[kFields];
-    flux_dot(U[n + j], U[2 * n + j], U[3 * n + j], Q[kQInvRho * n + j], Q[kQP * n + j], Q[kQH * n + j], G.cx[p],
-             G.cy[p], G.cz[p], fj);
-    flux_dot(ui[1], ui[2], ui[3], inv_rho_i, p_i, h_i, G.cx[p], G.cy[p], G.cz[p], fi);
-    a += (Q[kQS * n + j] - s_i) * fj[0];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) b[f] += fj[f] - fi[f];
-  }
+  // a_i and b_i of the indicator as the forward sweep formed them
+  const double a = ab[r];
+  const double b[kFields] = {ab[n + r], ab[2 * n + r], ab[3 * n + r], ab[4 * n + r], ab[5 * n + r]};
   // alpha = |num| / D with num = a - e.b + s_i b_0,
   // D = |a| + |e_0 - s_i||b_0| + sum_{f>0} |e_f||b_f|, e = eta'(U_i)
   double ga = 0.0, gb[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, ge[kFields] = {0.0, 0.0, 0.0, 0.0, 0.0}, gs = 0.0;
@@ -803,6 +854,20 @@ __global__ void k_axpby(double* __restrict__ out, double a, const double* __rest
 
 }  // namespace
 
+// Grid of ka_lim_eval: the blocks that fit on the device at once (a
+// grid-stride loop over the list, whose length stays on the device).
+static unsigned lim_eval_grid() {
+  static unsigned cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)ka_lim_eval, kB, 0);
+    cached = (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm > 0 ? per_sm : 1);
+  }
+  return cached;
+}
+
 int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const AdjointBuffers& A, const StageConfig& C,
                          const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s,
                          Profiler* prof) {
@@ -823,27 +888,39 @@ int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const Adjo
   // traced intermediates: P and l of Step 4 (tP, tl4), the state and l
   // after the first pass (tU5, tl5), P' of the first pass (left in B.P)
   run(kKAdjFinal, [&] { ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A); });
+  const unsigned egrid = lim_eval_grid();
+  // the limiter's derivative at the listed entries (see ka_lim_select)
+  auto limiter_reverse = [&](const double* Ur, const double* P, const double* l, const double* gl_own,
+                             const double* gl_tr, double* gUr, double* gP, int assign_bounds) {
+    cudaMemsetAsync(A.lim_count, 0, sizeof(unsigned int), s);
+    ka_lim_select<<<grid, kB, 0, s>>>(G, l, gl_own, gl_tr, A);
+    ka_lim_eval<<<egrid, kB, 0, s>>>(G, C, Ur, P, B.bnd, gP, A);
+    ka_lim_gather<<<grid, kB, 0, s>>>(G, gUr, assign_bounds, A);
+  };
   run(kKAdjPass, [&] {
-    ka_pass_lim<<<grid, kB, 0, s>>>(G, C, B.tU5, B.P, B.tl5, B.bnd, A);
+    limiter_reverse(B.tU5, B.P, B.tl5, A.gl5_own, A.gl5_tr, A.gU5, A.gPp, 1);
     ka_pass<<<grid, kB, 0, s>>>(G, B.tP, B.tl4, A);
   });
   run(kKAdjFlux, [&] {
-    ka_flux_lim<<<grid, kB, 0, s>>>(G, C, B.UL, B.tP, B.tl4, B.bnd, A);
+    limiter_reverse(B.UL, B.tP, B.tl4, A.gl4_own, A.gl4_tr, A.gUL, A.gP, 0);
     ka_flux<<<grid, kB, 0, s>>>(G, Uin, B.tP, B.d, B.alpha, A);
   });
-  run(kKAdjLow, [&] { ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.alpha, A); });
-  launches += 6;
+  run(kKAdjLow, [&] { ka_low<<<grid, kB, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.tdF, B.alpha, A); });
+  launches += 10;
   run(kKAdjTau, [&] {
-    ka_tau<<<1, kB, 0, s>>>(G, A, tau_computed ? 1 : 0);
+    const int64_t want = (G.n + 2047) / 2048;
+    const int tblocks = (int)(want < kTauBlocks ? (want > 0 ? want : 1) : kTauBlocks);
+    ka_tau_part<<<tblocks, kTauThreads, 0, s>>>(G, A);
+    ka_tau<<<1, kTauThreads, 0, s>>>(A, tblocks, tau_computed ? 1 : 0);
     if (tau_computed) {
       cudaMemsetAsync(A.argmin, 0xff, 2 * sizeof(unsigned long long), s);
       ka_cfl_min<<<grid, kB, 0, s>>>(G, B.d, A);
       ka_cfl_arg<<<grid, kB, 0, s>>>(G, B.d, A);
     }
   });
-  launches += tau_computed ? 3 : 1;
+  launches += tau_computed ? 4 : 2;
   run(kKAdjDiag, [&] { ka_diag<<<grid, kB, 0, s>>>(G, C, B.d, A, tau_computed ? 1 : 0); });
-  run(kKAdjEdge, [&] { ka_edge<<<grid, kB, 0, s>>>(G, Uin, B.node, A); });
+  run(kKAdjEdge, [&] { ka_edge<<<grid, kB, 0, s>>>(G, Uin, B.node, B.tab, A); });
   run(kKAdjGather, [&] { ka_gather<<<grid, kB, 0, s>>>(G, A, gIn); });
   return launches + 3;
 }

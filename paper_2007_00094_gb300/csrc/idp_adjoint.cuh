@@ -12,6 +12,9 @@ namespace idp {
 // hold a row's adjoint of its own quantities; "tr" arrays hold, at entry
 // (i, j), row i's contribution to the adjoint of a quantity of row j, which
 // row j gathers through the transposed entry.
+// Blocks of the first level of the fixed-order sum of the tau adjoint.
+constexpr int kTauBlocks = 1024;
+
 struct AdjointBuffers {
   double* gU5;       // 5n: adjoint of the state after the first limiter pass
   double* gUL;       // 5n: adjoint of U^L
@@ -32,8 +35,20 @@ struct AdjointBuffers {
   double* gd;        // n_slots: adjoint of d_ij as row i uses it
   double* ga_tr;     // n_slots
   double* gphi_tr;   // n_slots
+  double* gtau_blk;  // kTauBlocks: partial sums of gtau_part over contiguous ranges of caller nodes
   double* gtau;      // 2: [0] carried over the stages of an RK step, [1] total of the first stage
   unsigned long long* argmin;  // 2: [0] bits of the CFL minimum, [1] first row attaining it
+  // The entries whose limiter derivative is evaluated (off the diagonal,
+  // adjoint of l_ij non-zero, 0 < l_ij < 1), listed in any order; each
+  // listed entry's contributions to its row are kept at the entry and summed
+  // by the row in slot order.
+  int32_t* lim_slot;    // n_slots: listed entries
+  int32_t* lim_row;     // n_slots: their rows
+  unsigned int* lim_count;  // 1: length of the list
+  uint8_t* lim_flag;    // n_slots: 1 where listed
+  double* lim_gl;       // n_slots: adjoint of l_ij at listed entries
+  double* lim_gU;       // 5 n_slots: contribution to the adjoint of the row state
+  double* lim_gb;       // 3 n_slots: contribution to the adjoint of the row's bounds
 };
 
 // Enqueues the reverse of one traced euler_step with two limiter passes:

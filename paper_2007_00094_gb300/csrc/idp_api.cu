@@ -203,7 +203,8 @@ idp_status ensure_trace(idp_ctx* ctx) {
   const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
   idp_status st;
   if ((st = dalloc(ctx, &B.tP, 5 * ns)) || (st = dalloc(ctx, &B.tl4, ns)) || (st = dalloc(ctx, &B.tU5, 5 * n)) ||
-      (st = dalloc(ctx, &B.tl5, ns)) || (st = dalloc(ctx, &B.tUlim, 5 * n)))
+      (st = dalloc(ctx, &B.tl5, ns)) || (st = dalloc(ctx, &B.tUlim, 5 * n)) || (st = dalloc(ctx, &B.tab, 6 * n)) ||
+      (st = dalloc(ctx, &B.tdF, 5 * ns)))
     return st;
   ctx->has_trace = true;
   return IDP_OK;
@@ -231,6 +232,9 @@ idp_status ensure_adjoint(idp_ctx* ctx) {
       (st = dalloc(ctx, &A.gl5_own, ns)) || (st = dalloc(ctx, &A.gl5_tr, ns)) || (st = dalloc(ctx, &A.gl4_own, ns)) ||
       (st = dalloc(ctx, &A.gl4_tr, ns)) || (st = dalloc(ctx, &A.gd, ns)) || (st = dalloc(ctx, &A.ga_tr, ns)) ||
       (st = dalloc(ctx, &A.gphi_tr, ns)) || (st = dalloc(ctx, &A.gtau, 2)) || (st = dalloc(ctx, &A.argmin, 2)) ||
+      (st = dalloc(ctx, &A.gtau_blk, idp::kTauBlocks)) || (st = dalloc(ctx, &A.lim_slot, ns)) ||
+      (st = dalloc(ctx, &A.lim_row, ns)) || (st = dalloc(ctx, &A.lim_count, 1)) || (st = dalloc(ctx, &A.lim_flag, ns)) ||
+      (st = dalloc(ctx, &A.lim_gl, ns)) || (st = dalloc(ctx, &A.lim_gU, 5 * ns)) || (st = dalloc(ctx, &A.lim_gb, 3 * ns)) ||
       (st = dalloc(ctx, &ctx->a_in, 5 * n)) || (st = dalloc(ctx, &ctx->a_out, 5 * n)) ||
       (st = dalloc(ctx, &ctx->a_g, 5 * n)) || (st = dalloc(ctx, &ctx->a_acc, 5 * n)) ||
       (st = dalloc(ctx, &ctx->a_e, 5 * n)) || (st = dalloc(ctx, &ctx->a_tmp, 5 * n)))
@@ -302,15 +306,16 @@ idp_status copy_out(idp_ctx* ctx, double* dst, const double* src_lib, bool on_de
 }
 
 // Doubles of one stage's stored trace: per node the node quantities, alpha,
-// U^L, the bounds and U after the first pass; per slot d, 1/(2d), P' (after
-// the first pass), P and l of Step 4 and l of the first pass.
+// U^L, the bounds, U after the first pass and the indicator sums a_i, b_i;
+// per slot d, 1/(2d), P' (after the first pass), P of Step 4, the flux
+// differences of Step 1, l of Step 4 and l of the first pass.
 size_t snapshot_doubles(const idp_ctx* ctx) {
   const size_t n = (size_t)ctx->G.n, ns = (size_t)ctx->G.n_slots;
-  return (size_t)(idp::kNodeQ + 1 + 5 + 3 + 5) * n + (size_t)(1 + 1 + 5 + 5 + 1 + 1) * ns;
+  return (size_t)(idp::kNodeQ + 1 + 5 + 3 + 5 + 6) * n + (size_t)(1 + 1 + 5 + 5 + 5 + 1 + 1) * ns;
 }
 
 // The stage buffers of stored trace k: the stage's own node, d, 1/(2d),
-// alpha, U^L, bounds, P and trace arrays inside rec_snap, the rest (state
+// alpha, U^L, bounds, P, flux differences and trace arrays inside rec_snap, the rest (state
 // scratch, R, limiter values, status) shared with ctx->B.
 idp::StageBuffers snapshot_set(const idp_ctx* ctx, int k) {
   idp::StageBuffers B = ctx->B;
@@ -325,10 +330,12 @@ idp::StageBuffers snapshot_set(const idp_ctx* ctx, int k) {
   take(&B.UL, 5 * n);
   take(&B.bnd, 3 * n);
   take(&B.tU5, 5 * n);
+  take(&B.tab, 6 * n);
   take(&B.d, ns);
   take(&B.dinv, ns);
   take(&B.P, 5 * ns);
   take(&B.tP, 5 * ns);
+  take(&B.tdF, 5 * ns);
   take(&B.tl4, ns);
   take(&B.tl5, ns);
   B.Ulast = nullptr;  // the stored traces leave the last stage's output and bounds alone
@@ -720,7 +727,7 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
     IDP_CUDA(ctx, cudaMemset(X.d, 0, sizeof(float) * ns));
     IDP_CUDA(ctx, cudaMemset(X.dinv, 0, sizeof(float) * ns));
   }
-  B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = nullptr;
+  B.tP = B.tl4 = B.tU5 = B.tl5 = B.tUlim = B.tab = B.tdF = nullptr;
   IDP_CUDA(ctx, cudaMemset(B.scal, 0, sizeof(idp::DeviceScalars)));
   if ((st = alloc_instances(ctx, 1, std::vector<int32_t>())) != IDP_OK) return st;
   ctx->has_mesh = true;

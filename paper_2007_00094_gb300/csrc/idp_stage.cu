@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge(DeviceGraph G, const double*
 // m_j.c_ij of Step 1, summed over all j in I(i) in slot order.
 __device__ __forceinline__ double row_diag(const DeviceGraph& G, const double* U, const double* Q, double* d,
                                            double* dinv, const double* dF, const double* mc, double* alpha,
-                                           int64_t r) {
+                                           double* ab, int64_t r) {
   const int64_t n = G.n, ns = G.n_slots;
   const int64_t base = slot_base(G, r);
   const int len = G.row_len[r];
@@ -216,6 +216,14 @@ __device__ __forceinline__ double row_diag(const DeviceGraph& G, const double* U
   const double D = fabs(a) + fabs(e0 - s_i) * fabs(b0) + fabs(e1) * fabs(b1) + fabs(e2) * fabs(b2) +
                    fabs(e3) * fabs(b3) + fabs(e4) * fabs(b4);
   alpha[r] = positive_k(D) ? fabs(num) / D : 0.0;
+  if (ab) {  // traced for the adjoint
+    ab[r] = a;
+    ab[n + r] = b0;
+    ab[2 * n + r] = b1;
+    ab[3 * n + r] = b2;
+    ab[4 * n + r] = b3;
+    ab[5 * n + r] = b4;
+  }
   return G.mi[r] / (2.0 * sum);
 }
 
@@ -223,9 +231,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, const double*
                                                  const double* __restrict__ Q, double* __restrict__ d,
                                                  double* __restrict__ dinv, const double* __restrict__ dF,
                                                  const double* __restrict__ mc, double* __restrict__ alpha,
-                                                 DeviceScalars* scal) {
+                                                 double* __restrict__ ab, DeviceScalars* scal) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, U, Q, d, dinv, dF, mc, alpha, r) : INFINITY);
+  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, U, Q, d, dinv, dF, mc, alpha, ab, r) : INFINITY);
 }
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
@@ -558,7 +566,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_stage_persistent(PersistentSta
   });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[2], n, [&](int64_t r) {
-    reduce_tau_candidate(G, r, r < n ? row_diag(G, a.Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, r) : INFINITY);
+    reduce_tau_candidate(G, r, r < n ? row_diag(G, a.Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, nullptr, r) : INFINITY);
   });
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[3], n, [&](int64_t r) {
@@ -762,11 +770,16 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
     ++launches;
   };
   run(kKNode, [&] { k_node<<<grid, kBlock, 0, s>>>(G.n, Uin, B.node, B.scal); });
-  // m_j.c_ij of Step 1 lives in l[1] until Step 2 (l[1] is next written by the first limiter pass)
-  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.scal); });
-  run(kKDiag, [&] { k_diag<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, B.scal); });
+  // m_j.c_ij of Step 1 lives in l[1] until Step 2 (l[1] is next written by the first limiter pass);
+  // the flux differences live in P until Step 3, or in the trace when tracing
+  double* dF = trace ? B.tdF : B.P;
+  run(kKEdge, [&] { k_edge<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, dF, B.l[1], B.scal); });
+  run(kKDiag, [&] {
+    k_diag<<<grid, kBlock, 0, s>>>(G, Uin, B.node, B.d, B.dinv, dF, B.l[1], B.alpha, trace ? B.tab : nullptr,
+                                   B.scal);
+  });
   run(kKLowOrder, [&] {
-    k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
+    k_low_order<<<grid, kBlock, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, dF, B.alpha, B.UL, B.R, B.bnd, B.scal,
                                         tau_mode, accumulate_time ? 1 : 0);
   });
   run(kKFluxLimit, [&] {

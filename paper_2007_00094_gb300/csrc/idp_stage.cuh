@@ -89,6 +89,8 @@ struct StageBuffers {
   double* tU5;
   double* tl5;
   double* tUlim;
+  double* tab;  // 6n: a_i and b_i (5) of the indicator, as Step 2 formed them
+  double* tdF;  // 5 n_slots: (f_j - f_i).c_ij of Step 1 (a traced stage keeps them here instead of in P)
 };
 
 struct StageConfig {
