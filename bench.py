@@ -69,6 +69,12 @@ NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 2.147e9, "low_order": 2.199e
 # entry (slot) and per node.
 MIXED_BYTES = {"node": (0, 92), "edge": (35, 52), "low_order": (32, 164),
                "flux_limit": (36, 116), "limiter_pass": (60, 112), "final": (36, 124)}
+# The same with row patterns (structured grids): the column index (4 B),
+# transpose map (4 B), flags (1 B) and table code (2 B) of a slot come from
+# the row's pattern (a 2-byte id per node and a table that stays on chip);
+# Step 3 keeps the column stream.
+MIXED_BYTES_PATTERNS = {"node": (0, 92), "edge": (28, 54), "low_order": (32, 164),
+                        "flux_limit": (30, 118), "limiter_pass": (52, 114), "final": (28, 126)}
 
 
 def _hbm_peak():
@@ -204,9 +210,10 @@ def pattern_mixed(stream, args):
                  "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}
         if prec == 1:
             entry["entry_table_values"] = s.entry_table_size()
+            entry["row_patterns"] = s.row_pattern_count()
             dom = max(prof, key=lambda k: prof[k][0])
             dom_ms, dom_n = prof[dom]
-            per_slot, per_node = MIXED_BYTES[dom]
+            per_slot, per_node = (MIXED_BYTES_PATTERNS if entry["row_patterns"] else MIXED_BYTES)[dom]
             bytes_per_launch = per_slot * s.nnz + per_node * mesh.n_nodes
             peak, src = _hbm_peak()
             achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
@@ -437,7 +444,7 @@ def pattern_q1_2d(stream, args):
                     "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, 3D step channel) x "
                             f"{s.nnz} nnz per launch"}
         else:
-            per_slot, per_node = MIXED_BYTES[dom]
+            per_slot, per_node = (MIXED_BYTES_PATTERNS if s.row_pattern_count() else MIXED_BYTES)[dom]
             achieved = (per_slot * s.nnz + per_node * mesh.n_nodes) / per_launch_s / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                     "frac": achieved / peak_hbm, "traffic": None, "peak_source": src,

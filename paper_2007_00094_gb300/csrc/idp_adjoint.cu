@@ -417,13 +417,20 @@ __global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, const double* __res
   const double a_i = alpha[r];
   const double inv_mi = G.inv_mi[r];
   const double scale = tau * inv_mi * (double)(len - 1);
-  double galpha_i = 0.0, gtau = 0.0;
+  double galpha_i = 0.0, tp_sum = 0.0;
+  // the first writer of the entry adjoints gU_tr, gd and ga_tr and of gU_own
+  // in the reversed stage: assigns them (zero on the diagonal)
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
     if (j == r) {
 #pragma unroll
-      for (int f = 0; f < kFields; ++f) A.gR_tr[f * ns + p] = 0.0;
+      for (int f = 0; f < kFields; ++f) {
+        A.gR_tr[f * ns + p] = 0.0;
+        A.gU_tr[f * ns + p] = 0.0;
+      }
+      A.gd[p] = 0.0;
+      A.ga_tr[p] = 0.0;
       continue;
     }
     double pij[kFields], gP[kFields];
@@ -446,22 +453,22 @@ __global__ void __launch_bounds__(kB) ka_flux(DeviceGraph G, const double* __res
       gRi[f] -= scale * b_ji * gP[f];
       A.gR_tr[f * ns + p] = scale * b_ij * gP[f];
       gdd += scale * (uj[f] - ui[f]) * gP[f];
-      A.gU_tr[f * ns + p] += scale * dd * gP[f];
+      A.gU_tr[f * ns + p] = scale * dd * gP[f];
       gUi[f] -= scale * dd * gP[f];
       tp += pij[f] * gP[f];
     }
-    A.gd[p] += (Aij - 1.0) * gdd;
+    A.gd[p] = (Aij - 1.0) * gdd;
     galpha_i += 0.5 * dij * gdd;
-    A.ga_tr[p] += 0.5 * dij * gdd;
-    if (tau > 0.0) gtau += tp / tau;  // P_ij is linear in tau
+    A.ga_tr[p] = 0.5 * dij * gdd;
+    tp_sum += tp;
   }
 #pragma unroll
   for (int f = 0; f < kFields; ++f) {
     A.gR_own[f * n + r] = gRi[f];
-    A.gU_own[f * n + r] += gUi[f];
+    A.gU_own[f * n + r] = gUi[f];
   }
   A.ga_own[r] = galpha_i;
-  A.gtau_part[r] = gtau;
+  A.gtau_part[r] = tau > 0.0 ? tp_sum / tau : 0.0;  // P_ij is linear in tau
 }
 
 // Step 3 reverse: U^L_i = U_i + sum_j (2 tau/m_i) d_ij Ubar_ij, the bounds
@@ -481,7 +488,7 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
   load5(U, n, r, ui);
   load5(A.gUL, n, r, gUL);
   load5(A.gR_own, n, r, gR);
-  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
+  const double inv_rho_i = Q[kQInvRho * n + r], h_i = Q[kQH * n + r];
   // gather R's adjoint; locate the first entries attaining the bounds (the
   // doubled bar-state densities formed as Step 3 forms them, from its flux
   // differences)
@@ -523,7 +530,7 @@ __global__ void __launch_bounds__(kB) ka_low(DeviceGraph G, const double* __rest
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
     const double dij = d[p];
-    if (k == kphi) A.gphi_tr[p] += g_pmin;
+    A.gphi_tr[p] = k == kphi ? g_pmin : 0.0;  // the only writer
     if (j == r) {
       // Ubar_ii = U_i
       if (dij != 0.0) {
@@ -706,7 +713,7 @@ __global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __res
     galpha += A.ga_tr[pt];
     gphi += A.gphi_tr[pt];
   }
-  const double inv_rho_i = Q[kQInvRho * n + r], p_i = Q[kQP * n + r], h_i = Q[kQH * n + r];
+  const double inv_rho_i = Q[kQInvRho * n + r], h_i = Q[kQH * n + r];
   const double s_i = Q[kQS * n + r];
   // a_i and b_i of the indicator as the forward sweep formed them
   const double a = ab[r];
@@ -872,7 +879,6 @@ int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const Adjo
                          const double* Uin, const double* gE, double* gIn, bool tau_computed, cudaStream_t s,
                          Profiler* prof) {
   const unsigned grid = (unsigned)((G.n + kB - 1) / kB);
-  const size_t n = (size_t)G.n, ns = (size_t)G.n_slots;
   const bool timed = prof && prof->enabled;
   int launches = 0;
   auto run = [&](int id, auto&& launch) {
@@ -880,11 +886,8 @@ int launch_adjoint_stage(const DeviceGraph& G, const StageBuffers& B, const Adjo
     launch();
     if (timed) prof->end(s);
   };
-  cudaMemsetAsync(A.gU_own, 0, sizeof(double) * kFields * n, s);
-  cudaMemsetAsync(A.gU_tr, 0, sizeof(double) * kFields * ns, s);
-  cudaMemsetAsync(A.gd, 0, sizeof(double) * ns, s);
-  cudaMemsetAsync(A.ga_tr, 0, sizeof(double) * ns, s);
-  cudaMemsetAsync(A.gphi_tr, 0, sizeof(double) * ns, s);
+  // gU_own, gU_tr, gd and ga_tr are first written (assigned) by ka_flux,
+  // gphi_tr only by ka_low
   // traced intermediates: P and l of Step 4 (tP, tl4), the state and l
   // after the first pass (tU5, tl5), P' of the first pass (left in B.P)
   run(kKAdjFinal, [&] { ka_final<<<grid, kB, 0, s>>>(G, gE, B.P, B.tl5, A); });

@@ -8,6 +8,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "idp.h"
@@ -30,6 +31,7 @@ struct idp_ctx {
   idp::StageConfig C{};
   idp::MixedGraph MG{};
   int64_t n_entry_values = 0;  // size of the mixed stage's entry table (0: per-entry arrays)
+  int64_t n_row_patterns = 0;  // row patterns of the mixed stage (0: per-slot column and transpose arrays)
   // row order (idp_config.renumber): library row of each caller node and back,
   // on the device, and a 5n buffer for reordering states at the interface
   bool renumbered = false;
@@ -568,10 +570,10 @@ namespace {
 // tuples (c_x, c_y, c_z, m_ij, |c_ij|, 1/|c_ij|) of all slots, padding
 // included, compared bitwise.  Left off when there are more than
 // kEntryTableMax of them.
-idp_status upload_entry_table(idp_ctx* ctx, const idp::HostEntriesF& E) {
+idp_status upload_entry_table(idp_ctx* ctx, const idp::HostEntriesF& E, std::vector<uint16_t>& code) {
   const size_t ns = E.cx.size();
   std::map<std::array<uint32_t, 6>, uint16_t> index;
-  std::vector<uint16_t> code(ns);
+  code.assign(ns, 0);
   std::vector<float4> tab;
   auto bits = [](float f) {
     uint32_t u;
@@ -583,7 +585,10 @@ idp_status upload_entry_table(idp_ctx* ctx, const idp::HostEntriesF& E) {
                                          bits(E.m[p]),  bits(E.cn[p]), bits(E.inv_cn[p])};
     auto it = index.find(key);
     if (it == index.end()) {
-      if ((int)index.size() == idp::kEntryTableMax) return IDP_OK;  // not a table mesh: per-entry arrays
+      if ((int)index.size() == idp::kEntryTableMax) {  // not a table mesh: per-entry arrays
+        code.clear();
+        return IDP_OK;
+      }
       it = index.emplace(key, (uint16_t)index.size()).first;
       tab.push_back(make_float4(E.cx[p], E.cy[p], E.cz[p], E.m[p]));
       tab.push_back(make_float4(E.cn[p], E.inv_cn[p], 0.0f, 0.0f));
@@ -597,6 +602,63 @@ idp_status upload_entry_table(idp_ctx* ctx, const idp::HostEntriesF& E) {
   ctx->MG.ecode = dcode;
   ctx->MG.etab = dtab;
   ctx->n_entry_values = (int64_t)index.size();
+  return IDP_OK;
+}
+
+// Row patterns of the mixed stage (with idp_config.entry_table): each row's
+// entries as (column offset j - r, index k' of the transposed entry in row
+// j, flags, entry-table code); rows with equal sequences share a pattern.
+// Left off (per-slot arrays) when there are more than kRowPatternMax
+// patterns or an offset or index does not fit its field.  The records are
+// derived from the SELL arrays themselves, so the kernels read the same
+// columns, slots, flags and codes either way.
+idp_status upload_row_patterns(idp_ctx* ctx, const std::vector<uint16_t>& code) {
+  const idp::SellLayout& L = ctx->L;
+  const int64_t n = L.n;
+  int width = 0;
+  for (int64_t r = 0; r < n; ++r) width = L.row_len[r] > width ? L.row_len[r] : width;
+  if (n == 0 || width == 0 || width > 255) return IDP_OK;
+  struct Hash {
+    size_t operator()(const std::vector<uint64_t>& v) const {
+      uint64_t h = 1469598103934665603ull;  // FNV-1a over the words
+      for (uint64_t w : v) h = (h ^ w) * 1099511628211ull;
+      return (size_t)h;
+    }
+  };
+  std::unordered_map<std::vector<uint64_t>, uint16_t, Hash> index;
+  std::vector<uint16_t> rpat((size_t)n);
+  std::vector<uint2> tab;
+  std::vector<uint64_t> sig;
+  for (int64_t r = 0; r < n; ++r) {
+    const int len = L.row_len[r];
+    const int64_t base = (int64_t)L.slice_ptr[r >> 5] + (r & 31);
+    sig.assign((size_t)len, 0);
+    for (int k = 0; k < len; ++k) {
+      const int64_t p = base + 32 * (int64_t)k;
+      const int64_t j = L.col[p];
+      const int64_t rel = L.tpos[p] - ((int64_t)L.slice_ptr[j >> 5] + (j & 31));
+      const int64_t dj = j - r;
+      if (rel < 0 || rel % 32 != 0 || rel / 32 >= L.row_len[j] || dj < -2147483647LL || dj > 2147483647LL) return IDP_OK;
+      const uint32_t y = (uint32_t)(rel / 32) | ((uint32_t)L.flags[p] << 8) | ((uint32_t)(code.empty() ? 0 : code[p]) << 16);
+      sig[k] = (uint64_t)(uint32_t)(int32_t)dj | ((uint64_t)y << 32);
+    }
+    auto it = index.find(sig);
+    if (it == index.end()) {
+      if ((int)index.size() == idp::kRowPatternMax) return IDP_OK;
+      it = index.emplace(sig, (uint16_t)index.size()).first;
+      for (int k = 0; k < width; ++k)
+        tab.push_back(k < len ? make_uint2((uint32_t)sig[k], (uint32_t)(sig[k] >> 32)) : make_uint2(0u, 0u));
+    }
+    rpat[(size_t)r] = it->second;
+  }
+  uint16_t* drp;
+  uint2* dtab;
+  idp_status st;
+  if ((st = upload(ctx, &drp, rpat)) || (st = upload(ctx, &dtab, tab))) return st;
+  ctx->MG.rpat = drp;
+  ctx->MG.ptab = dtab;
+  ctx->MG.pwidth = width;
+  ctx->n_row_patterns = (int64_t)index.size();
   return IDP_OK;
 }
 
@@ -704,9 +766,14 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
                               to_float(L.inv_cn)};
     float* fimi;
     if ((st = upload(ctx, &fimi, to_float(L.inv_mi))) != IDP_OK) return st;
-    ctx->MG = idp::MixedGraph{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fimi, nullptr, nullptr};
+    ctx->MG = idp::MixedGraph{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, fimi,
+                              nullptr, nullptr, nullptr, nullptr, 0};
     ctx->n_entry_values = 0;
-    if (ctx->cfg.entry_table && (st = upload_entry_table(ctx, E))) return st;
+    ctx->n_row_patterns = 0;
+    if (ctx->cfg.entry_table) {
+      std::vector<uint16_t> code;
+      if ((st = upload_entry_table(ctx, E, code)) || (st = upload_row_patterns(ctx, code))) return st;
+    }
     if (!ctx->MG.ecode) {
       float *fcx, *fcy, *fcz, *fm, *fcn, *finv;
       if ((st = upload(ctx, &fcx, E.cx)) || (st = upload(ctx, &fcy, E.cy)) || (st = upload(ctx, &fcz, E.cz)) ||
@@ -745,6 +812,12 @@ idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz) {
 idp_status idp_entry_table_size(idp_ctx* ctx, int64_t* n_values) {
   if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
   if (n_values) *n_values = ctx->n_entry_values;
+  return IDP_OK;
+}
+
+idp_status idp_row_pattern_count(idp_ctx* ctx, int64_t* n_patterns) {
+  if (!ctx || !ctx->has_mesh) return fail(ctx, IDP_ERR_STATE, "no mesh");
+  if (n_patterns) *n_patterns = ctx->n_row_patterns;
   return IDP_OK;
 }
 

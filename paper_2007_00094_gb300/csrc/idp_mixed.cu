@@ -69,6 +69,39 @@ __device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
   return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
 }
 
+// Entry k (slot p) of row r: column j, slot pt of the transposed entry,
+// flags and entry-table code, from the row's pattern record when the mesh
+// has row patterns (pat = its records), else from the per-slot arrays.
+// Fields a caller does not use cost nothing (their loads are dropped).
+struct SlotRef {
+  int64_t j;
+  int64_t pt;
+  unsigned int fl;
+  int code;
+};
+
+__device__ __forceinline__ const uint2* row_pattern(const MixedGraph& M, int64_t r) {
+  return M.rpat ? M.ptab + (int64_t)M.rpat[r] * M.pwidth : nullptr;
+}
+
+__device__ __forceinline__ SlotRef slot_ref(const DeviceGraph& G, const MixedGraph& M, const uint2* pat, int64_t r,
+                                            int k, int64_t p) {
+  SlotRef e;
+  if (pat) {
+    const uint2 w = __ldg(&pat[k]);
+    e.j = r + (int32_t)w.x;
+    e.pt = slot_base(G, e.j) + 32 * (int64_t)(w.y & 0xffu);
+    e.fl = (w.y >> 8) & 0xffu;
+    e.code = (int)(w.y >> 16);
+  } else {
+    e.j = G.col[p];
+    e.pt = G.tpos[p];
+    e.fl = G.flags[p];
+    e.code = M.ecode ? (int)M.ecode[p] : 0;
+  }
+  return e;
+}
+
 template <typename T>
 __device__ __forceinline__ void load5(const T* U, int64_t n, int64_t i, T* u) {
 #pragma unroll
@@ -389,11 +422,13 @@ __device__ __forceinline__ double row_edge_m(const DeviceGraph& G, const MixedGr
   const float Ei = U[4 * n + r];
   const float s_i = Q[kQS * n + r], h_i = Q[kQH * n + r];
   float a = 0.0f, b0 = 0.0f, b1 = 0.0f, b2 = 0.0f, b3 = 0.0f, b4 = 0.0f, dsum = 0.0f;
+  const uint2* pat = row_pattern(M, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
-    const uint8_t fl = G.flags[p];
-    const EntryF e = entry_f(M, p);
+    const SlotRef sr = slot_ref(G, M, pat, r, k, p);
+    const int64_t j = sr.j;
+    const unsigned int fl = sr.fl;
+    const EntryF e = entry_f_code(M, p, sr.code);
     const float cx = e.cx, cy = e.cy, cz = e.cz;
     const SideF sj = load_side_f(U, Q, n, j);
     const float s_j = Q[kQS * n + j], h_j = Q[kQH * n + j];
@@ -427,7 +462,7 @@ __device__ __forceinline__ double row_edge_m(const DeviceGraph& G, const MixedGr
         ef.cz = -e.cz;
       }
     } else {
-      const EntryF tr = entry_f(M, G.tpos[p]);
+      const EntryF tr = entry_f(M, sr.pt);
       if (upper) et = tr; else ef = tr;
     }
     float dij = 0.0f;
@@ -494,6 +529,8 @@ __device__ __forceinline__ void row_low_order_m(const DeviceGraph& G, const Stag
     }
   }
   float dmin = 0.0f, dmax = 0.0f, phi_min = INFINITY;
+  // the column stream, not the row pattern: measured faster here (this
+  // kernel's seven neighbour gathers lean on L1 more than the others')
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
     const int64_t j = G.col[p];
@@ -572,9 +609,11 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
   const float a_i = alpha[r];
   const float inv_mi = (float)G.inv_mi[r];
   const float scale = (float)(tau * G.inv_mi[r] * (double)(len - 1));
+  const uint2* pat = row_pattern(M, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
+    const SlotRef sr = slot_ref(G, M, pat, r, k, p);
+    const int64_t j = sr.j;
     if (j == r) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f) st_stream(&P[f * ns + p], 0.0f);
@@ -582,7 +621,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
       continue;
     }
     float pij[kFields];
-    const float m = entry_f(M, p).m;
+    const float m = entry_f_code(M, p, sr.code).m;
     const float b_ij = -m * M.inv_mi[j];
     const float b_ji = -m * inv_mi;
     const float dij = d[p];
@@ -596,7 +635,7 @@ __device__ __forceinline__ void row_flux_limit_m(const DeviceGraph& G, const Mix
   }
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
+__global__ void __launch_bounds__(kMaxBlock, 4) k_flux_limit_m(DeviceGraph G, MixedGraph M, StageConfig C,
                                                          const float* __restrict__ Uf, const float* __restrict__ d,
                                                          const float* __restrict__ alpha, const double* __restrict__ UL,
                                                          const float* __restrict__ R, const double* __restrict__ bnd,
@@ -608,7 +647,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit_m(DeviceGraph G, Mixed
 
 // Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
 // FP32, added to FP64), P_ij <- (1 - min) P_ij and new l_ij.
-__device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const StageConfig& C,
+__device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const MixedGraph& M, const StageConfig& C,
                                                    const double* Ucur, double* Unext,
                                                    float* P, const float* lold,
                                                    float* lnew, const double* bnd,
@@ -619,10 +658,12 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
   const float lam = (float)G.lam[r];
   float inc[kFields] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   const unsigned long long keep = l2_policy_last(), drop = l2_policy_first();
+  const uint2* pat = row_pattern(M, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    const float w = lam * fminf(lold[p], lold[G.tpos[p]]);
+    const SlotRef sr = slot_ref(G, M, pat, r, k, p);
+    if (sr.j == r) continue;
+    const float w = lam * fminf(lold[p], lold[sr.pt]);
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
       inc[f] = fmaf(w, ld_policy(&P[f * ns + p], keep), inc[f]);
@@ -642,8 +683,9 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
   float lk_n = 0.0f, p_n[kFields];
   auto fetch = [&](int k) {
     const int64_t q = base + 32 * (int64_t)k;
-    diag_n = G.col[q] == r;
-    lk_n = fminf(lold[q], lold[G.tpos[q]]);
+    const SlotRef sr = slot_ref(G, M, pat, r, k, q);
+    diag_n = sr.j == r;
+    lk_n = fminf(lold[q], lold[sr.pt]);
 #pragma unroll
     for (int f = 0; f < kFields; ++f) p_n[f] = ld_policy(&P[f * ns + q], drop);
   };
@@ -672,16 +714,17 @@ __device__ __forceinline__ void row_limiter_pass_m(const DeviceGraph& G, const S
   }
 }
 
-__global__ void __launch_bounds__(kMaxBlock, 4) k_limiter_pass_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock, 4) k_limiter_pass_m(DeviceGraph G, MixedGraph M, StageConfig C,
+                                                           const double* __restrict__ Ucur,
                                                            double* __restrict__ Unext, float* __restrict__ P,
                                                            const float* __restrict__ lold, float* __restrict__ lnew,
                                                            const double* __restrict__ bnd) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_limiter_pass_m(G, C, Ucur, Unext, P, lold, lnew, bnd, r);
+  if (r < G.n) row_limiter_pass_m(G, M, C, Ucur, Unext, P, lold, lnew, bnd, r);
 }
 
 // Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
-__device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageConfig& C,
+__device__ __forceinline__ void row_final_m(const DeviceGraph& G, const MixedGraph& M, const StageConfig& C,
                                             const double* Ucur, const float* P,
                                             const float* l, const double* Un,
                                             double* Uout, double* Ulim, DeviceScalars* scal,
@@ -691,10 +734,12 @@ __device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageCon
   const int len = G.row_len[r];
   const float lam = (float)G.lam[r];
   float inc[kFields] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  const uint2* pat = row_pattern(M, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    const float w = lam * fminf(l[p], l[G.tpos[p]]);
+    const SlotRef sr = slot_ref(G, M, pat, r, k, p);
+    if (sr.j == r) continue;
+    const float w = lam * fminf(l[p], l[sr.pt]);
 #pragma unroll
     for (int f = 0; f < kFields; ++f) inc[f] = fmaf(w, P[f * ns + p], inc[f]);
   }
@@ -730,13 +775,14 @@ __device__ __forceinline__ void row_final_m(const DeviceGraph& G, const StageCon
   for (int f = 0; f < kFields; ++f) Uout[f * n + r] = out[f];
 }
 
-__global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, StageConfig C, const double* __restrict__ Ucur,
+__global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, MixedGraph M, StageConfig C,
+                                                    const double* __restrict__ Ucur,
                                                     const float* __restrict__ P, const float* __restrict__ l,
                                                     const double* __restrict__ Un, double* __restrict__ Uout,
                                                     double* __restrict__ Ulim, DeviceScalars* scal, int blend,
                                                     int skip_write_on_error) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_final_m(G, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
+  if (r < G.n) row_final_m(G, M, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
 }
 
 struct PersistentStageMixed {
@@ -783,7 +829,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStag
     double* next = B.Uw[wbuf];
     const int ph = 4 + pass < 11 ? 4 + pass : 11;
     for_each_row_tile(&tile[ph], n, [&](int64_t r) {
-      if (r < n) row_limiter_pass_m(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd, r);
+      if (r < n) row_limiter_pass_m(G, M, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd, r);
     });
     cur = next;
     wbuf ^= 1;
@@ -791,7 +837,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_stage_persistent_m(PersistentStag
   }
   if (!grid_barrier(a.bar, C.spin_limit, B.scal)) return;
   for_each_row_tile(&tile[11], n, [&](int64_t r) {
-    if (r < n) row_final_m(G, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, B.Ulast, B.scal, a.blend, a.skip_write_on_error, r);
+    if (r < n) row_final_m(G, M, C, cur, X.P, X.l[lbuf], a.Un, a.Uout, B.Ulast, B.scal, a.blend, a.skip_write_on_error, r);
   });
 }
 
@@ -839,7 +885,7 @@ int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const Sta
   for (int pass = 1; pass < C.limiter_passes; ++pass) {
     double* next = B.Uw[wbuf];
     run(kKLimiterPass,
-        [&] { k_limiter_pass_m<<<grid, kBlock, 0, s>>>(G, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd); });
+        [&] { k_limiter_pass_m<<<grid, kBlock, 0, s>>>(G, M, C, cur, next, X.P, X.l[lbuf], X.l[lbuf ^ 1], B.bnd); });
     if (trace && pass == 1) cudaMemcpyAsync(B.tU5, next, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
     cur = next;
     wbuf ^= 1;
@@ -847,7 +893,7 @@ int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const Sta
   }
   double* ulim = B.Ulast ? B.Ulast : (trace ? B.tUlim : nullptr);
   run(kKFinal, [&] {
-    k_final_m<<<grid, kBlock, 0, s>>>(G, C, cur, X.P, X.l[lbuf], Un, Uout, ulim, B.scal, blend,
+    k_final_m<<<grid, kBlock, 0, s>>>(G, M, C, cur, X.P, X.l[lbuf], Un, Uout, ulim, B.scal, blend,
                                       skip_write_on_error ? 1 : 0);
   });
   if (trace && B.Ulast)

@@ -20,9 +20,21 @@ struct MixedGraph {
   // (|c|, 1/|c|, 0, 0) = etab[2 ecode[p] + 1].
   const uint16_t* ecode;
   const float4* etab;
+  // Row patterns (nullptr: per-slot arrays).  On a structured grid most rows
+  // differ from others only by a shift of their column indices: rows whose
+  // entries k have the same column offset j - r, the same index k' of the
+  // transposed entry in row j, the same flags and the same entry-table code
+  // share a pattern, rpat[r] is row r's, and ptab[rpat[r] * pwidth + k]
+  // holds entry k as (j - r, k' | flags << 8 | code << 16).  The kernels
+  // (all but Step 3's) then read one record per entry from a table that
+  // stays in L1 instead of the column, transpose, flag and code streams.
+  const uint16_t* rpat;
+  const uint2* ptab;
+  int pwidth;
 };
 
 constexpr int kEntryTableMax = 4096;
+constexpr int kRowPatternMax = 4096;
 
 // Host-side FP32 copies of the per-slot entries (SELL order).
 struct HostEntriesF {
@@ -35,10 +47,9 @@ struct EntryF {
   float cx, cy, cz, m, cn, inv_cn;
 };
 
-__device__ __forceinline__ EntryF entry_f(const MixedGraph& M, int64_t p) {
+__device__ __forceinline__ EntryF entry_f_code(const MixedGraph& M, int64_t p, int c) {
   EntryF e;
   if (M.ecode) {
-    const int c = M.ecode[p];
     const float4 a = __ldg(&M.etab[2 * c]), b = __ldg(&M.etab[2 * c + 1]);
     e.cx = a.x;
     e.cy = a.y;
@@ -55,6 +66,10 @@ __device__ __forceinline__ EntryF entry_f(const MixedGraph& M, int64_t p) {
     e.inv_cn = M.inv_cn[p];
   }
   return e;
+}
+
+__device__ __forceinline__ EntryF entry_f(const MixedGraph& M, int64_t p) {
+  return entry_f_code(M, p, M.ecode ? (int)M.ecode[p] : 0);
 }
 
 struct MixedBuffers {

@@ -34,7 +34,8 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_check_bounds", "idp_launch_count", "idp_profile", "idp_profile_read", "idp_tau_max_noalloc", "idp_set_instances",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
             "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad",
-            "idp_entry_table_size", "idp_upload_sparsity", "idp_check_local_bounds", "idp_probe_fp64_peak"]
+            "idp_entry_table_size", "idp_upload_sparsity", "idp_check_local_bounds", "idp_probe_fp64_peak",
+            "idp_row_pattern_count"]
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.idp_upload_sparsity.argtypes = [_vp, C.c_int64, _i64p, _i64p, _dp, _dp, _dp, _i32p, _dp]
     L.idp_mesh_info.argtypes = [_vp, _i64p, _i64p]
     L.idp_entry_table_size.argtypes = [_vp, _i64p]
+    L.idp_row_pattern_count.argtypes = [_vp, _i64p]
     L.idp_get_matrices.argtypes = [_vp, _i64p, _i64p, _dp, _dp, _dp]
     L.idp_init_state.argtypes = [_vp, _vp, C.c_int]
     L.idp_get_state.argtypes = [_vp, _vp, C.c_int]
@@ -282,6 +284,12 @@ class Solver:
         """Distinct FP32 entries in the mixed stage's entry table (0: per-entry arrays)."""
         v = C.c_int64(0)
         _check(self._ctx, load().idp_entry_table_size(self._ctx, C.byref(v)))
+        return int(v.value)
+
+    def row_pattern_count(self) -> int:
+        """Row patterns of the mixed stage (0: per-entry column and transpose arrays)."""
+        v = C.c_int64(0)
+        _check(self._ctx, load().idp_row_pattern_count(self._ctx, C.byref(v)))
         return int(v.value)
 
     def matrices(self):

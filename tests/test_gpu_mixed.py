@@ -143,8 +143,10 @@ def test_mixed_keeps_the_discretization_error_on_sod():
 @pytest.mark.parametrize("case", ["slip_cube", "periodic_vortex", "rect2d", "jittered"])
 def test_entry_table_gives_bitwise_the_per_entry_result(case):
     """The FP32 entries stored as 16-bit indices into a table of the distinct
-    values (uniform grids) give bitwise the result of per-entry arrays; a
-    jittered mesh has too many distinct entries and keeps the arrays."""
+    values (uniform grids) and the column / transposed-entry positions read
+    from row patterns give bitwise the result of per-entry arrays; a jittered
+    mesh has too many distinct entries and keeps the value arrays, but its
+    connectivity is that of the grid and uses row patterns."""
     from paper_2007_00094_gb300 import workloads as W
     if case == "slip_cube":
         mesh = W.sod_cube_mesh(20)
@@ -159,10 +161,11 @@ def test_entry_table_gives_bitwise_the_per_entry_result(case):
     else:
         mesh = W.box_mesh((20, 18, 16), periodic=(False, False, False), jitter=0.2, seed=4)
         U = W.sod_state(mesh)
-    out, sizes = [], []
+    out, sizes, patterns = [], [], []
     for table in (1, 0):
         s = _solver(mesh, precision=1, entry_table=table)
         sizes.append(s.entry_table_size())
+        patterns.append(s.row_pattern_count())
         s.init_state(U)
         s.step(4)
         s.synchronize()
@@ -171,4 +174,6 @@ def test_entry_table_gives_bitwise_the_per_entry_result(case):
         assert sizes == [0, 0]
     else:
         assert 0 < sizes[0] <= 729 and sizes[1] == 0
+    # per axis: the two boundary layers of each side and the interior (5^3 in 3D, 5^2 in 2D)
+    assert 0 < patterns[0] <= (25 if case == "rect2d" else 125) and patterns[1] == 0
     np.testing.assert_array_equal(out[0], out[1])

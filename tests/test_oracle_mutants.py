@@ -32,10 +32,16 @@ MUTANTS = {
     "psi_margin_sign": ("const int ok = psi >= -margin * scale;", "const int ok = psi >= margin * scale;"),
 }
 
-PINS = ["tests/test_oracle_symmetry.py", "tests/test_oracle_matrices.py", "tests/test_oracle_2d.py",
+# fast pins first (a mutant run stops at its first failing pin); the
+# convergence pin last
+PINS = ["tests/test_oracle_margin.py", "tests/test_oracle_stage.py::test_ssprk3_temporal_order",
+        "tests/test_oracle_symmetry.py", "tests/test_oracle_matrices.py",
+        "tests/test_oracle_2d.py::test_uniform_periodic_closed_forms_2d",
+        "tests/test_oracle_2d.py::test_identities_any_quad_mesh",
+        "tests/test_oracle_2d.py::test_quad_assembly_is_the_extruded_hex_assembly",
+        "tests/test_oracle_2d.py::test_2d_stage_keeps_mz_zero_conserves_and_preserves_free_stream",
         "tests/test_oracle_stage.py::test_conservation_periodic", "tests/test_oracle_stage.py::test_trace_identities",
-        "tests/test_oracle_stage.py::test_sod_converges_to_exact", "tests/test_oracle_stage.py::test_ssprk3_temporal_order",
-        "tests/test_oracle_margin.py"]
+        "tests/test_oracle_stage.py::test_sod_converges_to_exact"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
