@@ -493,6 +493,62 @@ def pattern_renumber(stream, args):
     return out
 
 
+def pattern_sharded(stream, args):
+    """The sharded stage on one GPU (idp_shards_*, Sec. 4.1, Fig. 1-2): the
+    step channel's rows in 2 and 4 contiguous ranges with one ghost layer,
+    halo exchanges (gather kernel, device copy, scatter kernel) between the
+    stage's phases.  FP64 ms per SSP-RK3 step against the unsharded stage on
+    the same matrices, the values exchanged per step, and whether the states
+    after the timed steps are bitwise equal."""
+    import numpy as np
+    import torch
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import ShardedSolver, Solver
+
+    mesh = W.forward_step_mesh(m=args.m, jitter=0.2, seed=2007)
+    U0 = W.forward_step_state(mesh)
+    s = Solver(mesh, stream=stream)
+    rowptr, col, mij, cij, mi = s.matrices()
+    s.close()
+    sp = dict(rowptr=rowptr, col=col, mij=mij, cij=cij, mi=mi, bc=mesh.bc, inflow=mesh.inflow)
+    steps, warm = args.pattern_steps, args.warmup
+
+    def timed(solver):
+        solver.init_state(U0)
+        solver.step(warm)
+        solver.synchronize()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(steps)
+        e1.record(stream)
+        solver.synchronize()
+        return e0.elapsed_time(e1) / steps, solver.get_state()
+
+    ref = Solver(sparsity=sp, stream=stream)
+    ms_ref, U_ref = timed(ref)
+    ref.close()
+    out = {"config": {"workload": f"mach3_forward_facing_step_h1/{args.m}_jitter0.2_seed2007", "nodes": mesh.n_nodes,
+                      "nnz": len(col), "steps_timed": steps, "warmup": warm, "precision": "fp64"},
+           "unsharded_ms_per_step": ms_ref}
+    for k in (2, 4):
+        sh = ShardedSolver(sp, n_shards=k, stream=stream)
+        ms, U = timed(sh)
+        nn, ne, launches = sh.halo_size()
+        ghosts = sum(sh.plan.info(q)[0] - (sh.plan.info(q)[2] - sh.plan.info(q)[1]) for q in range(k))
+        sh.close()
+        # per stage: alpha (1 field), R (5), U (5) at ghost nodes; l twice at halo entries
+        values = 3 * (11 * nn + 2 * ne)
+        out[f"shards_{k}"] = {"ms_per_step": ms, "over_unsharded": ms / ms_ref,
+                              "value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": "node-stage updates/s",
+                              "ghost_nodes": int(ghosts), "halo_node_values_per_field": nn,
+                              "halo_entry_values": ne, "exchanged_bytes_per_step": 8 * values,
+                              "launches_per_step": launches / steps,
+                              "bitwise_equal_to_unsharded": bool(np.array_equal(U, U_ref))}
+    return out
+
+
 def job_rate(local_ms, units_per_rank, dist=None, device="cpu"):
     """Whole-job rate of a weak-scaling run: the slowest rank's time (max over
     ranks) and all ranks' units divided by it.  Returns (ms_max, units/s)."""
@@ -690,7 +746,7 @@ def main():
     ap.add_argument("--adj-fd-trace-steps", type=int, default=10)
     ap.add_argument("--m2d", type=int, default=1000, help="cells per unit length of the 2D channel mesh")
     ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "adjoint_fd", "relaxation", "q1_2d",
-                                       "renumber"],
+                                       "renumber", "sharded"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -715,7 +771,8 @@ def main():
         build.build()
         run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
                "adjoint_fd": pattern_adjoint_fd,
-               "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d, "renumber": pattern_renumber}[args.only]
+               "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d, "renumber": pattern_renumber,
+               "sharded": pattern_sharded}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return
     dist = None
@@ -817,7 +874,7 @@ def main():
             line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
                                 "adjoint": pattern_adjoint(stream, args),
                                 "relaxation": pattern_relaxation(stream, args), "q1_2d": pattern_q1_2d(stream, args),
-                                "renumber": pattern_renumber(stream, args)}
+                                "renumber": pattern_renumber(stream, args), "sharded": pattern_sharded(stream, args)}
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(mesh, U0, args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -369,6 +369,87 @@ idp_status idp_adjoint_euler_step(idp_ctx* ctx, const double* U, double tau, con
 idp_status idp_adjoint_record(idp_ctx* ctx, int n_steps, int checkpoint_every);
 idp_status idp_adjoint_backward(idp_ctx* ctx, const double* gU_final, double* gU_initial, int on_device);
 
+/* Domain decomposition (Sec. 4.1, Fig. 1): the rows split into contiguous
+ * ranges, each shard owning one range and holding one ghost layer (the
+ * neighbours of its rows that other shards own), and the values shards
+ * exchange at the stage's synchronisation points (Fig. 2).
+ *
+ * idp_shard_plan_create builds the plan of a CSR pattern (the conventions of
+ * idp_upload_sparsity: host rowptr n_nodes+1, col nnz, columns increasing in
+ * each row, structurally symmetric) for n_shards ranges row_begin (host,
+ * n_shards+1 values, 0 first, n_nodes last, strictly increasing; NULL: equal
+ * ranges).  IDP_ERR_ARG for a bad pattern or partition.  The plan is host
+ * memory only (no GPU needed); release it with idp_shard_plan_destroy.
+ * Queries, all host arrays sized by idp_shard_plan_info:
+ *  - info: local node count (own rows and ghosts), the local ids of the own
+ *    rows [own_begin, own_end), local entry count; any pointer may be NULL;
+ *  - nodes: the global id of every local node, increasing (local ids keep
+ *    the global order, so each row keeps its column order);
+ *  - csr: the local CSR (rowptr, local col) of the entries between local nodes
+ *    (all entries of an own row, those inside the shard of a ghost row) and
+ *    the global CSR entry of each (any pointer may be NULL);
+ *  - list: the exchange list of kind IDP_SEND_NODES (own rows that are ghosts
+ *    of peer), IDP_RECV_NODES (ghosts owned by peer), IDP_SEND_ENTRIES
+ *    (entries (g, i) of own rows g with i owned by peer), IDP_RECV_ENTRIES
+ *    (entries (g, i) of ghost rows g owned by peer with i an own row), as
+ *    local node or local entry ids in the order of global ids: a shard's send
+ *    list for a peer and the peer's receive list for it enumerate the same
+ *    values.  *count receives the length; ids (may be NULL) the list. */
+typedef struct idp_shard_plan idp_shard_plan;
+enum { IDP_SEND_NODES = 0, IDP_RECV_NODES = 1, IDP_SEND_ENTRIES = 2, IDP_RECV_ENTRIES = 3 };
+idp_status idp_shard_plan_create(int64_t n_nodes, const int64_t* rowptr, const int64_t* col, int n_shards,
+                                 const int64_t* row_begin, idp_shard_plan** out);
+void idp_shard_plan_destroy(idp_shard_plan* plan);
+idp_status idp_shard_plan_info(const idp_shard_plan* plan, int shard, int64_t* n_local, int64_t* own_begin,
+                               int64_t* own_end, int64_t* nnz_local);
+idp_status idp_shard_plan_nodes(const idp_shard_plan* plan, int shard, int64_t* nodes);
+idp_status idp_shard_plan_csr(const idp_shard_plan* plan, int shard, int64_t* rowptr, int64_t* col, int64_t* entry);
+idp_status idp_shard_plan_list(const idp_shard_plan* plan, int shard, int peer, int kind, int64_t* count,
+                               int64_t* ids);
+
+/* The sharded stage on the current GPU: one context per shard of the plan
+ * (its rows and ghosts, the matrices of idp_upload_sparsity restricted to
+ * them), all on cuda_stream.  Each euler_step runs phase by phase over the
+ * shards, and between phases the shards exchange, at the synchronisation
+ * points of Fig. 2 (Sec. 4.1): alpha_j and a min-reduction of the CFL bound
+ * after Step 2, R_j after Step 3, l_ji after Step 4 and after every limiter
+ * pass, U_j after Step 6.  An exchange is a gather kernel on the sender, one
+ * device-to-device cudaMemcpyAsync into the receiver's buffer and a scatter
+ * kernel on the receiver.  Every own row computes what an unsharded context
+ * computes, in the same order: states, time and tau_n are bitwise those of
+ * idp_step on the same matrices.
+ *   cfg           : NULL for the defaults; FP64 only, relax = 0, renumber = 0
+ *                   (else IDP_ERR_ARG)
+ *   plan          : borrowed during the call (the group keeps a copy)
+ *   mij, cij, mi, node_bc, inflow_state : the whole mesh's arrays, as for
+ *                   idp_upload_sparsity with the plan's pattern; mi NULL: the
+ *                   row sums of m_ij
+ * idp_shards_init_state / idp_shards_get_state take the whole state (5 x
+ * n_nodes host doubles, global numbering; init rejects non-admissible states);
+ * idp_shards_step enqueues n_steps SSP-RK3 steps (eq. ssprk3) without waiting;
+ * idp_shards_synchronize waits and returns the first latched error of any
+ * shard (a shard with an error in the third stage keeps its state, the others
+ * may not); idp_shards_get_time as idp_get_time.  idp_shards_context lends the
+ * context of one shard (for idp_get_field and the like; local numbering, its
+ * ghost rows hold exchanged or partial values); it stays owned by the group.
+ * idp_shards_halo_size: values per exchange summed over all links (node
+ * values per field, entry values) and the launches of the last
+ * idp_shards_step; any pointer may be NULL. */
+typedef struct idp_shards idp_shards;
+idp_status idp_shards_create(const idp_config* cfg, void* cuda_stream, const idp_shard_plan* plan, const double* mij,
+                             const double* cij, const double* mi, const int32_t* node_bc, const double* inflow_state,
+                             idp_shards** out);
+void idp_shards_destroy(idp_shards* sh);
+const char* idp_shards_last_error(const idp_shards* sh);
+idp_status idp_shards_init_state(idp_shards* sh, const double* U);
+idp_status idp_shards_get_state(idp_shards* sh, double* U);
+idp_status idp_shards_step(idp_shards* sh, int n_steps);
+idp_status idp_shards_synchronize(idp_shards* sh);
+idp_status idp_shards_get_time(idp_shards* sh, double* t, double* last_tau);
+idp_status idp_shards_context(idp_shards* sh, int shard, idp_ctx** out);
+idp_status idp_shards_halo_size(const idp_shards* sh, int64_t* node_values, int64_t* entry_values,
+                                int64_t* launches);
+
 /* FP64 fused multiply-add rate of the current GPU, for the roofline of the
  * FP64 stage (its heavy kernels are bound by the FP64 pipe; the paper has no
  * counterpart, it measures CPU peaks instead, Sec. 5, Table 1).  Runs one

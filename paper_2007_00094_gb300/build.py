@@ -15,8 +15,9 @@ LIB = os.path.join(HERE, "libidp.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["idp_stage.cu", "idp_mixed.cu", "idp_api.cu", "idp_noalloc.cu", "idp_adjoint.cu", "idp_probe.cu"]
-CXX_SOURCES = ["idp_mesh.cpp"]
+CUDA_SOURCES = ["idp_stage.cu", "idp_mixed.cu", "idp_api.cu", "idp_noalloc.cu", "idp_adjoint.cu", "idp_probe.cu",
+                "idp_shard.cu"]
+CXX_SOURCES = ["idp_mesh.cpp", "idp_shard_plan.cpp"]
 # The FP32-mixed kernels run the same row functions in the per-step kernels and
 # in the persistent kernel, whose results must be bitwise equal.  Without FMA
 # contraction every multiply and add is rounded as written (fused only where

@@ -815,6 +815,47 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
   return launches;
 }
 
+int euler_phase_count(const StageConfig& C) { return 3 + C.limiter_passes; }
+
+double* phase_l_buffer(const StageBuffers& B, int phase) { return B.l[(phase - 2) & 1]; }
+
+int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
+                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
+                       bool skip_write_on_error, int phase, cudaStream_t s, int block) {
+  const unsigned grid = (unsigned)((G.n + block - 1) / block);
+  const int passes = C.limiter_passes;
+  if (phase == 0) {
+    k_node<<<grid, block, 0, s>>>(G.n, Uin, B.node, B.scal);
+    k_edge<<<grid, block, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.scal);
+    k_diag<<<grid, block, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, nullptr, B.scal);
+    return 3;
+  }
+  if (phase == 1) {
+    k_low_order<<<grid, block, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
+                                       tau_mode, accumulate_time ? 1 : 0);
+    return 1;
+  }
+  if (phase == 2) {
+    k_flux_limit<<<grid, block, 0, s>>>(G, C, Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], B.scal, tau_mode);
+    return 1;
+  }
+  // pass p reads the state of pass p - 1 (U^L for p = 1) and l of pass p - 1;
+  // the buffers alternate as in launch_euler_step
+  auto state_after = [&](int p) -> double* { return p == 0 ? B.UL : B.Uw[(p - 1) & 1]; };
+  const int p = phase - 2;
+  if (p >= 1 && p < passes) {
+    k_limiter_pass<<<grid, block, 0, s>>>(G, C, state_after(p - 1), B.Uw[(p - 1) & 1], B.P, B.l[(p - 1) & 1],
+                                          B.l[p & 1], B.bnd);
+    return 1;
+  }
+  if (p == passes) {
+    k_final<<<grid, block, 0, s>>>(G, C, state_after(passes - 1), B.P, B.l[(passes - 1) & 1], Un, Uout, B.Ulast,
+                                   B.scal, blend, skip_write_on_error ? 1 : 0);
+    return 1;
+  }
+  return 0;
+}
+
 cudaError_t launch_barrier_selftest(GridBarrier* bar, long long spin_limit, int blocks, int rounds, int skip_block0,
                                     unsigned int* passes, DeviceScalars* scal, cudaStream_t s) {
   cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);

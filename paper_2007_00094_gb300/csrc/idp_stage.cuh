@@ -270,6 +270,24 @@ int launch_euler_step(const DeviceGraph& G, const StageBuffers& B, const StageCo
                       bool skip_write_on_error, bool trace, cudaStream_t s, Profiler* prof = nullptr,
                       int block = 128, GridBarrier* bar = nullptr);
 
+// One euler_step in phases, for a caller that interleaves the phases of
+// several contexts (the sharded stage) and exchanges, between two phases, the
+// values that the next phase reads at rows of other shards:
+//   phase 0             Steps 0-2: node quantities, d_ij, alpha_i, CFL bound
+//                       (then: alpha_j and the tau reduction)
+//   phase 1             Step 3: U^L, R_i, bounds (then: R_j)
+//   phase 2             Step 4: P_ij, l_ij (then: l_ji, in phase_l_buffer)
+//   phase 2 + p         limiter pass p = 1 .. passes-1 of Step 5 (then: l_ji)
+//   phase 2 + passes    Step 6: last pass, boundary values, RK blend (then: U)
+// The kernels and arguments are those of launch_euler_step's per-step
+// schedule.  Returns the number of launches.
+int euler_phase_count(const StageConfig& C);
+int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageConfig& C, const double* Uin,
+                       double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
+                       bool skip_write_on_error, int phase, cudaStream_t s, int block);
+// The limiter-value buffer that phase 2 + p (p >= 0) writes.
+double* phase_l_buffer(const StageBuffers& B, int phase);
+
 // Blocks of the persistent stage kernel that fit on the device at once.
 int persistent_grid_limit(int block, bool mixed);
 // The FP32-mixed persistent stage kernel (idp_mixed.cu).

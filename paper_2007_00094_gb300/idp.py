@@ -35,7 +35,12 @@ EXPORTED = ["idp_config_default", "idp_create", "idp_destroy", "idp_last_error",
             "idp_get_instance_times", "idp_set_schedule", "idp_autotune", "idp_adjoint_euler_step",
             "idp_adjoint_record", "idp_adjoint_backward", "idp_barrier_selftest", "idp_upload_mesh_quad",
             "idp_entry_table_size", "idp_upload_sparsity", "idp_check_local_bounds", "idp_probe_fp64_peak",
-            "idp_row_pattern_count"]
+            "idp_row_pattern_count", "idp_shard_plan_create", "idp_shard_plan_destroy", "idp_shard_plan_info",
+            "idp_shard_plan_nodes", "idp_shard_plan_csr", "idp_shard_plan_list", "idp_shards_create",
+            "idp_shards_destroy", "idp_shards_last_error", "idp_shards_init_state", "idp_shards_get_state",
+            "idp_shards_step", "idp_shards_synchronize", "idp_shards_get_time", "idp_shards_context",
+            "idp_shards_halo_size"]
+SEND_NODES, RECV_NODES, SEND_ENTRIES, RECV_ENTRIES = 0, 1, 2, 3
 NOALLOC_MAX_NODES = 2097152
 KERNELS = ["node", "edge", "diag", "low_order", "flux_limit", "limiter_pass", "final", "adj_final", "adj_pass",
            "adj_flux", "adj_low", "adj_tau", "adj_diag", "adj_edge", "adj_gather"]
@@ -117,6 +122,25 @@ def load(path: str = LIB_PATH):
     L.idp_adjoint_record.argtypes = [_vp, C.c_int, C.c_int]
     L.idp_adjoint_backward.argtypes = [_vp, _vp, _vp, C.c_int]
     L.idp_barrier_selftest.argtypes = [_vp, C.c_int, C.c_int, C.c_int, C.c_longlong, C.POINTER(C.c_int)]
+    L.idp_shard_plan_create.argtypes = [C.c_int64, _i64p, _i64p, C.c_int, _i64p, C.POINTER(_vp)]
+    L.idp_shard_plan_destroy.argtypes = [_vp]
+    L.idp_shard_plan_destroy.restype = None
+    L.idp_shard_plan_info.argtypes = [_vp, C.c_int, _i64p, _i64p, _i64p, _i64p]
+    L.idp_shard_plan_nodes.argtypes = [_vp, C.c_int, _i64p]
+    L.idp_shard_plan_csr.argtypes = [_vp, C.c_int, _i64p, _i64p, _i64p]
+    L.idp_shard_plan_list.argtypes = [_vp, C.c_int, C.c_int, C.c_int, _i64p, _i64p]
+    L.idp_shards_create.argtypes = [C.POINTER(IdpConfig), _vp, _vp, _dp, _dp, _dp, _i32p, _dp, C.POINTER(_vp)]
+    L.idp_shards_destroy.argtypes = [_vp]
+    L.idp_shards_destroy.restype = None
+    L.idp_shards_last_error.argtypes = [_vp]
+    L.idp_shards_last_error.restype = C.c_char_p
+    L.idp_shards_init_state.argtypes = [_vp, _dp]
+    L.idp_shards_get_state.argtypes = [_vp, _dp]
+    L.idp_shards_step.argtypes = [_vp, C.c_int]
+    L.idp_shards_synchronize.argtypes = [_vp]
+    L.idp_shards_get_time.argtypes = [_vp, _dp, _dp]
+    L.idp_shards_context.argtypes = [_vp, C.c_int, C.POINTER(_vp)]
+    L.idp_shards_halo_size.argtypes = [_vp, _i64p, _i64p, _i64p]
     _lib = L
     return L
 
@@ -449,3 +473,138 @@ def rollout(solver, U0, n_steps, checkpoint_every=10):
     if _ROLLOUT is None:
         _ROLLOUT = _rollout_function()
     return _ROLLOUT.apply(U0, solver, int(n_steps), int(checkpoint_every))
+
+
+class ShardPlan:
+    """Row partition with one ghost layer and its exchange lists
+    (idp_shard_plan_*; host memory only, usable without a GPU)."""
+
+    def __init__(self, rowptr, col, n_shards, row_begin=None):
+        L = load()
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int64)
+        self.n = len(self.rowptr) - 1
+        self.n_shards = int(n_shards)
+        rb = None if row_begin is None else np.ascontiguousarray(row_begin, dtype=np.int64)
+        self._plan = _vp()
+        st = L.idp_shard_plan_create(self.n, _ptr(self.rowptr, _i64p), _ptr(self.col, _i64p), self.n_shards,
+                                     None if rb is None else _ptr(rb, _i64p), C.byref(self._plan))
+        if st != IDP_OK:
+            raise IdpError(st, "idp_shard_plan_create failed")
+
+    def close(self):
+        if self._plan:
+            load().idp_shard_plan_destroy(self._plan)
+            self._plan = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, shard):
+        """(n_local, own_begin, own_end, nnz_local) of one shard."""
+        v = [C.c_int64() for _ in range(4)]
+        st = load().idp_shard_plan_info(self._plan, int(shard), *[C.byref(x) for x in v])
+        if st != IDP_OK:
+            raise IdpError(st, "idp_shard_plan_info failed")
+        return tuple(int(x.value) for x in v)
+
+    def nodes(self, shard):
+        out = np.empty(self.info(shard)[0], dtype=np.int64)
+        _check(None, load().idp_shard_plan_nodes(self._plan, int(shard), _ptr(out, _i64p)))
+        return out
+
+    def csr(self, shard):
+        """Local (rowptr, col, global entry of each local entry)."""
+        nl, _, _, el = self.info(shard)
+        rp, cl, en = np.empty(nl + 1, np.int64), np.empty(el, np.int64), np.empty(el, np.int64)
+        _check(None, load().idp_shard_plan_csr(self._plan, int(shard), _ptr(rp, _i64p), _ptr(cl, _i64p),
+                                               _ptr(en, _i64p)))
+        return rp, cl, en
+
+    def list(self, shard, peer, kind):
+        """Exchange list (SEND_NODES, RECV_NODES, SEND_ENTRIES, RECV_ENTRIES) of shard for peer."""
+        cnt = C.c_int64()
+        L = load()
+        _check(None, L.idp_shard_plan_list(self._plan, int(shard), int(peer), int(kind), C.byref(cnt), None))
+        out = np.empty(cnt.value, dtype=np.int64)
+        if cnt.value:
+            _check(None, L.idp_shard_plan_list(self._plan, int(shard), int(peer), int(kind), C.byref(cnt),
+                                               _ptr(out, _i64p)))
+        return out
+
+
+class ShardedSolver:
+    """The sharded stage on the current GPU (idp_shards_*): one context per
+    shard of a ShardPlan, with halo exchanges between the stage's phases."""
+
+    def __init__(self, sparsity, n_shards=2, row_begin=None, config: IdpConfig | None = None, stream=None,
+                 **overrides):
+        """``sparsity``: the whole mesh's matrices as for Solver(sparsity=...)
+        (rowptr, col, mij, cij (3, nnz), mi, bc, inflow)."""
+        L = load()
+        get = (lambda k: sparsity.get(k)) if isinstance(sparsity, dict) else (lambda k: getattr(sparsity, k, None))
+        self.plan = ShardPlan(get("rowptr"), get("col"), n_shards, row_begin)
+        self.n = self.plan.n
+        cfg = config or idp_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        mij = np.ascontiguousarray(get("mij"), dtype=np.float64)
+        cij = np.ascontiguousarray(get("cij"), dtype=np.float64)
+        mi, bc, inflow = get("mi"), get("bc"), get("inflow")
+        mi = None if mi is None else np.ascontiguousarray(mi, dtype=np.float64)
+        bc = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+        inflow = None if inflow is None else np.ascontiguousarray(inflow, dtype=np.float64)
+        assert cij.shape == (3, len(self.plan.col)) and mij.shape == (len(self.plan.col),)
+        self._sh = _vp()
+        st = L.idp_shards_create(C.byref(cfg), _stream_handle(stream), self.plan._plan, _ptr(mij), _ptr(cij),
+                                 None if mi is None else _ptr(mi), None if bc is None else _ptr(bc, _i32p),
+                                 None if inflow is None else _ptr(inflow), C.byref(self._sh))
+        if st != IDP_OK:
+            raise IdpError(st, "idp_shards_create failed")
+
+    def _check(self, st):
+        if st != IDP_OK:
+            raise IdpError(st, load().idp_shards_last_error(self._sh).decode())
+
+    def close(self):
+        if self._sh:
+            load().idp_shards_destroy(self._sh)
+            self._sh = _vp()
+        self.plan.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_state(self, U):
+        a = np.ascontiguousarray(U, dtype=np.float64)
+        assert a.size == 5 * self.n
+        self._check(load().idp_shards_init_state(self._sh, _ptr(a)))
+
+    def get_state(self):
+        a = np.empty((5, self.n))
+        self._check(load().idp_shards_get_state(self._sh, _ptr(a)))
+        return a
+
+    def step(self, n_steps=1):
+        self._check(load().idp_shards_step(self._sh, int(n_steps)))
+
+    def synchronize(self):
+        self._check(load().idp_shards_synchronize(self._sh))
+
+    def time(self):
+        t, tau = C.c_double(), C.c_double()
+        self._check(load().idp_shards_get_time(self._sh, C.byref(t), C.byref(tau)))
+        return t.value, tau.value
+
+    def halo_size(self):
+        """(node values per field, entry values) per exchange, and the launches of the last step call."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(load().idp_shards_halo_size(self._sh, C.byref(a), C.byref(b), C.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
