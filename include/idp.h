@@ -413,11 +413,14 @@ idp_status idp_shard_plan_list(const idp_shard_plan* plan, int shard, int peer, 
  * shards, and between phases the shards exchange, at the synchronisation
  * points of Fig. 2 (Sec. 4.1): alpha_j and a min-reduction of the CFL bound
  * after Step 2, R_j after Step 3, l_ji after Step 4 and after every limiter
- * pass, U_j after Step 6.  An exchange is a gather kernel on the sender, one
- * device-to-device cudaMemcpyAsync into the receiver's buffer and a scatter
- * kernel on the receiver.  Every own row computes what an unsharded context
- * computes, in the same order: states, time and tau_n are bitwise those of
- * idp_step on the same matrices.
+ * pass, U_j after Step 6.  Ghost rows run Steps 0-1 only.  Every shard works
+ * on a stream of its own (created by the group, ordered after cuda_stream at
+ * the start of idp_shards_step and joined into it at the end), and the
+ * exchanges order the shards by events: a gather kernel on the sender's
+ * stream, one device-to-device cudaMemcpyAsync into the receiver's buffer, a
+ * scatter kernel on the receiver's stream.  Every own row computes what an
+ * unsharded context computes, in the same order: states, time and tau_n are
+ * bitwise those of idp_step on the same matrices.
  *   cfg           : NULL for the defaults; FP64 only, relax = 0, renumber = 0
  *                   (else IDP_ERR_ARG)
  *   plan          : borrowed during the call (the group keeps a copy)
@@ -425,7 +428,8 @@ idp_status idp_shard_plan_list(const idp_shard_plan* plan, int shard, int peer, 
  *                   idp_upload_sparsity with the plan's pattern; mi NULL: the
  *                   row sums of m_ij
  * idp_shards_init_state / idp_shards_get_state take the whole state (5 x
- * n_nodes host doubles, global numbering; init rejects non-admissible states);
+ * n_nodes host doubles, global numbering; init rejects non-admissible states)
+ * and wait for all shards first;
  * idp_shards_step enqueues n_steps SSP-RK3 steps (eq. ssprk3) without waiting;
  * idp_shards_synchronize waits and returns the first latched error of any
  * shard (a shard with an error in the third stage keeps its state, the others

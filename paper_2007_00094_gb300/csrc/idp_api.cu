@@ -643,6 +643,8 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
   idp::DeviceGraph& G = ctx->G;
   G.n = L.n;
   G.n_slots = L.n_slots;
+  G.row0 = 0;
+  G.row1 = L.n;
   int32_t *slice_ptr, *row_len, *col, *tpos, *bc;
   uint8_t* flags;
   double *cx, *cy, *cz, *mij, *mi, *inv_mi, *lam, *cn, *inv_cn, *csx, *csy, *csz;

@@ -11,17 +11,20 @@
 //   after each pass   l_ji again (the pass recomputes it)
 //   after Step 6      the stage output U_j of ghost rows
 //
-// Ghost rows run the kernels too, on their entries inside the shard: Steps 0
-// and 1 there are exact (node values, and the pair values of entries whose
-// pair a ghost row evaluates, d_ij and the flux differences, which an own row
-// reads through its lower entries), the rest is overwritten by the exchanges
-// before an own row reads it.  Every own row therefore computes what it
-// computes unsharded, in the same order, and the result is bitwise the same.
+// Ghost rows run Steps 0 and 1, on their entries inside the shard, and are
+// exact there: node values, and the pair values of the pairs a ghost row
+// evaluates (d_ij, 1/(2 d_ij), the flux differences and m_j.c_ij), which an
+// own row reads through its lower entries.  Steps 2-6 run on own rows only;
+// what they read at ghost rows arrives by the exchanges.  Every own row
+// therefore computes what it computes unsharded, in the same order, and the
+// result is bitwise the same.
 //
-// An exchange is pack (a gather kernel on the sender), one cudaMemcpyAsync
-// of the packed buffer into the receiver's buffer, and unpack (a scatter
-// kernel on the receiver); with one GPU per shard the copy is the
-// transfer between GPUs.
+// Each shard runs on a stream of its own, as it would on its own GPU; the
+// exchanges and the tau reduction order the shards by events.  An exchange
+// is pack (a gather kernel on the sender's stream), one cudaMemcpyAsync of
+// the packed buffer into the receiver's buffer (with one GPU per shard, the
+// transfer between GPUs), and unpack (a scatter kernel on the receiver's
+// stream).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,19 +40,29 @@ struct idp_shard_plan {
 };
 
 struct idp_shards {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the caller's stream
   std::string err;
   idp::ShardPlan P;
   std::vector<idp_ctx*> ctx;
+  // Each shard works on a stream of its own, as it would on a GPU of its
+  // own; what one shard needs from another is ordered by events.
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;  // every event the group created
+  std::vector<cudaEvent_t> ev_phase, ev_end;  // per shard
+  cudaEvent_t ev_start = nullptr, ev_tau = nullptr;
   // one link per ordered pair of shards with values to exchange
   struct Link {
     int src = 0, dst = 0;
     int64_t nn = 0, ne = 0;                  // node and entry values per field
     int64_t *sn = nullptr, *dn = nullptr;    // sender / receiver local node ids
     int64_t *ss = nullptr, *ds = nullptr;    // sender / receiver slots
-    double *send = nullptr, *recv = nullptr; // packed buffers (max(5 nn, ne) doubles)
+    double* send = nullptr;                  // packed buffer of the sender (max(5 nn, ne) doubles)
+    double* recv[2] = {nullptr, nullptr};    // receiver's buffers, alternating between exchanges
+    cudaEvent_t copied = nullptr;            // the sender's copy of the current exchange is done
+    cudaEvent_t unpacked[2] = {nullptr, nullptr};  // the receiver has emptied recv[k]
   };
   std::vector<Link> links;
+  int64_t exchanges = 0;  // parity of the receive buffers
   unsigned long long** words = nullptr;  // device: each shard's CFL reduction word
   std::vector<void*> allocs;
   bool has_state = false;
@@ -137,35 +150,65 @@ unsigned grid_for(int64_t work) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-// Exchanges a node array (comps fields, stride n of each shard) or a slot
-// array over every link.  field(s) gives shard s's array.
-template <typename F>
-int exchange_nodes(idp_shards* sh, int comps, F&& field) {
+// One exchange over every link: pack(k) enqueues the sender's gather of
+// link k into its send buffer, unpack(k, buf) the receiver's scatter.  The
+// sender copies into the receiver's buffer of this exchange's parity once
+// the receiver has emptied it (two exchanges back), and the receiver waits
+// for the copy.
+template <typename Pack, typename Unpack, typename Values>
+int exchange(idp_shards* sh, Pack&& pack, Unpack&& unpack, Values&& values) {
+  const int par = (int)(sh->exchanges++ & 1);
   int launches = 0;
-  for (const idp_shards::Link& k : sh->links) {
-    if (k.nn == 0) continue;
-    const int64_t m = k.nn;
-    k_pack_nodes<<<grid_for(comps * m), kXBlock, 0, sh->stream>>>(field(k.src), sh->ctx[k.src]->G.n, comps, k.sn, m,
-                                                                   k.send);
-    cudaMemcpyAsync(k.recv, k.send, sizeof(double) * comps * m, cudaMemcpyDeviceToDevice, sh->stream);
-    k_unpack_nodes<<<grid_for(comps * m), kXBlock, 0, sh->stream>>>(field(k.dst), sh->ctx[k.dst]->G.n, comps, k.dn,
-                                                                     m, k.recv);
-    launches += 2;
+  for (idp_shards::Link& k : sh->links) {
+    const int64_t m = values(k);
+    if (m == 0) continue;
+    cudaStream_t s = sh->streams[k.src];
+    pack(k, s);
+    cudaStreamWaitEvent(s, k.unpacked[par], 0);
+    cudaMemcpyAsync(k.recv[par], k.send, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    cudaEventRecord(k.copied, s);
+    ++launches;
+  }
+  for (idp_shards::Link& k : sh->links) {
+    if (values(k) == 0) continue;
+    cudaStream_t s = sh->streams[k.dst];
+    cudaStreamWaitEvent(s, k.copied, 0);
+    unpack(k, k.recv[par], s);
+    cudaEventRecord(k.unpacked[par], s);
+    ++launches;
   }
   return launches;
 }
 
+// A node array of comps fields (stride n of each shard); field(s) gives
+// shard s's array.
+template <typename F>
+int exchange_nodes(idp_shards* sh, int comps, F&& field) {
+  return exchange(
+      sh,
+      [&](const idp_shards::Link& k, cudaStream_t s) {
+        k_pack_nodes<<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.src), sh->ctx[k.src]->G.n, comps, k.sn, k.nn,
+                                                                 k.send);
+      },
+      [&](const idp_shards::Link& k, const double* buf, cudaStream_t s) {
+        k_unpack_nodes<<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.dst), sh->ctx[k.dst]->G.n, comps, k.dn, k.nn,
+                                                                   buf);
+      },
+      [&](const idp_shards::Link& k) { return (int64_t)comps * k.nn; });
+}
+
+// A per-slot array.
 template <typename F>
 int exchange_slots(idp_shards* sh, F&& field) {
-  int launches = 0;
-  for (const idp_shards::Link& k : sh->links) {
-    if (k.ne == 0) continue;
-    k_pack_slots<<<grid_for(k.ne), kXBlock, 0, sh->stream>>>(field(k.src), k.ss, k.ne, k.send);
-    cudaMemcpyAsync(k.recv, k.send, sizeof(double) * k.ne, cudaMemcpyDeviceToDevice, sh->stream);
-    k_unpack_slots<<<grid_for(k.ne), kXBlock, 0, sh->stream>>>(field(k.dst), k.ds, k.ne, k.recv);
-    launches += 2;
-  }
-  return launches;
+  return exchange(
+      sh,
+      [&](const idp_shards::Link& k, cudaStream_t s) {
+        k_pack_slots<<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.src), k.ss, k.ne, k.send);
+      },
+      [&](const idp_shards::Link& k, const double* buf, cudaStream_t s) {
+        k_unpack_slots<<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.dst), k.ds, k.ne, buf);
+      },
+      [](const idp_shards::Link& k) { return k.ne; });
 }
 
 // One euler_step of every shard (the roles of U^n, the stage state and the
@@ -185,11 +228,19 @@ int sharded_stage(idp_shards* sh, int stage) {
       double* Uout = stage == 2 ? B.U : B.Us;
       const int blend = stage == 0 ? idp::kBlendNone : (stage == 1 ? idp::kBlendStage2 : idp::kBlendStage3);
       launches += idp::launch_euler_phase(c->G, B, c->C, Uin, Uout, B.U, blend, stage == 0 ? 0 : 1, stage == 0,
-                                          stage == 2, ph, sh->stream, c->block);
+                                          stage == 2, ph, sh->streams[s], c->block);
     }
     if (S == 1) continue;
     if (ph == 0) {
-      k_tau_allreduce<<<1, 1, 0, sh->stream>>>(sh->words, S);
+      // tau_n is global: the minimum of every shard's CFL bound, formed on
+      // shard 0's stream once every shard has its own
+      for (int s = 0; s < S; ++s) {
+        cudaEventRecord(sh->ev_phase[s], sh->streams[s]);
+        cudaStreamWaitEvent(sh->streams[0], sh->ev_phase[s], 0);
+      }
+      k_tau_allreduce<<<1, 1, 0, sh->streams[0]>>>(sh->words, S);
+      cudaEventRecord(sh->ev_tau, sh->streams[0]);
+      for (int s = 1; s < S; ++s) cudaStreamWaitEvent(sh->streams[s], sh->ev_tau, 0);
       ++launches;
       launches += exchange_nodes(sh, 1, [&](int s) { return sh->ctx[s]->B.alpha; });
     } else if (ph == 1) {
@@ -201,6 +252,18 @@ int sharded_stage(idp_shards* sh, int stage) {
     }
   }
   return launches;
+}
+
+// Waits (on the host) for every shard's stream.
+idp_status sync_all(idp_shards* sh) {
+  for (cudaStream_t s : sh->streams) SH_CUDA(sh, cudaStreamSynchronize(s));
+  return IDP_OK;
+}
+
+idp_status new_event(idp_shards* sh, cudaEvent_t* e) {
+  SH_CUDA(sh, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  sh->events.push_back(*e);
+  return IDP_OK;
 }
 
 }  // namespace
@@ -274,9 +337,11 @@ idp_status idp_shard_plan_list(const idp_shard_plan* plan, int shard, int peer, 
 
 void idp_shards_destroy(idp_shards* sh) {
   if (!sh) return;
-  if (!sh->ctx.empty()) cudaStreamSynchronize(sh->stream);
+  for (cudaStream_t s : sh->streams) cudaStreamSynchronize(s);
   for (idp_ctx* c : sh->ctx) idp_destroy(c);
   for (void* p : sh->allocs) cudaFree(p);
+  for (cudaEvent_t e : sh->events) cudaEventDestroy(e);
+  for (cudaStream_t s : sh->streams) cudaStreamDestroy(s);
   delete sh;
 }
 
@@ -324,6 +389,20 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
   }
   idp_status st = IDP_OK;
   for (int s = 0; s < S && st == IDP_OK; ++s) {
+    cudaStream_t q = nullptr;
+    if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      st = sfail(sh, IDP_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+      break;
+    }
+    sh->streams.push_back(q);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((st = new_event(sh, &a)) || (st = new_event(sh, &b))) break;
+    sh->ev_phase.push_back(a);
+    sh->ev_end.push_back(b);
+  }
+  if (st == IDP_OK && (st = new_event(sh, &sh->ev_start)) == IDP_OK) st = new_event(sh, &sh->ev_tau);
+  for (int s = 0; s < S && st == IDP_OK; ++s) {
     const idp::ShardLocal& L = P.shard[s];
     const int64_t nl = (int64_t)L.nodes.size(), el = (int64_t)L.col.size();
     std::vector<double> lm(el), lc(3 * el), lmi(nl);
@@ -338,12 +417,19 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
       if (node_bc) lbc[l] = node_bc[L.nodes[l]];
     }
     idp_ctx* c = nullptr;
-    st = idp_create(&cfg, cuda_stream, &c);
+    st = idp_create(&cfg, sh->streams[s], &c);
     if (st != IDP_OK) break;
     sh->ctx.push_back(c);
     st = idp_upload_sparsity(c, nl, L.rowptr.data(), L.col.data(), lm.data(), lc.data(), lmi.data(), lbc.data(),
                              inflow_state);
-    if (st != IDP_OK) sh->err = std::string("shard ") + std::to_string(s) + ": " + idp_last_error(c);
+    if (st != IDP_OK) {
+      sh->err = std::string("shard ") + std::to_string(s) + ": " + idp_last_error(c);
+      break;
+    }
+    // ghost rows take Steps 0-1 only: what they compute after that is
+    // overwritten by the exchanges before an own row reads it
+    c->G.row0 = L.own_lo;
+    c->G.row1 = L.own_hi;
   }
   // links: the sender's lists index its own rows, the receiver's its ghosts;
   // entries become slots of each side's layout
@@ -364,7 +450,9 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
       for (size_t q = 0; q < de.size(); ++q) ds[q] = sh->ctx[b]->L.slot_of_entry[de[q]];
       const size_t buf = (size_t)std::max<int64_t>(5 * k.nn, k.ne);
       if ((st = supload(sh, &k.sn, sn)) || (st = supload(sh, &k.dn, dn)) || (st = supload(sh, &k.ss, ss)) ||
-          (st = supload(sh, &k.ds, ds)) || (st = salloc(sh, &k.send, buf)) || (st = salloc(sh, &k.recv, buf)))
+          (st = supload(sh, &k.ds, ds)) || (st = salloc(sh, &k.send, buf)) || (st = salloc(sh, &k.recv[0], buf)) ||
+          (st = salloc(sh, &k.recv[1], buf)) || (st = new_event(sh, &k.copied)) ||
+          (st = new_event(sh, &k.unpacked[0])) || (st = new_event(sh, &k.unpacked[1])))
         break;
       sh->links.push_back(k);
     }
@@ -389,6 +477,8 @@ idp_status idp_shards_context(idp_shards* sh, int shard, idp_ctx** out) {
 
 idp_status idp_shards_init_state(idp_shards* sh, const double* U) {
   if (!sh || !U) return IDP_ERR_ARG;
+  idp_status st0 = sync_all(sh);
+  if (st0 != IDP_OK) return st0;
   const int64_t n = sh->P.n;
   for (size_t s = 0; s < sh->ctx.size(); ++s) {
     const idp::ShardLocal& L = sh->P.shard[s];
@@ -406,6 +496,8 @@ idp_status idp_shards_init_state(idp_shards* sh, const double* U) {
 idp_status idp_shards_get_state(idp_shards* sh, double* U) {
   if (!sh || !U) return IDP_ERR_ARG;
   if (!sh->has_state) return sfail(sh, IDP_ERR_STATE, "no state");
+  idp_status st0 = sync_all(sh);
+  if (st0 != IDP_OK) return st0;
   const int64_t n = sh->P.n;
   for (size_t s = 0; s < sh->ctx.size(); ++s) {
     const idp::ShardLocal& L = sh->P.shard[s];
@@ -422,9 +514,17 @@ idp_status idp_shards_get_state(idp_shards* sh, double* U) {
 idp_status idp_shards_step(idp_shards* sh, int n_steps) {
   if (!sh || n_steps < 0) return IDP_ERR_ARG;
   if (!sh->has_state) return sfail(sh, IDP_ERR_STATE, "no state");
+  // the shards' streams start after what the caller enqueued before, and
+  // the caller's stream continues once every shard is done
+  SH_CUDA(sh, cudaEventRecord(sh->ev_start, sh->stream));
+  for (cudaStream_t s : sh->streams) SH_CUDA(sh, cudaStreamWaitEvent(s, sh->ev_start, 0));
   int64_t launches = 0;
   for (int k = 0; k < n_steps; ++k)
     for (int stage = 0; stage < 3; ++stage) launches += sharded_stage(sh, stage);
+  for (size_t s = 0; s < sh->streams.size(); ++s) {
+    SH_CUDA(sh, cudaEventRecord(sh->ev_end[s], sh->streams[s]));
+    SH_CUDA(sh, cudaStreamWaitEvent(sh->stream, sh->ev_end[s], 0));
+  }
   sh->launches = launches;
   SH_CUDA(sh, cudaGetLastError());
   return IDP_OK;

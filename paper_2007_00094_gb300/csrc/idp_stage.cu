@@ -2,6 +2,7 @@
 // sliced-ELL graph.  Kernel boundaries are the global dependencies of the
 // algorithm (Fig. 2): alpha_j and d_ji after Step 1, tau after Step 2, R_j
 // after Step 3, l_ji after Steps 4 and 5.
+#include <algorithm>
 #include <cfloat>
 
 #include "idp_internal.h"
@@ -12,6 +13,11 @@ namespace idp {
 namespace {
 
 constexpr int kBlock = 128;  // state-check kernels
+
+// Rows of the per-step kernels of Steps 2-6: [row0, row1), launched from the
+// start of row0's slice so that a warp's rows share one slice.
+__device__ __forceinline__ int64_t row_start(const DeviceGraph& G) { return G.row0 & ~(int64_t)(kSlice - 1); }
+__device__ __forceinline__ bool computes_row(const DeviceGraph& G, int64_t r) { return r >= G.row0 && r < G.row1; }
 
 __device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
   return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
@@ -232,8 +238,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_diag(DeviceGraph G, const double*
                                                  double* __restrict__ dinv, const double* __restrict__ dF,
                                                  const double* __restrict__ mc, double* __restrict__ alpha,
                                                  double* __restrict__ ab, DeviceScalars* scal) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  reduce_tau_candidate(G, r, r < G.n ? row_diag(G, U, Q, d, dinv, dF, mc, alpha, ab, r) : INFINITY);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  reduce_tau_candidate(G, r, computes_row(G, r) ? row_diag(G, U, Q, d, dinv, dF, mc, alpha, ab, r) : INFINITY);
 }
 
 // Step 3: low-order update through the bar states (eq. def-ubar), R_i
@@ -319,9 +325,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order(DeviceGraph G, StageCon
                                                       const double* __restrict__ alpha, double* __restrict__ UL,
                                                       double* __restrict__ R, double* __restrict__ bnd,
                                                       DeviceScalars* scal, int tau_mode, int accumulate_time) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
-  if (r < G.n) row_low_order(G, C, U, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  instance_books(G, t, tau_mode, C.cfl, accumulate_time, scal);
+  const int64_t r = row_start(G) + t;
+  if (computes_row(G, r)) row_low_order(G, C, U, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
 }
 
 // Step 4: antidiffusive fluxes P_ij (eq. def-p) with b_ij = -m_ij/m_j,
@@ -381,8 +388,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_flux_limit(DeviceGraph G, StageCo
                                                        const double* __restrict__ bnd, double* __restrict__ P,
                                                        double* __restrict__ l, const DeviceScalars* scal,
                                                        int tau_mode) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_flux_limit(G, C, U, d, alpha, UL, R, bnd, P, l, tau_mode, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_flux_limit(G, C, U, d, alpha, UL, R, bnd, P, l, tau_mode, r);
 }
 
 // Steps 5, 6, ...: U_i += sum_j lambda_i min(l_ij, l_ji) P_ij, then (not in
@@ -480,8 +487,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_limiter_pass(DeviceGraph G, Stage
                                                          double* __restrict__ Unext, double* __restrict__ P,
                                                          const double* __restrict__ lold, double* __restrict__ lnew,
                                                          const double* __restrict__ bnd) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_limiter_pass(G, C, Ucur, Unext, P, lold, lnew, bnd, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_limiter_pass(G, C, Ucur, Unext, P, lold, lnew, bnd, r);
 }
 
 // Last limiter pass, boundary post-processing (slip walls drop the flagged
@@ -540,8 +547,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_final(DeviceGraph G, StageConfig 
                                                   const double* __restrict__ Un, double* __restrict__ Uout,
                                                   double* __restrict__ Ulim, DeviceScalars* scal, int blend,
                                                   int skip_write_on_error) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_final(G, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_final(G, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
 }
 
 // One euler_step in a single cooperative launch: the phases of the kernels
@@ -823,20 +830,24 @@ int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageC
                        double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
                        bool skip_write_on_error, int phase, cudaStream_t s, int block) {
   const unsigned grid = (unsigned)((G.n + block - 1) / block);
+  // Steps 2-6 over rows [row0, row1) (the first block also keeps the
+  // instance books, which need at least n_inst threads)
+  const int64_t own = std::max<int64_t>(G.row1 - (G.row0 & ~(int64_t)(kSlice - 1)), G.n_inst);
+  const unsigned grid_own = (unsigned)((own + block - 1) / block);
   const int passes = C.limiter_passes;
   if (phase == 0) {
     k_node<<<grid, block, 0, s>>>(G.n, Uin, B.node, B.scal);
     k_edge<<<grid, block, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.scal);
-    k_diag<<<grid, block, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, nullptr, B.scal);
+    k_diag<<<grid_own, block, 0, s>>>(G, Uin, B.node, B.d, B.dinv, B.P, B.l[1], B.alpha, nullptr, B.scal);
     return 3;
   }
   if (phase == 1) {
-    k_low_order<<<grid, block, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
+    k_low_order<<<grid_own, block, 0, s>>>(G, C, Uin, B.node, B.d, B.dinv, B.P, B.alpha, B.UL, B.R, B.bnd, B.scal,
                                        tau_mode, accumulate_time ? 1 : 0);
     return 1;
   }
   if (phase == 2) {
-    k_flux_limit<<<grid, block, 0, s>>>(G, C, Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], B.scal, tau_mode);
+    k_flux_limit<<<grid_own, block, 0, s>>>(G, C, Uin, B.d, B.alpha, B.UL, B.R, B.bnd, B.P, B.l[0], B.scal, tau_mode);
     return 1;
   }
   // pass p reads the state of pass p - 1 (U^L for p = 1) and l of pass p - 1;
@@ -844,12 +855,12 @@ int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageC
   auto state_after = [&](int p) -> double* { return p == 0 ? B.UL : B.Uw[(p - 1) & 1]; };
   const int p = phase - 2;
   if (p >= 1 && p < passes) {
-    k_limiter_pass<<<grid, block, 0, s>>>(G, C, state_after(p - 1), B.Uw[(p - 1) & 1], B.P, B.l[(p - 1) & 1],
+    k_limiter_pass<<<grid_own, block, 0, s>>>(G, C, state_after(p - 1), B.Uw[(p - 1) & 1], B.P, B.l[(p - 1) & 1],
                                           B.l[p & 1], B.bnd);
     return 1;
   }
   if (p == passes) {
-    k_final<<<grid, block, 0, s>>>(G, C, state_after(passes - 1), B.P, B.l[(passes - 1) & 1], Un, Uout, B.Ulast,
+    k_final<<<grid_own, block, 0, s>>>(G, C, state_after(passes - 1), B.P, B.l[(passes - 1) & 1], Un, Uout, B.Ulast,
                                    B.scal, blend, skip_write_on_error ? 1 : 0);
     return 1;
   }

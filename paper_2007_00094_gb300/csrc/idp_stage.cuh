@@ -14,6 +14,9 @@ namespace idp {
 struct DeviceGraph {
   int64_t n;
   int64_t n_slots;
+  // Rows that the per-step kernels of Steps 2-6 compute: [row0, row1), all
+  // rows unless the context is a shard (whose ghost rows need Steps 0-1 only)
+  int64_t row0, row1;
   const int32_t* slice_ptr;
   const int32_t* row_len;
   const int32_t* col;
