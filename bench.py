@@ -58,10 +58,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # one pass, no replay) on the workloads of this file at full size: the step
 # channel at h = 1/120 (FP64) and the 128^3 Sod cube (FP32-mixed), one stage
 # after three warm-up steps (profiles/ holds the launch lists).
-NCU_TRAFFIC_BYTES = {"node": 0.227e9, "edge": 5.137e9, "diag": 4.469e9, "low_order": 4.074e9,
-                     "flux_limit": 4.360e9, "limiter_pass": 7.991e9, "final": 3.723e9}
-NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 2.147e9, "low_order": 2.199e9, "flux_limit": 2.169e9,
-                           "limiter_pass": 4.717e9, "final": 2.077e9}
+NCU_TRAFFIC_BYTES = {"node": 0.225e9, "edge": 5.137e9, "diag": 4.469e9, "low_order": 4.073e9,
+                     "flux_limit": 4.360e9, "limiter_pass": 8.011e9, "final": 3.698e9}
+NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.199e9, "flux_limit": 1.819e9,
+                           "limiter_pass": 3.617e9, "final": 1.606e9}
 
 
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
@@ -549,6 +549,43 @@ def pattern_sharded(stream, args):
     return out
 
 
+def pattern_steps(stream, args):
+    """A plain run for profilers: `--warmup` SSP-RK3 steps, then `--steps`
+    more, of one workload (`--case channel`: the step channel h = 1/m;
+    `--case sod`: the Sod cube with --sod-n nodes per axis) in one precision
+    (`--precision`), unsharded or in `--shards` shards; prints ms per step."""
+    import torch
+
+    from paper_2007_00094_gb300 import workloads as W
+    from paper_2007_00094_gb300.idp import ShardedSolver, Solver
+
+    if args.case == "sod":
+        mesh = W.sod_cube_mesh(args.sod_n)
+        U0 = W.sod_state(mesh)
+    else:
+        mesh = W.forward_step_mesh(m=args.m, jitter=0.2, seed=2007)
+        U0 = W.forward_step_state(mesh)
+    if args.shards > 1:
+        s = Solver(mesh, stream=stream)
+        rowptr, col, mij, cij, mi = s.matrices()
+        s.close()
+        sp = dict(rowptr=rowptr, col=col, mij=mij, cij=cij, mi=mi, bc=mesh.bc, inflow=mesh.inflow)
+        solver = ShardedSolver(sp, n_shards=args.shards, stream=stream, precision=args.precision)
+    else:
+        solver = Solver(mesh, stream=stream, precision=args.precision)
+    solver.init_state(U0)
+    solver.step(args.warmup)
+    solver.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    solver.synchronize()
+    solver.close()
+    return {"case": args.case, "nodes": mesh.n_nodes, "precision": args.precision, "shards": args.shards,
+            "warmup": args.warmup, "steps": args.steps, "ms_per_step": e0.elapsed_time(e1) / args.steps}
+
+
 def job_rate(local_ms, units_per_rank, dist=None, device="cpu"):
     """Whole-job rate of a weak-scaling run: the slowest rank's time (max over
     ranks) and all ranks' units divided by it.  Returns (ms_max, units/s)."""
@@ -745,8 +782,11 @@ def main():
     ap.add_argument("--adj-fd-directions", type=int, default=2)
     ap.add_argument("--adj-fd-trace-steps", type=int, default=10)
     ap.add_argument("--m2d", type=int, default=1000, help="cells per unit length of the 2D channel mesh")
+    ap.add_argument("--case", default="channel", choices=["channel", "sod"], help="workload of --only steps")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP64, 1 FP32-mixed (--only steps)")
+    ap.add_argument("--shards", type=int, default=1, help="shards on one GPU (--only steps)")
     ap.add_argument("--only", choices=["fp32_mixed", "batched", "adjoint", "adjoint_fd", "relaxation", "q1_2d",
-                                       "renumber", "sharded"],
+                                       "renumber", "sharded", "steps"],
                     help="run one pattern alone and print its JSON (no headline line)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -772,7 +812,7 @@ def main():
         run = {"fp32_mixed": pattern_mixed, "batched": pattern_batched, "adjoint": pattern_adjoint,
                "adjoint_fd": pattern_adjoint_fd,
                "relaxation": pattern_relaxation, "q1_2d": pattern_q1_2d, "renumber": pattern_renumber,
-               "sharded": pattern_sharded}[args.only]
+               "sharded": pattern_sharded, "steps": pattern_steps}[args.only]
         print(json.dumps({"pattern": args.only, **run(torch.cuda.current_stream(), args)}), flush=True)
         return
     dist = None
