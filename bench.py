@@ -38,17 +38,18 @@ FLOP_PER_NNZ = {"node": 8.0, "edge": 262.0, "diag": 1.0, "low_order": 248.0, "fl
                 "limiter_pass": 155.0, "final": 12.0}
 # FP64 arithmetic the kernels execute per stored entry: thread-level
 # 2 x DFMA + DADD + DMUL from ncu (smsp__sass_thread_inst_executed_op_d*) on
-# the step channel at h = 1/80 (17,679,673 entries).  This is the `achieved`
+# the step channel at h = 1/80 (17,679,673 entries), first euler_step after
+# three warm-up steps.  This is the `achieved`
 # work of the FP64 roofline; the paper's per-step counts above overstate what
 # these kernels execute (lambda_max once per unordered edge, flux differences
 # once per pair, powers without pow, tests on 32-bit words), so a rate from
 # them can exceed the pipe.
-FP64_FLOP_PER_NNZ_EXECUTED = {"node": 3.5, "edge": 43.4, "diag": 11.2, "low_order": 51.0, "flux_limit": 48.3,
-                              "limiter_pass": 13.5, "final": 11.2}
+FP64_FLOP_PER_NNZ_EXECUTED = {"node": 3.5, "edge": 45.3, "diag": 11.2, "low_order": 51.0, "flux_limit": 44.0,
+                              "limiter_pass": 14.6, "final": 10.6}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, % of active cycles) of
 # the same capture: the pipe also issues compares, conversions and min/max.
-FP64_PIPE_BUSY_NCU = {"node": 0.853, "edge": 0.848, "diag": 0.754, "low_order": 0.892, "flux_limit": 0.878,
-                      "limiter_pass": 0.716, "final": 0.697}
+FP64_PIPE_BUSY_NCU = {"node": 0.856, "edge": 0.847, "diag": 0.756, "low_order": 0.892, "flux_limit": 0.872,
+                      "limiter_pass": 0.791, "final": 0.671}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s).  The roofline uses the
 # rate the library's own FMA-stream probe measures in the same run
@@ -497,9 +498,9 @@ def pattern_sharded(stream, args):
     """The sharded stage on one GPU (idp_shards_*, Sec. 4.1, Fig. 1-2): the
     step channel's rows in 2 and 4 contiguous ranges with one ghost layer,
     halo exchanges (gather kernel, device copy, scatter kernel) between the
-    stage's phases.  FP64 ms per SSP-RK3 step against the unsharded stage on
-    the same matrices, the values exchanged per step, and whether the states
-    after the timed steps are bitwise equal."""
+    stage's phases.  FP64 and FP32-mixed ms per SSP-RK3 step against the
+    unsharded stage on the same matrices, the bytes exchanged per step, and
+    whether the states after the timed steps are bitwise equal."""
     import numpy as np
     import torch
 
@@ -526,26 +527,30 @@ def pattern_sharded(stream, args):
         solver.synchronize()
         return e0.elapsed_time(e1) / steps, solver.get_state()
 
-    ref = Solver(sparsity=sp, stream=stream)
-    ms_ref, U_ref = timed(ref)
-    ref.close()
     out = {"config": {"workload": f"mach3_forward_facing_step_h1/{args.m}_jitter0.2_seed2007", "nodes": mesh.n_nodes,
-                      "nnz": len(col), "steps_timed": steps, "warmup": warm, "precision": "fp64"},
-           "unsharded_ms_per_step": ms_ref}
-    for k in (2, 4):
-        sh = ShardedSolver(sp, n_shards=k, stream=stream)
-        ms, U = timed(sh)
-        nn, ne, launches = sh.halo_size()
-        ghosts = sum(sh.plan.info(q)[0] - (sh.plan.info(q)[2] - sh.plan.info(q)[1]) for q in range(k))
-        sh.close()
-        # per stage: alpha (1 field), R (5), U (5) at ghost nodes; l twice at halo entries
-        values = 3 * (11 * nn + 2 * ne)
-        out[f"shards_{k}"] = {"ms_per_step": ms, "over_unsharded": ms / ms_ref,
-                              "value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": "node-stage updates/s",
-                              "ghost_nodes": int(ghosts), "halo_node_values_per_field": nn,
-                              "halo_entry_values": ne, "exchanged_bytes_per_step": 8 * values,
-                              "launches_per_step": launches / steps,
-                              "bitwise_equal_to_unsharded": bool(np.array_equal(U, U_ref))}
+                      "nnz": len(col), "steps_timed": steps, "warmup": warm}}
+    for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
+        ref = Solver(sparsity=sp, stream=stream, precision=prec)
+        ms_ref, U_ref = timed(ref)
+        ref.close()
+        row = {"unsharded_ms_per_step": ms_ref}
+        for k in (2, 4):
+            sh = ShardedSolver(sp, n_shards=k, stream=stream, precision=prec)
+            ms, U = timed(sh)
+            nn, ne, launches = sh.halo_size()
+            ghosts = sum(sh.plan.info(q)[0] - (sh.plan.info(q)[2] - sh.plan.info(q)[1]) for q in range(k))
+            sh.close()
+            # per stage: alpha (1 field), R (5), U (5) at ghost nodes, l twice at halo entries;
+            # alpha, R and l are FP32 in the mixed stage
+            w = 8 if prec == 0 else 4
+            nbytes = 3 * (w * 6 * nn + 8 * 5 * nn + w * 2 * ne)
+            row[f"shards_{k}"] = {"ms_per_step": ms, "over_unsharded": ms / ms_ref,
+                                  "value": mesh.n_nodes * 3 / (ms * 1e-3), "unit": "node-stage updates/s",
+                                  "ghost_nodes": int(ghosts), "halo_node_values_per_field": nn,
+                                  "halo_entry_values": ne, "exchanged_bytes_per_step": nbytes,
+                                  "launches_per_step": launches / steps,
+                                  "bitwise_equal_to_unsharded": bool(np.array_equal(U, U_ref))}
+        out[name] = row
     return out
 
 
@@ -902,7 +907,7 @@ def main():
                          "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": traffic,
                          "peak_source": peak64_src, "peak_clocks": peak64_clocks,
                          "peak_derived_from_unit_counts": FP64_PEAK_TFLOPS,
-                         "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, h = 1/80) x {nnz} "
+                         "work": f"{FP64_FLOP_PER_NNZ_EXECUTED[dom]} executed FP64 flop/nnz (ncu, h = 1/80 after 3 warm-up steps) x {nnz} "
                                  f"nnz per launch",
                          "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU.get(dom),
                          "paper_flop_rate": FLOP_PER_NNZ[dom] * nnz / per_launch_s / 1e12},

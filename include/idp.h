@@ -421,8 +421,9 @@ idp_status idp_shard_plan_list(const idp_shard_plan* plan, int shard, int peer, 
  * scatter kernel on the receiver's stream.  Every own row computes what an
  * unsharded context computes, in the same order: states, time and tau_n are
  * bitwise those of idp_step on the same matrices.
- *   cfg           : NULL for the defaults; FP64 only, relax = 0, renumber = 0
- *                   (else IDP_ERR_ARG)
+ *   cfg           : NULL for the defaults; FP64 or FP32-mixed precision (the
+ *                   mixed stage exchanges its FP32 alpha, R and l), relax = 0,
+ *                   renumber = 0 (else IDP_ERR_ARG)
  *   plan          : borrowed during the call (the group keeps a copy)
  *   mij, cij, mi, node_bc, inflow_state : the whole mesh's arrays, as for
  *                   idp_upload_sparsity with the plan's pattern; mi NULL: the

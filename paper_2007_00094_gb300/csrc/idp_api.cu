@@ -710,6 +710,7 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
     // scale: it becomes an exact zero.
     double cscale = 0.0;
     for (size_t p = 0; p < ns; ++p) cscale = std::fmax(cscale, L.cn[p]);
+    if (ctx->c_scale > 0.0) cscale = ctx->c_scale;
     auto to_float = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
     auto c_float = [&](const std::vector<double>& v) {
       std::vector<float> f(v.size());

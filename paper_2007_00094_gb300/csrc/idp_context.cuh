@@ -19,7 +19,10 @@ struct idp_ctx {
   int device = 0;
   std::string err;
   bool has_mesh = false, has_state = false, has_trace = false;
-  bool stage_ran = false;  // B.Ulast and B.bnd hold the output and bounds of one stage of the current state
+  bool stage_ran = false;
+  // > 0: the largest |c_ij| of the whole mesh, for the FP32 copies of the
+  // mixed stage (a shard's context sees part of the mesh); 0: its own
+  double c_scale = 0.0;  // B.Ulast and B.bnd hold the output and bounds of one stage of the current state
   idp::HostMatrices M;
   idp::SellLayout L;
   idp::DeviceGraph G{};

@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_edge_m(DeviceGraph G, MixedGraph 
                                                    const float* __restrict__ Q, float* __restrict__ d,
                                                    float* __restrict__ dinv, float* __restrict__ dF,
                                                    float* __restrict__ alpha, DeviceScalars* scal) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  reduce_tau_candidate(G, r, r < G.n ? row_edge_m(G, M, U, Q, d, dinv, dF, alpha, r) : INFINITY);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  reduce_tau_candidate(G, r, computes_row(G, r) ? row_edge_m(G, M, U, Q, d, dinv, dF, alpha, r) : INFINITY);
 }
 
 // Step 3: U^L_i = U_i + sum_j (2 tau d_ij/m_i)(Ubar_ij - U_i) with
@@ -583,9 +583,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_low_order_m(DeviceGraph G, StageC
                                                         double* __restrict__ UL, float* __restrict__ R,
                                                         double* __restrict__ bnd, DeviceScalars* scal, int tau_mode,
                                                         int accumulate_time) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  instance_books(G, r, tau_mode, C.cfl, accumulate_time, scal);
-  if (r < G.n) row_low_order_m(G, C, U, Uf, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  instance_books(G, t, tau_mode, C.cfl, accumulate_time, scal);
+  const int64_t r = row_start(G) + t;
+  if (computes_row(G, r)) row_low_order_m(G, C, U, Uf, Q, d, dinv, dF, alpha, UL, R, bnd, tau_mode, r);
 }
 
 // Step 4 in FP32: P_ij and the first limiter values.
@@ -641,8 +642,8 @@ __global__ void __launch_bounds__(kMaxBlock, 4) k_flux_limit_m(DeviceGraph G, Mi
                                                          const float* __restrict__ R, const double* __restrict__ bnd,
                                                          float* __restrict__ P, float* __restrict__ l,
                                                          const DeviceScalars* scal, int tau_mode) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_flux_limit_m(G, M, C, Uf, d, alpha, UL, R, bnd, P, l, tau_mode, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_flux_limit_m(G, M, C, Uf, d, alpha, UL, R, bnd, P, l, tau_mode, r);
 }
 
 // Limiter pass: U_next = U_cur + sum_j lambda_i min(l_ij, l_ji) P_ij (sum in
@@ -719,8 +720,8 @@ __global__ void __launch_bounds__(kMaxBlock, 4) k_limiter_pass_m(DeviceGraph G, 
                                                            double* __restrict__ Unext, float* __restrict__ P,
                                                            const float* __restrict__ lold, float* __restrict__ lnew,
                                                            const double* __restrict__ bnd) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_limiter_pass_m(G, M, C, Ucur, Unext, P, lold, lnew, bnd, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_limiter_pass_m(G, M, C, Ucur, Unext, P, lold, lnew, bnd, r);
 }
 
 // Last pass, boundary post-processing and the SSP-RK3 blend (FP64).
@@ -781,8 +782,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_final_m(DeviceGraph G, MixedGraph
                                                     const double* __restrict__ Un, double* __restrict__ Uout,
                                                     double* __restrict__ Ulim, DeviceScalars* scal, int blend,
                                                     int skip_write_on_error) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < G.n) row_final_m(G, M, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
+  const int64_t r = row_start(G) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (computes_row(G, r)) row_final_m(G, M, C, Ucur, P, l, Un, Uout, Ulim, scal, blend, skip_write_on_error, r);
 }
 
 struct PersistentStageMixed {
@@ -899,6 +900,43 @@ int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const Sta
   if (trace && B.Ulast)
     cudaMemcpyAsync(B.tUlim, B.Ulast, sizeof(double) * kFields * G.n, cudaMemcpyDeviceToDevice, s);
   return launches;
+}
+
+int launch_euler_phase_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B,
+                             const MixedBuffers& X, const StageConfig& C, const double* Uin, double* Uout,
+                             const double* Un, int blend, int tau_mode, bool accumulate_time,
+                             bool skip_write_on_error, int phase, cudaStream_t s, int block) {
+  const unsigned grid = (unsigned)((G.n + block - 1) / block);
+  const unsigned grid_own = own_row_grid(G, block);
+  const int passes = C.limiter_passes;
+  if (phase == 0) {
+    k_node_m<<<grid, block, 0, s>>>(G, Uin, X.Q, X.Uf, B.scal);
+    k_edge_m<<<grid_own, block, 0, s>>>(G, M, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.scal);
+    return 2;
+  }
+  if (phase == 1) {
+    k_low_order_m<<<grid_own, block, 0, s>>>(G, C, Uin, X.Uf, X.Q, X.d, X.dinv, X.P, X.alpha, B.UL, X.R, B.bnd,
+                                             B.scal, tau_mode, accumulate_time ? 1 : 0);
+    return 1;
+  }
+  if (phase == 2) {
+    k_flux_limit_m<<<grid_own, block, 0, s>>>(G, M, C, X.Uf, X.d, X.alpha, B.UL, X.R, B.bnd, X.P, X.l[0], B.scal,
+                                              tau_mode);
+    return 1;
+  }
+  auto state_after = [&](int p) -> double* { return p == 0 ? B.UL : B.Uw[(p - 1) & 1]; };
+  const int p = phase - 2;
+  if (p >= 1 && p < passes) {
+    k_limiter_pass_m<<<grid_own, block, 0, s>>>(G, M, C, state_after(p - 1), B.Uw[(p - 1) & 1], X.P,
+                                                X.l[(p - 1) & 1], X.l[p & 1], B.bnd);
+    return 1;
+  }
+  if (p == passes) {
+    k_final_m<<<grid_own, block, 0, s>>>(G, M, C, state_after(passes - 1), X.P, X.l[(passes - 1) & 1], Un, Uout,
+                                         B.Ulast, B.scal, blend, skip_write_on_error ? 1 : 0);
+    return 1;
+  }
+  return 0;
 }
 
 }  // namespace idp

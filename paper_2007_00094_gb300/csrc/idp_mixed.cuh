@@ -89,4 +89,14 @@ int launch_euler_step_mixed(const DeviceGraph& G, const MixedGraph& M, const Sta
                             int tau_mode, bool accumulate_time, bool skip_write_on_error, bool trace, cudaStream_t s,
                             Profiler* prof, int block = 128, GridBarrier* bar = nullptr);
 
+// The phases of launch_euler_phase (idp_stage.cuh) for the FP32-mixed stage,
+// whose Step 2 runs inside Step 1: phase 0 = Steps 0-2 (node quantities of
+// all rows, then d_ij, alpha_i and the CFL bound of the own rows), then
+// Step 3, Step 4, the limiter passes and Step 6 as there; alpha, R and l are
+// FP32 arrays of MixedBuffers.
+int launch_euler_phase_mixed(const DeviceGraph& G, const MixedGraph& M, const StageBuffers& B,
+                             const MixedBuffers& X, const StageConfig& C, const double* Uin, double* Uout,
+                             const double* Un, int blend, int tau_mode, bool accumulate_time,
+                             bool skip_write_on_error, int phase, cudaStream_t s, int block);
+
 }  // namespace idp

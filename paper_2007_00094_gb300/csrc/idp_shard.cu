@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -106,8 +107,9 @@ idp_status supload(idp_shards* sh, T** p, const std::vector<T>& v) {
 }
 
 // buf[c m + k] = X[c n + idx[k]] for comps fields of a node array
-__global__ void k_pack_nodes(const double* __restrict__ X, int64_t n, int comps, const int64_t* __restrict__ idx,
-                             int64_t m, double* __restrict__ buf) {
+template <typename T>
+__global__ void k_pack_nodes(const T* __restrict__ X, int64_t n, int comps, const int64_t* __restrict__ idx,
+                             int64_t m, T* __restrict__ buf) {
   const int64_t total = (int64_t)comps * m;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = t / m, k = t - c * m;
@@ -115,8 +117,9 @@ __global__ void k_pack_nodes(const double* __restrict__ X, int64_t n, int comps,
   }
 }
 
-__global__ void k_unpack_nodes(double* __restrict__ X, int64_t n, int comps, const int64_t* __restrict__ idx,
-                               int64_t m, const double* __restrict__ buf) {
+template <typename T>
+__global__ void k_unpack_nodes(T* __restrict__ X, int64_t n, int comps, const int64_t* __restrict__ idx, int64_t m,
+                               const T* __restrict__ buf) {
   const int64_t total = (int64_t)comps * m;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = t / m, k = t - c * m;
@@ -125,14 +128,16 @@ __global__ void k_unpack_nodes(double* __restrict__ X, int64_t n, int comps, con
 }
 
 // buf[k] = X[idx[k]] for a per-slot array, and back
-__global__ void k_pack_slots(const double* __restrict__ X, const int64_t* __restrict__ idx, int64_t m,
-                             double* __restrict__ buf) {
+template <typename T>
+__global__ void k_pack_slots(const T* __restrict__ X, const int64_t* __restrict__ idx, int64_t m,
+                             T* __restrict__ buf) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
     buf[k] = X[idx[k]];
 }
 
-__global__ void k_unpack_slots(double* __restrict__ X, const int64_t* __restrict__ idx, int64_t m,
-                               const double* __restrict__ buf) {
+template <typename T>
+__global__ void k_unpack_slots(T* __restrict__ X, const int64_t* __restrict__ idx, int64_t m,
+                               const T* __restrict__ buf) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
     X[idx[k]] = buf[k];
 }
@@ -154,23 +159,23 @@ unsigned grid_for(int64_t work) {
 // link k into its send buffer, unpack(k, buf) the receiver's scatter.  The
 // sender copies into the receiver's buffer of this exchange's parity once
 // the receiver has emptied it (two exchanges back), and the receiver waits
-// for the copy.
-template <typename Pack, typename Unpack, typename Values>
-int exchange(idp_shards* sh, Pack&& pack, Unpack&& unpack, Values&& values) {
+// for the copy.  bytes(k) is the size of link k's message.
+template <typename Pack, typename Unpack, typename Bytes>
+int exchange(idp_shards* sh, Pack&& pack, Unpack&& unpack, Bytes&& bytes) {
   const int par = (int)(sh->exchanges++ & 1);
   int launches = 0;
   for (idp_shards::Link& k : sh->links) {
-    const int64_t m = values(k);
-    if (m == 0) continue;
+    const size_t b = bytes(k);
+    if (b == 0) continue;
     cudaStream_t s = sh->streams[k.src];
     pack(k, s);
     cudaStreamWaitEvent(s, k.unpacked[par], 0);
-    cudaMemcpyAsync(k.recv[par], k.send, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(k.recv[par], k.send, b, cudaMemcpyDeviceToDevice, s);
     cudaEventRecord(k.copied, s);
     ++launches;
   }
   for (idp_shards::Link& k : sh->links) {
-    if (values(k) == 0) continue;
+    if (bytes(k) == 0) continue;
     cudaStream_t s = sh->streams[k.dst];
     cudaStreamWaitEvent(s, k.copied, 0);
     unpack(k, k.recv[par], s);
@@ -182,40 +187,43 @@ int exchange(idp_shards* sh, Pack&& pack, Unpack&& unpack, Values&& values) {
 
 // A node array of comps fields (stride n of each shard); field(s) gives
 // shard s's array.
-template <typename F>
+template <typename T, typename F>
 int exchange_nodes(idp_shards* sh, int comps, F&& field) {
   return exchange(
       sh,
       [&](const idp_shards::Link& k, cudaStream_t s) {
-        k_pack_nodes<<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.src), sh->ctx[k.src]->G.n, comps, k.sn, k.nn,
-                                                                 k.send);
+        k_pack_nodes<T><<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.src), sh->ctx[k.src]->G.n, comps, k.sn,
+                                                                    k.nn, reinterpret_cast<T*>(k.send));
       },
       [&](const idp_shards::Link& k, const double* buf, cudaStream_t s) {
-        k_unpack_nodes<<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.dst), sh->ctx[k.dst]->G.n, comps, k.dn, k.nn,
-                                                                   buf);
+        k_unpack_nodes<T><<<grid_for(comps * k.nn), kXBlock, 0, s>>>(field(k.dst), sh->ctx[k.dst]->G.n, comps, k.dn,
+                                                                      k.nn, reinterpret_cast<const T*>(buf));
       },
-      [&](const idp_shards::Link& k) { return (int64_t)comps * k.nn; });
+      [&](const idp_shards::Link& k) { return sizeof(T) * (size_t)comps * (size_t)k.nn; });
 }
 
 // A per-slot array.
-template <typename F>
+template <typename T, typename F>
 int exchange_slots(idp_shards* sh, F&& field) {
   return exchange(
       sh,
       [&](const idp_shards::Link& k, cudaStream_t s) {
-        k_pack_slots<<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.src), k.ss, k.ne, k.send);
+        k_pack_slots<T><<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.src), k.ss, k.ne, reinterpret_cast<T*>(k.send));
       },
       [&](const idp_shards::Link& k, const double* buf, cudaStream_t s) {
-        k_unpack_slots<<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.dst), k.ds, k.ne, buf);
+        k_unpack_slots<T><<<grid_for(k.ne), kXBlock, 0, s>>>(field(k.dst), k.ds, k.ne,
+                                                              reinterpret_cast<const T*>(buf));
       },
-      [](const idp_shards::Link& k) { return k.ne; });
+      [&](const idp_shards::Link& k) { return sizeof(T) * (size_t)k.ne; });
 }
 
 // One euler_step of every shard (the roles of U^n, the stage state and the
-// blend as in the unsharded SSP-RK3 step).
+// blend as in the unsharded SSP-RK3 step).  The FP32-mixed stage exchanges
+// its FP32 alpha, R and l.
 int sharded_stage(idp_shards* sh, int stage) {
   const int S = (int)sh->ctx.size();
   const idp::StageConfig& C0 = sh->ctx[0]->C;
+  const bool mixed = sh->ctx[0]->mixed;
   const int phases = idp::euler_phase_count(C0);
   const int passes = C0.limiter_passes;
   int launches = 0;
@@ -227,8 +235,13 @@ int sharded_stage(idp_shards* sh, int stage) {
       const double* Uin = stage == 0 ? B.U : B.Us;
       double* Uout = stage == 2 ? B.U : B.Us;
       const int blend = stage == 0 ? idp::kBlendNone : (stage == 1 ? idp::kBlendStage2 : idp::kBlendStage3);
-      launches += idp::launch_euler_phase(c->G, B, c->C, Uin, Uout, B.U, blend, stage == 0 ? 0 : 1, stage == 0,
-                                          stage == 2, ph, sh->streams[s], c->block);
+      if (mixed)
+        launches += idp::launch_euler_phase_mixed(c->G, c->MG, B, c->MB, c->C, Uin, Uout, B.U, blend,
+                                                  stage == 0 ? 0 : 1, stage == 0, stage == 2, ph, sh->streams[s],
+                                                  c->block);
+      else
+        launches += idp::launch_euler_phase(c->G, B, c->C, Uin, Uout, B.U, blend, stage == 0 ? 0 : 1, stage == 0,
+                                            stage == 2, ph, sh->streams[s], c->block);
     }
     if (S == 1) continue;
     if (ph == 0) {
@@ -242,13 +255,23 @@ int sharded_stage(idp_shards* sh, int stage) {
       cudaEventRecord(sh->ev_tau, sh->streams[0]);
       for (int s = 1; s < S; ++s) cudaStreamWaitEvent(sh->streams[s], sh->ev_tau, 0);
       ++launches;
-      launches += exchange_nodes(sh, 1, [&](int s) { return sh->ctx[s]->B.alpha; });
+      if (mixed)
+        launches += exchange_nodes<float>(sh, 1, [&](int s) { return sh->ctx[s]->MB.alpha; });
+      else
+        launches += exchange_nodes<double>(sh, 1, [&](int s) { return sh->ctx[s]->B.alpha; });
     } else if (ph == 1) {
-      launches += exchange_nodes(sh, 5, [&](int s) { return sh->ctx[s]->B.R; });
+      if (mixed)
+        launches += exchange_nodes<float>(sh, 5, [&](int s) { return sh->ctx[s]->MB.R; });
+      else
+        launches += exchange_nodes<double>(sh, 5, [&](int s) { return sh->ctx[s]->B.R; });
     } else if (ph < 2 + passes) {
-      launches += exchange_slots(sh, [&](int s) { return idp::phase_l_buffer(sh->ctx[s]->B, ph); });
+      if (mixed)
+        launches += exchange_slots<float>(sh, [&](int s) { return sh->ctx[s]->MB.l[(ph - 2) & 1]; });
+      else
+        launches += exchange_slots<double>(sh, [&](int s) { return idp::phase_l_buffer(sh->ctx[s]->B, ph); });
     } else {
-      launches += exchange_nodes(sh, 5, [&](int s) { return stage == 2 ? sh->ctx[s]->B.U : sh->ctx[s]->B.Us; });
+      launches +=
+          exchange_nodes<double>(sh, 5, [&](int s) { return stage == 2 ? sh->ctx[s]->B.U : sh->ctx[s]->B.Us; });
     }
   }
   return launches;
@@ -361,7 +384,9 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
   }
   // FP64 per-step kernels in the caller's row order; the bound relaxation
   // scales by the volume of the whole domain, which no shard sees
-  if (cfg.precision != IDP_PRECISION_FP64 || cfg.relax != 0 || cfg.renumber != 0) return IDP_ERR_ARG;
+  if ((cfg.precision != IDP_PRECISION_FP64 && cfg.precision != IDP_PRECISION_MIXED) || cfg.relax != 0 ||
+      cfg.renumber != 0)
+    return IDP_ERR_ARG;
   idp_shards* sh = new (std::nothrow) idp_shards;
   if (!sh) return IDP_ERR_OOM;
   sh->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -386,6 +411,13 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
         m_all[L.nodes[l]] = m;
       }
     }
+  }
+  // the FP32 copies of c_ij take exact zeros relative to the largest |c_ij|
+  // of the whole mesh, as an unsharded context does
+  double c_scale = 0.0;
+  for (int64_t e = 0; e < nnz; ++e) {
+    const double x = cij[e], y = cij[nnz + e], z = cij[2 * nnz + e];
+    c_scale = std::fmax(c_scale, std::sqrt(x * x + y * y + z * z));
   }
   idp_status st = IDP_OK;
   for (int s = 0; s < S && st == IDP_OK; ++s) {
@@ -420,6 +452,7 @@ idp_status idp_shards_create(const idp_config* cfg_in, void* cuda_stream, const 
     st = idp_create(&cfg, sh->streams[s], &c);
     if (st != IDP_OK) break;
     sh->ctx.push_back(c);
+    c->c_scale = c_scale;
     st = idp_upload_sparsity(c, nl, L.rowptr.data(), L.col.data(), lm.data(), lc.data(), lmi.data(), lbc.data(),
                              inflow_state);
     if (st != IDP_OK) {

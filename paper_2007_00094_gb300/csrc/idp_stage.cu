@@ -14,11 +14,6 @@ namespace {
 
 constexpr int kBlock = 128;  // state-check kernels
 
-// Rows of the per-step kernels of Steps 2-6: [row0, row1), launched from the
-// start of row0's slice so that a warp's rows share one slice.
-__device__ __forceinline__ int64_t row_start(const DeviceGraph& G) { return G.row0 & ~(int64_t)(kSlice - 1); }
-__device__ __forceinline__ bool computes_row(const DeviceGraph& G, int64_t r) { return r >= G.row0 && r < G.row1; }
-
 __device__ __forceinline__ int64_t slot_base(const DeviceGraph& G, int64_t r) {
   return (int64_t)G.slice_ptr[r >> 5] + (r & 31);
 }
@@ -830,10 +825,7 @@ int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageC
                        double* Uout, const double* Un, int blend, int tau_mode, bool accumulate_time,
                        bool skip_write_on_error, int phase, cudaStream_t s, int block) {
   const unsigned grid = (unsigned)((G.n + block - 1) / block);
-  // Steps 2-6 over rows [row0, row1) (the first block also keeps the
-  // instance books, which need at least n_inst threads)
-  const int64_t own = std::max<int64_t>(G.row1 - (G.row0 & ~(int64_t)(kSlice - 1)), G.n_inst);
-  const unsigned grid_own = (unsigned)((own + block - 1) / block);
+  const unsigned grid_own = own_row_grid(G, block);  // Steps 2-6
   const int passes = C.limiter_passes;
   if (phase == 0) {
     k_node<<<grid, block, 0, s>>>(G.n, Uin, B.node, B.scal);

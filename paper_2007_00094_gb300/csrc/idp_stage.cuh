@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "idp_device.cuh"
+#include "idp_internal.h"
 
 namespace idp {
 
@@ -55,6 +56,11 @@ struct DeviceGraph {
 };
 
 __device__ __forceinline__ int instance_of(const DeviceGraph& G, int64_t r) { return G.inst ? G.inst[r] : 0; }
+
+// Rows of the per-step kernels of Steps 2-6: [row0, row1), launched from the
+// start of row0's slice so that a warp's rows share one slice.
+__device__ __forceinline__ int64_t row_start(const DeviceGraph& G) { return G.row0 & ~(int64_t)(kSlice - 1); }
+__device__ __forceinline__ bool computes_row(const DeviceGraph& G, int64_t r) { return r >= G.row0 && r < G.row1; }
 
 // Device status bits latched by the kernels.
 enum : int {
@@ -290,6 +296,13 @@ int launch_euler_phase(const DeviceGraph& G, const StageBuffers& B, const StageC
                        bool skip_write_on_error, int phase, cudaStream_t s, int block);
 // The limiter-value buffer that phase 2 + p (p >= 0) writes.
 double* phase_l_buffer(const StageBuffers& B, int phase);
+// Own-row grid of Steps 2-6 ([row0, row1) from the start of row0's slice,
+// at least n_inst threads for the instance books).
+inline unsigned own_row_grid(const DeviceGraph& G, int block) {
+  int64_t own = G.row1 - (G.row0 & ~(int64_t)(kSlice - 1));
+  if (own < G.n_inst) own = G.n_inst;
+  return (unsigned)((own + block - 1) / block);
+}
 
 // Blocks of the persistent stage kernel that fit on the device at once.
 int persistent_grid_limit(int block, bool mixed);

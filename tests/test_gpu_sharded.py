@@ -25,11 +25,11 @@ def _sparsity(mesh):
     return dict(rowptr=rowptr, col=col, mij=mij, cij=cij, mi=mi, bc=mesh.bc, inflow=mesh.inflow)
 
 
-def _run_both(mesh, U, n_shards, steps, row_begin=None, mi=True):
+def _run_both(mesh, U, n_shards, steps, row_begin=None, mi=True, precision=0):
     from paper_2007_00094_gb300.idp import ShardedSolver, Solver
 
     sp = _sparsity(mesh)
-    ref = Solver(sparsity=sp)
+    ref = Solver(sparsity=sp, precision=precision)
     ref.init_state(U)
     ref.step(steps)
     ref.synchronize()
@@ -37,7 +37,7 @@ def _run_both(mesh, U, n_shards, steps, row_begin=None, mi=True):
     ref.close()
     if not mi:
         sp = dict(sp, mi=None)
-    sh = ShardedSolver(sp, n_shards=n_shards, row_begin=row_begin)
+    sh = ShardedSolver(sp, n_shards=n_shards, row_begin=row_begin, precision=precision)
     sh.init_state(U)
     sh.step(steps)
     sh.synchronize()
@@ -50,23 +50,39 @@ def _run_both(mesh, U, n_shards, steps, row_begin=None, mi=True):
 @pytest.mark.parametrize("name", ["vortex17", "ffs10", "wallbox_jitter", "sod_jitter", "ffs2d_10",
                                   "wallrect_jitter"])
 @pytest.mark.parametrize("n_shards", [2, 3])
-def test_sharded_bitwise_equals_unsharded(name, n_shards):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sharded_bitwise_equals_unsharded(name, n_shards, precision):
+    """FP64 and FP32-mixed (whose shards exchange FP32 alpha, R and l and use
+    the whole mesh's scale for the FP32 copies of c_ij)."""
     require_gpu()
     mesh, U = _mesh(name)
-    out, t, out_ref, t_ref, halo = _run_both(mesh, U, n_shards, steps=3)
+    out, t, out_ref, t_ref, halo = _run_both(mesh, U, n_shards, steps=3, precision=precision)
     assert halo[0] > 0 and halo[1] > 0
     assert t == t_ref, (t, t_ref)
     assert np.array_equal(out, out_ref), float(np.abs(out - out_ref).max())
 
 
-def test_sharded_uneven_ranges_and_row_sum_masses():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sharded_uneven_ranges_and_row_sum_masses(precision):
     require_gpu()
     mesh, U = _mesh("ffs10")
     n = mesh.n_nodes
     # four shards of unequal size, one of them a single slice; lumped masses
     # formed by the group as row sums of m_ij (no mi given)
     rb = [0, 37, 37 + 32, n // 2 + 5, n]
-    out, t, out_ref, t_ref, _ = _run_both(mesh, U, 4, steps=2, row_begin=rb, mi=False)
+    out, t, out_ref, t_ref, _ = _run_both(mesh, U, 4, steps=2, row_begin=rb, mi=False, precision=precision)
+    assert t == t_ref
+    assert np.array_equal(out, out_ref)
+
+
+def test_sharded_mixed_on_a_structured_grid_keeps_table_and_patterns():
+    """On a uniform grid the shards' FP32-mixed contexts still find the entry
+    table and row patterns (ghost rows add patterns of their own) and stay
+    bitwise equal to the unsharded stage."""
+    require_gpu()
+    mesh = W.sod_cube_mesh(24)
+    U = W.sod_state(mesh)
+    out, t, out_ref, t_ref, _ = _run_both(mesh, U, 3, steps=3, precision=1)
     assert t == t_ref
     assert np.array_equal(out, out_ref)
 
@@ -95,7 +111,7 @@ def test_sharded_rejects_unsupported_configs():
 
     mesh, _ = _mesh("tiny3")
     sp = _sparsity(mesh)
-    for kw in (dict(precision=1), dict(relax=1), dict(renumber=1)):
+    for kw in (dict(relax=1), dict(renumber=1), dict(precision=2)):
         with pytest.raises(IdpError):
             ShardedSolver(sp, n_shards=2, **kw)
 
