@@ -464,8 +464,9 @@ def pattern_q1_2d(stream, args):
 def pattern_renumber(stream, args):
     """Row order: the step channel (h = 1/m) with its nodes in the generator's
     lexicographic order, randomly shuffled (seeded) as given, and shuffled but
-    renumbered by the library (idp_config.renumber, reverse Cuthill-McKee);
-    FP64 and FP32-mixed ms per SSP-RK3 step."""
+    renumbered by the library (idp_config.renumber: 1 reverse Cuthill-McKee,
+    2 Morton order of the node coordinates, also from the lexicographic
+    order); FP64 and FP32-mixed ms per SSP-RK3 step."""
     import numpy as np
 
     from paper_2007_00094_gb300 import workloads as W
@@ -485,7 +486,8 @@ def pattern_renumber(stream, args):
     for name, prec in (("fp64", 0), ("fp32_mixed", 1)):
         row = {}
         for label, m, u, ren in (("lexicographic", mesh, U0, 0), ("shuffled", shuf, U_shuf, 0),
-                                 ("shuffled_renumbered", shuf, U_shuf, 1)):
+                                 ("shuffled_renumbered", shuf, U_shuf, 1), ("shuffled_morton", shuf, U_shuf, 2),
+                                 ("lexicographic_morton", mesh, U0, 2)):
             s = Solver(m, stream=stream, precision=prec, renumber=ren)
             s.init_state(u)
             row[label] = _time_steps(s, stream, args.pattern_steps, args.warmup, profile=False)[0]

@@ -77,12 +77,19 @@ typedef struct {
                                for the traces of one checkpoint segment, so that idp_adjoint_backward
                                evaluates each stage forward once instead of twice; 0: the traced
                                stages are recomputed.  Gradients are bitwise the same either way. */
-  int renumber;             /* 1: the library orders its rows by reverse Cuthill-McKee over the
-                               stencil graph (locality of the neighbour gathers for meshes whose nodes
-                               come in an arbitrary order); 0 (default): the caller's node order.
-                               States, fields, gradients, matrices and instance offsets stay in the
-                               caller's numbering at this interface, and results are bitwise the same
-                               either way (every row sum keeps the caller's column order). */
+  int renumber;             /* row order of the library, for the locality of the neighbour gathers on
+                               meshes whose nodes come in an arbitrary order.  0 (default): the
+                               caller's node order; 1: reverse Cuthill-McKee over the stencil graph,
+                               every row sum in the caller's column order, so results are bitwise
+                               those of 0; 2: Morton (Z-order) of the node coordinates, so that the 32
+                               rows of a slice are a compact block of space, and every row's entries
+                               ordered by their offset in the reference cell, so that a warp's gathers
+                               at one slot are neighbours at one offset whatever order the caller's ids
+                               come in: results equal those of 0 up to the rounding of the reordered
+                               sums (mesh uploads only: with
+                               idp_upload_sparsity, which has no coordinates, IDP_ERR_ARG).  States,
+                               fields, gradients, matrices and instance offsets stay in the caller's
+                               numbering at this interface. */
 } idp_config;
 
 /* Fills the defaults: gamma 1.4, cfl 0.5, 2 limiter passes, 2 Newton steps,
@@ -339,7 +346,9 @@ idp_status idp_autotune(idp_ctx* ctx, int steps, int* block_size, int* use_graph
  * adjoint differentiates the stage as computed (Alg. 1 with the limiter of
  * Alg. 2/3 and the bound of Sec. 3.7, Newton steps included); at
  * non-smooth points it takes the branch the forward pass took:
- * min(l_ij, l_ji) and every min/max bound go to the first extremal entry,
+ * min(l_ij, l_ji) and every min/max bound go to the first extremal entry
+ * (in the row's column order: the caller's, or the cell-offset order of
+ * idp_config.renumber = 2),
  * tau_n = c_cfl min_i m_i/(-2 d_ii) (Sec. 3.3) to the first row attaining
  * the minimum.  Supported for precision IDP_PRECISION_FP64,
  * limiter_passes = 2 and a single instance, else IDP_ERR_ARG.  The

@@ -635,7 +635,7 @@ idp_status upload_mesh(idp_ctx* ctx, int dim, int64_t n_nodes, int64_t n_cells, 
 // a mesh upload that follows the matrices).
 idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
   idp_status st;
-  std::string msg = idp::build_sell(ctx->M, ctx->L, ctx->cfg.renumber != 0);
+  std::string msg = idp::build_sell(ctx->M, ctx->L, ctx->cfg.renumber);
   if (!msg.empty()) return fail(ctx, IDP_ERR_ARG, msg);
   for (int f = 0; f < 5; ++f) ctx->C.inflow[f] = inflow_state ? inflow_state[f] : 0.0;
 

@@ -27,6 +27,10 @@ struct HostMatrices {
   bool lumped_given = false;           // mi is the caller's (else m_i = sum_j m_ij)
   std::vector<uint8_t> boundary_pair;  // entry (i,j) lies on a common boundary face
   std::vector<int32_t> bc;
+  std::vector<double> xyz;  // 3n node coordinates (mesh uploads; empty for pre-assembled matrices)
+  // per entry (i, j): offset of j from i in the reference cell of the first
+  // cell holding both, (dz+1) 9 + (dy+1) 3 + (dx+1) (mesh uploads; else empty)
+  std::vector<uint8_t> offset;
 };
 
 // Sparsity pattern and exact Q1 matrices of Sec. 3.1 eq. (matrices); returns
@@ -55,7 +59,11 @@ struct SellLayout {
   std::vector<int64_t> slot_of_entry;   // caller CSR entry -> slot
 };
 
-// renumber: rows in reverse Cuthill-McKee order (else the caller's order).
-std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber = false);
+// Row order: renumber 0 = the caller's order, 1 = reverse Cuthill-McKee over
+// the stencil graph (each row's entries keep the caller's column order), 2 =
+// Morton (Z-order) of the node coordinates M.xyz (an error without them),
+// each row's entries ordered by their cell offset M.offset, then library
+// column.
+std::string build_sell(const HostMatrices& M, SellLayout& L, int renumber = 0);
 
 }  // namespace idp

@@ -137,6 +137,18 @@ std::string assemble_impl(int64_t n, int64_t nc, const int64_t* cells, const dou
   for (int64_t i = 0; i < n; ++i)
     if (inc_ptr[i + 1] == inc_ptr[i]) return "a node belongs to no cell";
 
+  // node coordinates, as the first cell around the node sees them (a node on
+  // a periodic seam has one position per side; either serves for ordering)
+  out.xyz.assign(3 * (size_t)n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t c = inc[inc_ptr[i]];
+    for (int v = 0; v < NV; ++v)
+      if (cells[NV * c + v] == i) {
+        for (int d = 0; d < D; ++d) out.xyz[3 * i + d] = xyz[(NV * c + v) * D + d];
+        break;
+      }
+  }
+
   // stencil I(i): union of the vertices of the cells around node i (sorted)
   out.n = n;
   out.rowptr.assign(n + 1, 0);
@@ -159,6 +171,7 @@ std::string assemble_impl(int64_t n, int64_t nc, const int64_t* cells, const dou
   out.mij.assign(nnz, 0.0);
   for (int d = 0; d < 3; ++d) out.cij[d].assign(nnz, 0.0);
   out.mi.assign(n, 0.0);
+  out.offset.assign(nnz, 0xff);
   auto find = [&](int64_t i, int64_t j) -> int64_t {
     const int64_t* b = out.col.data() + out.rowptr[i];
     const int64_t* e = out.col.data() + out.rowptr[i + 1];
@@ -192,6 +205,12 @@ std::string assemble_impl(int64_t n, int64_t nc, const int64_t* cells, const dou
           const int64_t k = find(vn[a], vn[b]);
           out.mij[k] += L.M[a][b];
           for (int d = 0; d < 3; ++d) out.cij[d][k] += L.C[d][a][b];
+          if (out.offset[k] == 0xff) {
+            // reference-corner offset of vertex b from vertex a (v = x + 2y + 4z bits)
+            const int dx = (b & 1) - (a & 1), dy = ((b >> 1) & 1) - ((a >> 1) & 1),
+                      dz = ((b >> 2) & 1) - ((a >> 2) & 1);
+            out.offset[k] = (uint8_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+          }
         }
       }
     }
@@ -321,13 +340,61 @@ std::vector<int64_t> rcm_order(const HostMatrices& M) {
   return order;
 }
 
-std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
+// Morton (Z-order) of the node coordinates: each coordinate scaled by the
+// largest extent of the bounding box to 21 bits, the bits interleaved (x
+// lowest), rows sorted by key and then by caller id.  Consecutive rows, and
+// so the 32 rows of a slice, are nodes of a compact block of space (4 x 4 x 2
+// on a uniform grid), whose stencils overlap; build_sell also orders each
+// row's entries by their offset in the reference cell, whatever order the
+// caller's ids give them.
+std::vector<int64_t> morton_order(const HostMatrices& M) {
+  const int64_t n = M.n;
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = INFINITY;
+    hi[d] = -INFINITY;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], M.xyz[3 * i + d]);
+      hi[d] = std::max(hi[d], M.xyz[3 * i + d]);
+    }
+  const double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]});
+  const double s = ext > 0.0 ? (double)((1 << 21) - 1) / ext : 0.0;
+  auto spread = [](uint64_t v) {  // 21 bits -> every third bit
+    v &= 0x1fffffull;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+  };
+  std::vector<std::pair<uint64_t, int64_t>> key(n);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t k = 0;
+    for (int d = 0; d < 3; ++d) {
+      double q = (M.xyz[3 * i + d] - lo[d]) * s;
+      q = std::min(std::max(q, 0.0), (double)((1 << 21) - 1));
+      k |= spread((uint64_t)q) << d;
+    }
+    key[i] = {k, i};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int64_t> order(n);
+  for (int64_t r = 0; r < n; ++r) order[r] = key[r].second;
+  return order;
+}
+
+std::string build_sell(const HostMatrices& M, SellLayout& L, int renumber) {
   const int64_t n = M.n;
   L.n = n;
   L.perm.resize(n);
   L.iperm.resize(n);
-  if (renumber) {
-    L.iperm = rcm_order(M);
+  if (renumber == 2 && (M.xyz.size() != 3 * (size_t)n || M.offset.size() != M.col.size()))
+    return "Morton row order needs node coordinates and cell offsets (a mesh upload)";
+  if (renumber == 1 || renumber == 2) {
+    L.iperm = renumber == 1 ? rcm_order(M) : morton_order(M);
     for (int64_t r = 0; r < n; ++r) L.perm[L.iperm[r]] = r;
   } else {
     for (int64_t i = 0; i < n; ++i) L.perm[i] = L.iperm[i] = i;  // caller order keeps mesh locality
@@ -365,6 +432,7 @@ std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
   L.bc.assign(n, 0);
   L.slot_of_entry.assign(M.rowptr[n], -1);
   auto slot = [&](int64_t r, int64_t k) -> int64_t { return L.slice_ptr[r / kSlice] + k * kSlice + (r % kSlice); };
+  std::vector<int64_t> ord;
   for (int64_t r = 0; r < n; ++r) {
     const int64_t i = L.iperm[r];
     const int64_t len = M.rowptr[i + 1] - M.rowptr[i];
@@ -385,8 +453,19 @@ std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
       L.col[p] = (int32_t)r;
       L.tpos[p] = (int32_t)p;
     }
+    // the row's entries in the caller's column order, or (Morton order) by
+    // their offset in the reference cell, then library column: the lanes of
+    // a warp then gather, at each slot, the neighbours at one offset, as in a
+    // lexicographic grid order
+    ord.resize(len);
+    for (int64_t k = 0; k < len; ++k) ord[k] = M.rowptr[i] + k;
+    if (renumber == 2)
+      std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        const int oa = M.offset[a], ob = M.offset[b];
+        return oa != ob ? oa < ob : L.perm[M.col[a]] < L.perm[M.col[b]];
+      });
     for (int64_t k = 0; k < len; ++k) {
-      const int64_t e = M.rowptr[i] + k;
+      const int64_t e = ord[k];
       const int64_t p = slot(r, k);
       const int64_t j = L.perm[M.col[e]];
       L.slot_of_entry[e] = p;
@@ -405,9 +484,11 @@ std::string build_sell(const HostMatrices& M, SellLayout& L, bool renumber) {
       L.csz[r] += L.cz[p];
       uint8_t f = 0;
       if (j == r) f |= kEntryDiag;
-      // the row of the larger caller id evaluates the pair's wavespeed, so the
-      // orientation does not depend on the row order
-      if (M.col[e] > i) f |= kEntryUpper;
+      // the row of the smaller caller id evaluates the pair's wavespeed, so the
+      // orientation does not depend on the row order; in Morton order the row
+      // from which the other lies at a positive cell offset ((dz, dy, dx) > 0
+      // lexicographically), so that the lanes of a warp agree at each slot
+      if (renumber == 2 ? M.offset[e] > 13 : M.col[e] > i) f |= kEntryUpper;
       L.flags[p] = f;
     }
   }

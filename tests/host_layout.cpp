@@ -14,7 +14,7 @@ extern "C" int host_layout(int dim, int64_t n, int64_t nc, const int64_t* cells,
   if (!msg.empty()) return 1;
   M.bc.assign(n, 0);
   idp::SellLayout L;
-  if (!idp::build_sell(M, L, renumber != 0).empty()) return 2;
+  if (!idp::build_sell(M, L, renumber).empty()) return 2;
   int64_t bad_perm = 0, bad_tpos = 0, bad_upper = 0, bad_diag = 0, bad_col = 0, bad_skew = 0, bad_map = 0;
   int64_t bandwidth = 0;
   for (int64_t i = 0; i < n; ++i) {
@@ -43,9 +43,12 @@ extern "C" int host_layout(int dim, int64_t n, int64_t nc, const int64_t* cells,
         ++diag;
         if (!(L.flags[p] & idp::kEntryDiag) || (L.flags[p] & idp::kEntryUpper)) ++bad_diag;
       } else {
-        // exactly one orientation of a pair is the upper one: the smaller caller id's row
+        // exactly one orientation of a pair is the upper one: the smaller caller
+        // id's row (Morton order: the row from which the other lies at a
+        // positive cell offset)
         const bool up = L.flags[p] & idp::kEntryUpper, up_t = L.flags[pt] & idp::kEntryUpper;
-        if (up == up_t || up != (j > i)) ++bad_upper;
+        const bool want = renumber == 2 ? M.offset[e] > 13 : j > i;
+        if (up == up_t || up != want) ++bad_upper;
         const bool sk = L.flags[p] & idp::kEntrySkew, sk_t = L.flags[pt] & idp::kEntrySkew;
         if (sk != sk_t) ++bad_skew;
       }

@@ -1,10 +1,12 @@
-"""Row renumbering (idp_config.renumber, reverse Cuthill-McKee): on meshes
-whose nodes come in a shuffled order, the library's results in the caller's
-numbering are bitwise those without renumbering (every row sum keeps the
-caller's column order; the wavespeed of a pair is evaluated by the row of
-the smaller caller id either way), for the FP64 and FP32-mixed stages,
-batches, intermediate fields and the adjoint; and within the parity bar of
-the oracle."""
+"""Row renumbering (idp_config.renumber) on meshes whose nodes come in a
+shuffled order.  Reverse Cuthill-McKee rows (renumber = 1): the library's
+results in the caller's numbering are bitwise those without renumbering
+(every row sum keeps the caller's column order; the wavespeed of a pair is
+evaluated by the row of the smaller caller id either way), for the FP64 and
+FP32-mixed stages, batches, intermediate fields and the adjoint.  Morton rows
+with the library's column order (renumber = 2) reorder the row sums: within
+the parity bar of the FP64 oracle, and in the FP32-mixed stage within FP32
+rounding of the caller-order run."""
 import numpy as np
 import pytest
 
@@ -73,14 +75,46 @@ def test_renumbered_rows_give_bitwise_the_same_result(name, precision):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_renumbered_shuffled_mesh_matches_oracle(name, n_threads):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_morton_rows_agree_within_rounding(name, precision):
+    """Morton rows, library column order: the same stage with its row sums in
+    another order.  FP64: 1e-12 relative per field in the 2-norm after 3 SSP-RK3
+    steps (the parity bar).  FP32-mixed: 5e-4 in the per-field L1 norm, the
+    bar the mixed stage meets against the FP64 oracle on these jittered meshes
+    (FP32 rounding of the reordered sums moves limiter decisions on the
+    discontinuous data, as FP32 rounding does against FP64)."""
+    from gpu_common import rel_field_err_l2
+
+    mesh, U = CASES[name]
+    out = {}
+    for renumber in (0, 2):
+        s = _solver(mesh, precision=precision, renumber=renumber)
+        s.init_state(U)
+        s.step(3)
+        s.synchronize()
+        out[renumber] = (s.get_state(), s.time()[0])
+        s.close()
+    a, b = out[2][0], out[0][0]
+    if precision == 0:
+        assert rel_field_err_l2(a, b).max() <= 1e-12
+        assert abs(out[2][1] - out[0][1]) <= 1e-13 * out[0][1]
+    else:
+        scale = np.abs(b).max(axis=1)
+        scale = np.where(scale > 1e-12 * scale.max(), scale, scale.max())
+        assert (np.abs(a - b).mean(axis=1) / scale).max() <= 5e-4
+        assert abs(out[2][1] - out[0][1]) <= 1e-5 * out[0][1]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("renumber", [1, 2])
+def test_renumbered_shuffled_mesh_matches_oracle(name, renumber, n_threads):
     mesh, U = CASES[name]
     om = O.assemble(mesh)
     ref = U
     for _ in range(2):
         ref, _, st = O.ssprk3_step(om, ref, O.default_params(n_threads=n_threads))
         assert st == 0
-    s = _solver(mesh, renumber=1)
+    s = _solver(mesh, renumber=renumber)
     s.init_state(U)
     s.step(2)
     s.synchronize()
@@ -120,3 +154,20 @@ def test_renumbered_batch_and_adjoint_are_bitwise_the_same():
         s.adjoint_record(2, checkpoint_every=1)
         grads.append(s.adjoint_backward(w))
     np.testing.assert_array_equal(grads[0], grads[1])
+    # (Morton rows order each row's entries differently, and the bounds'
+    # derivative goes to the first extremal entry of that order at a tie:
+    # another valid branch, so no comparison with the caller-order gradient.)
+
+
+def test_morton_order_needs_coordinates():
+    """Pre-assembled matrices carry no node coordinates: renumber = 2 is an
+    argument error there, and the context reports it."""
+    from paper_2007_00094_gb300.idp import IdpError, Solver
+
+    mesh, _ = CASES["ffs10"]
+    s = _solver(mesh)
+    rowptr, col, mij, cij, mi = s.matrices()
+    s.close()
+    with pytest.raises(IdpError):
+        Solver(sparsity=dict(rowptr=rowptr, col=col, mij=mij, cij=cij, mi=mi, bc=mesh.bc, inflow=mesh.inflow),
+               renumber=2)

@@ -67,7 +67,7 @@ MESHES = {
 
 
 @pytest.mark.parametrize("name", sorted(MESHES))
-@pytest.mark.parametrize("renumber", [0, 1])
+@pytest.mark.parametrize("renumber", [0, 1, 2])
 def test_layout_invariants(harness, name, renumber):
     mesh = _shuffle(MESHES[name](), 7) if renumber else MESHES[name]()
     perm, s = _layout(harness, mesh, renumber)
@@ -87,3 +87,43 @@ def test_renumbering_reduces_the_bandwidth_of_a_shuffled_mesh(harness, name):
     _, s_rcm = _layout(harness, shuffled, 1)
     assert s_shuf["bandwidth"] > 0.8 * base.n_nodes  # a shuffle spreads neighbours over the whole range
     assert s_rcm["bandwidth"] <= 1.5 * s_base["bandwidth"]  # RCM brings it back to the structured order's scale
+
+
+def _slice_spans(mesh, perm):
+    """Mean number of distinct stencil nodes that the 32 rows of a slice
+    touch (their gathers), for a row order perm (caller node -> row)."""
+    import oracle as O
+
+    om = O.assemble(mesh)
+    rows_of = np.argsort(perm)  # caller node of each row
+    spans = []
+    for s0 in range(0, mesh.n_nodes - 31, 32):
+        nodes = rows_of[s0:s0 + 32]
+        cols = np.concatenate([om.col[om.rowptr[i]:om.rowptr[i + 1]] for i in nodes])
+        spans.append(len(np.unique(cols)))
+    return float(np.mean(spans))
+
+
+def test_morton_order_depends_on_coordinates_only(harness):
+    """renumber = 2 orders rows by the Morton key of the node coordinates: a
+    shuffled copy of a mesh gets the same sequence of node positions."""
+    base = MESHES["ffs10"]()
+    shuf = _shuffle(base, 3)
+    pb, _ = _layout(harness, base, 2)
+    ps, _ = _layout(harness, shuf, 2)
+    xb = np.empty_like(base.x)
+    xb[pb] = base.x
+    xs = np.empty_like(shuf.x)
+    xs[ps] = shuf.x
+    np.testing.assert_array_equal(xb, xs)
+
+
+def test_morton_slices_are_compact_blocks(harness):
+    """On a uniform box the 32 rows of a Morton slice are a 4 x 4 x 2 block:
+    their stencils touch 6 x 6 x 4 = 144 nodes, where 32 consecutive rows of
+    the lexicographic order (two x lines of 16) touch 18 x 4 x 3 = 216."""
+    box = W.box_mesh((16, 16, 16), periodic=(False, False, False))
+    p0, _ = _layout(harness, box, 0)
+    p2, _ = _layout(harness, box, 2)
+    lex, mor = _slice_spans(box, p0), _slice_spans(box, p2)
+    assert mor < 0.8 * lex, (mor, lex)
