@@ -4,7 +4,9 @@ configuration `bench.py` times (default schedule on one stream).
 * 3D step channel, h = 1/120 (2,242,909 nodes, 59,373,973 entries), FP64: one
   euler_step (traced) and one SSP-RK3 step against the oracle on every node,
   from a seeded state with an oblique Riemann jump and smooth density
-  perturbations (the inflow state alone would leave most rows in free stream).
+  perturbations (the inflow state alone would leave most rows in free stream);
+  the sharded stage (4 shards) bitwise against the unsharded one, FP64 and
+  FP32-mixed.
 * 128^3 Sod cube, FP32-mixed: two SSP-RK3 steps against the oracle, per-field
   L1 error as in the small cases, invariants.
 * 256 uneven Riemann cubes (8.87 M nodes), persistent one-launch-per-stage
@@ -79,6 +81,34 @@ def test_full_size_channel_stage_parity(channel, n_threads):
     assert rel_field_err(out, ref).max() <= 1e-12
     assert rel_field_err_l2(out, ref).max() <= 1e-12
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_channel_sharded_bitwise(channel, precision):
+    """The sharded stage (4 row ranges with one ghost layer, halo exchanges,
+    one stream per shard) at the benchmark size: two SSP-RK3 steps bitwise
+    those of the unsharded stage on the same matrices, in both precisions."""
+    from paper_2007_00094_gb300.idp import ShardedSolver, Solver
+
+    mesh, _, U = channel
+    s = _solver(mesh)
+    rowptr, col, mij, cij, mi = s.matrices()
+    s.close()
+    sp = dict(rowptr=rowptr, col=col, mij=mij, cij=cij, mi=mi, bc=mesh.bc, inflow=mesh.inflow)
+    ref = Solver(sparsity=sp, precision=precision)
+    ref.init_state(U)
+    ref.step(2)
+    ref.synchronize()
+    want, t_want = ref.get_state(), ref.time()
+    ref.close()
+    sh = ShardedSolver(sp, n_shards=4, precision=precision)
+    sh.init_state(U)
+    sh.step(2)
+    sh.synchronize()
+    got, t_got = sh.get_state(), sh.time()
+    sh.close()
+    assert t_got == t_want
+    assert np.array_equal(got, want)
 
 
 def test_full_size_channel_rk3_parity_and_invariants(channel, n_threads):
