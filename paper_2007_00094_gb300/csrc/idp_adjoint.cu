@@ -698,7 +698,9 @@ __global__ void __launch_bounds__(kB) ka_diag(DeviceGraph G, StageConfig C, cons
 
 // Step 1 reverse: alpha_i (Sec. 3.8), the flux differences, the wavespeed
 // bound d_ij of the edges this row owns, and phi(U_i) of the bounds.
-__global__ void __launch_bounds__(kB) ka_edge(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
+// three blocks per SM: 168 registers (32 bytes spilled) instead of 180 at two
+// blocks; 50 % more warps to hide its gathers (2.96 -> 2.83 ms at 64^3)
+__global__ void __launch_bounds__(kB, 3) ka_edge(DeviceGraph G, const double* __restrict__ U, const double* __restrict__ Q,
                                               const double* __restrict__ ab, AdjointBuffers A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= G.n) return;
