@@ -1,6 +1,9 @@
-"""The multi-rank (N > 1) path of bench.py on CPU: world_size 2 over gloo.
-Each rank advances its own replica (no data-path collective); the whole-job
-rate is all ranks' units over the slowest rank's time."""
+"""Multi-rank paths on CPU, world_size 2 over gloo: bench.py's N > 1 run,
+where each rank advances its own replica (no data-path collective) and the
+whole-job rate is all ranks' units over the slowest rank's time; and the
+sharded stage's halo exchange between ranks (shard.HaloExchange over a
+ShardPlan: ghosts receive their owners' node and entry values, tau is the
+minimum over ranks)."""
 import os
 import socket
 import sys
