@@ -61,8 +61,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # after three warm-up steps (profiles/ holds the launch lists).
 NCU_TRAFFIC_BYTES = {"node": 0.225e9, "edge": 5.137e9, "diag": 4.469e9, "low_order": 4.073e9,
                      "flux_limit": 4.360e9, "limiter_pass": 8.011e9, "final": 3.698e9}
-NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.199e9, "flux_limit": 1.819e9,
-                           "limiter_pass": 3.617e9, "final": 1.606e9}
+NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.200e9, "flux_limit": 1.820e9,
+                           "limiter_pass": 3.615e9, "final": 1.607e9}
 
 
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
