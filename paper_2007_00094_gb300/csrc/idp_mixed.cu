@@ -312,6 +312,10 @@ __device__ __forceinline__ float limiter_mixed(const double* Ug, int64_t n, int6
   if (rhoP > A.gap_max && rhoP != 0.0f) tR = fabsf(A.gap_max) / fabsf(rhoP) * (1.0f - 2.384185791015625e-7f);
   if (tR * rhoP < A.gap_min && rhoP != 0.0f) tR = fabsf(A.gap_min) / fabsf(rhoP) * (1.0f - 2.384185791015625e-7f);
   tR = fminf(fmaxf(tR, 0.0f), 1.0f);
+  // t_R = 0 (a density bound that U sits on, e.g. collapsed bounds in a
+  // constant region, and rho(P) pushing past it): t_L stays in [0, t_R], so
+  // the line search can only return 0
+  if (tR == 0.0f) return 0.0f;
   float tL = 0.0f;
   const PsiLine L = make_line(A, P);
   float psiL = 0.0f, dpsiL = 0.0f, psiAtL, feL = 0.0f, qL = 0.0f;
