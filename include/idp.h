@@ -323,7 +323,8 @@ idp_status idp_get_instance_times(idp_ctx* ctx, double* t, double* last_tau);
  * are, Fig. 2).  A barrier wait is bounded by idp_config.barrier_spin_limit
  * polls; one that runs out ends the launch and latches IDP_ERR_TIMEOUT.
  * Traced and profiled stages always take the per-step kernels.  Results do
- * not depend on the schedule. */
+ * not depend on the schedule.  A new context uses block 64, per-step kernels
+ * and no graph. */
 idp_status idp_set_schedule(idp_ctx* ctx, int block_size, int use_graph, int persistent);
 /* Self-test of the persistent schedule's grid barrier: a cooperative launch
  * of `blocks` blocks (64 threads) that pass `rounds` barriers, each wait

@@ -46,7 +46,7 @@ struct idp_ctx {
   // per-instance device state (one instance unless idp_set_instances)
   std::vector<void*> inst_allocs;
   // schedule: block size of the stage kernels and CUDA-graph replay of idp_step
-  int block = 128;
+  int block = 64;  // measured fastest of 64, 128, 256 on the benchmark workloads
   bool use_graph = false;
   bool persistent = false;            // one cooperative launch per euler_step
   idp::GridBarrier* bar = nullptr;   // its grid barrier (device)
