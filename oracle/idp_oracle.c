@@ -21,8 +21,10 @@
  * temporal convergence of eq. (ssprk3), and the Psi margin of Reading A27
  * (it changes only limiter calls in which some Psi lay within the margin,
  * and it keeps rounding-level input perturbations from flipping limiter
- * decisions).  Parity unpinned: the lower bound of the limiter's t (it
- * depends on the Newton settings of Alg. 2, which the paper leaves open).
+ * decisions).  The limiter's t at the default Newton settings: the exact
+ * root of Psi where Psi is a quadratic in t (rho(P) = 0: Alg. 3's step is then
+ * exact, checked against the quadratic formula), admissible and below the
+ * bisection root otherwise, converging to it as the Newton steps grow.
  */
 #include "idp_oracle.h"
 

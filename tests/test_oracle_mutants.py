@@ -30,11 +30,15 @@ MUTANTS = {
     "rk3_stage2_weights": ("U2[q] = 0.75 * U[q] + 0.25 * E[q];", "U2[q] = 0.5 * U[q] + 0.5 * E[q];"),
     # the Psi margin applied with the wrong sign (a stricter test than Psi >= 0)
     "psi_margin_sign": ("const int ok = psi >= -margin * scale;", "const int ok = psi >= margin * scale;"),
+    # a wrong factor in the discriminant of Alg. 3's quadratic step
+    "newton_discriminant": ("double LamL = dPsiL * dPsiL - 4.0 * PsiL * d112;",
+                            "double LamL = dPsiL * dPsiL - 2.0 * PsiL * d112;"),
 }
 
 # fast pins first (a mutant run stops at its first failing pin); the
 # convergence pin last
 PINS = ["tests/test_oracle_margin.py", "tests/test_oracle_stage.py::test_ssprk3_temporal_order",
+        "tests/test_oracle_pointwise.py::test_limiter_is_exact_where_psi_is_quadratic",
         "tests/test_oracle_symmetry.py", "tests/test_oracle_matrices.py",
         "tests/test_oracle_2d.py::test_uniform_periodic_closed_forms_2d",
         "tests/test_oracle_2d.py::test_identities_any_quad_mesh",

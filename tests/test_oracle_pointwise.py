@@ -171,3 +171,35 @@ def test_limiter_newton_converges_with_more_steps():
     assert all(a >= b for a, b in zip(means, means[1:]))
     assert np.max(gaps[2]) < 1e-2
     assert np.max(gaps[8]) < 1e-12
+
+
+@pytest.mark.parametrize("newton_max", [1, 2])
+def test_limiter_is_exact_where_psi_is_quadratic(newton_max):
+    """With rho(P) = 0 the density is constant along U + tP, so
+    Psi(t) = rho eps(U + tP) - phi_min rho^(gamma+1) is the quadratic
+    c + b t + a t^2 with a = -|P_m|^2/2, b = rho P_E - m.P_m, c = Psi(0).
+    Alg. 3's step solves the quadratic through the bracket's values, slopes and
+    second divided differences, which is Psi itself here: at the default Newton
+    settings the limiter must return the positive root
+    t* = (b + sqrt(b^2 - 4ac)) / (-2a), from the quadratic formula, whenever
+    Psi(0) > 0 > Psi(1).  (The Psi margin of Reading A27 moves t by far less
+    than the tolerance.)"""
+    rng = np.random.default_rng(23 + newton_max)
+    prm = O.default_params(newton_max=newton_max)
+    n = 0
+    for _ in range(2000):
+        U = _state(rng.uniform(0.2, 3), rng.uniform(-2, 2, 3), rng.uniform(0.2, 5))
+        rho, m = U[0], U[1:4]
+        pmin = specific_entropy(U) * rng.uniform(0.3, 0.999)
+        P = rng.normal(size=5) * np.abs(U) * rng.choice([0.1, 0.5, 2.0])
+        P[0] = 0.0
+        a = -0.5 * float(P[1:4] @ P[1:4])
+        b = rho * P[4] - float(m @ P[1:4])
+        c = rho_eps(U) - pmin * rho ** 2.4
+        if not (c > 0.0 and a + b + c < 0.0):
+            continue  # the root must lie inside (0, 1)
+        tstar = (b + np.sqrt(b * b - 4.0 * a * c)) / (-2.0 * a)
+        t = O.limiter(U, P, 0.0, 1e9, pmin, prm)
+        assert abs(t - tstar) <= 1e-9 * tstar, (t, tstar)
+        n += 1
+    assert n > 500
