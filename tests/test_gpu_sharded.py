@@ -127,3 +127,18 @@ def test_sharded_rejects_non_admissible_state():
     with pytest.raises(IdpError):
         sh.init_state(Ub)
     sh.close()
+
+
+@pytest.mark.parametrize("n_shards", [1, 2, 3, 5])
+def test_sharded_degenerate_partitions(n_shards):
+    """Edge cases of the partition: one shard (no links: the plain stage in
+    phases), and the 3^3 periodic vortex, where every node neighbours every
+    other through the periodic seams, so each shard holds nearly the whole
+    mesh as ghosts and exchanges with every other shard."""
+    require_gpu()
+    mesh, U = _mesh("tiny3")
+    out, t, out_ref, t_ref, halo = _run_both(mesh, U, n_shards, steps=2)
+    assert t == t_ref
+    assert np.array_equal(out, out_ref)
+    if n_shards == 1:
+        assert halo[:2] == (0, 0)
