@@ -65,6 +65,44 @@ NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.200e
                            "limiter_pass": 3.615e9, "final": 1.607e9}
 
 
+# The byte and flop model of the method per stored entry and stage (3D Q1,
+# FP64): B_sched, the canonical five-sweep schedule with P_ij recomputed
+# (170 B per entry; 140 B with FP32 d and l), B_min, every matrix read once and
+# the state in and out (1,060 B per node-stage at 27 entries per row), and the
+# paper's operation count of ~869 flop per entry and stage (Table 3).
+B_SCHED_PER_ENTRY = {"fp64": 170.0, "fp32_mixed": 140.0}
+B_MIN_PER_NODE_STAGE = 1060.0
+F_PAPER_PER_ENTRY = 869.0
+
+
+def byte_model(rate, nodes, nnz, ncu_bytes_per_stage, hbm_peak_gbs, fp_peak_tflops, exec_flop_per_entry, precision):
+    """Measured DRAM bytes per node-stage against B_sched and B_min, and the
+    bound-implied fraction: the achieved node-stage rate over the smaller of
+    the HBM ceiling (peak / B_sched) and the FP ceiling (peak / flops per
+    node-stage), with the paper's flop count and with the kernels' executed
+    one (ncu)."""
+    per_node = nnz / nodes
+    b_sched = B_SCHED_PER_ENTRY[precision] * per_node
+    hbm_ceiling = hbm_peak_gbs * 1e9 / b_sched
+    out = {"entries_per_node": per_node, "b_sched_per_node_stage": b_sched,
+           "b_min_per_node_stage": B_MIN_PER_NODE_STAGE,
+           "ncu_dram_bytes_per_node_stage": None if ncu_bytes_per_stage is None else ncu_bytes_per_stage / nodes,
+           "hbm_ceiling": hbm_ceiling}
+    if ncu_bytes_per_stage is not None:
+        out["ncu_bytes_over_b_sched"] = ncu_bytes_per_stage / nodes / b_sched
+    if fp_peak_tflops:
+        fp_paper = fp_peak_tflops * 1e12 / (F_PAPER_PER_ENTRY * per_node)
+        out["fp_ceiling_paper_flops"] = fp_paper
+        out["bound_implied_frac_paper_flops"] = rate / min(hbm_ceiling, fp_paper)
+        if exec_flop_per_entry:
+            fp_exec = fp_peak_tflops * 1e12 / (exec_flop_per_entry * per_node)
+            out["fp_ceiling_executed_flops"] = fp_exec
+            out["bound_implied_frac_executed_flops"] = rate / min(hbm_ceiling, fp_exec)
+    else:
+        out["bound_implied_frac"] = rate / hbm_ceiling
+    return out
+
+
 # Algorithmic bytes of the FP32-mixed kernels (each array the kernel must read
 # or write once; neighbour gathers counted once per node): bytes per stored
 # entry (slot) and per node.
@@ -222,6 +260,9 @@ def pattern_mixed(stream, args):
             entry["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                                  "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                                  "work": f"{per_slot} B/entry x {s.nnz} + {per_node} B/node x {mesh.n_nodes}"}
+            stage_bytes = sum(NCU_TRAFFIC_BYTES_MIXED.values()) if args.sod_n == 128 else None
+            entry["byte_model"] = byte_model(entry["value"], mesh.n_nodes, s.nnz, stage_bytes, peak, None, None,
+                                             "fp32_mixed")
         out[name] = entry
         s.close()
     # the same mixed stage reading per-entry FP32 arrays instead of the entry table
@@ -917,6 +958,9 @@ def main():
             "kernels_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
             "clocks": clocks,
         }
+        exec_flops = sum(FP64_FLOP_PER_NNZ_EXECUTED.values())
+        line["byte_model"] = byte_model(value, N, nnz, sum(NCU_TRAFFIC_BYTES.values()) if args.m == 120 else None,
+                                        _hbm_peak()[0], peak64, exec_flops, "fp64")
         if not args.no_patterns:
             line["patterns"] = {"fp32_mixed": pattern_mixed(stream, args), "batched": pattern_batched(stream, args),
                                 "adjoint": pattern_adjoint(stream, args),

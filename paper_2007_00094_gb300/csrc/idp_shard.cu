@@ -64,6 +64,7 @@ struct idp_shards {
   };
   std::vector<Link> links;
   int64_t exchanges = 0;  // parity of the receive buffers
+  cudaError_t enqueue_error = cudaSuccess;  // first failed copy or event call of the last step
   unsigned long long** words = nullptr;  // device: each shard's CFL reduction word
   std::vector<void*> allocs;
   bool has_state = false;
@@ -155,6 +156,11 @@ unsigned grid_for(int64_t work) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+// Keeps the first error of an enqueued copy or event call for idp_shards_step.
+void note(idp_shards* sh, cudaError_t e) {
+  if (e != cudaSuccess && sh->enqueue_error == cudaSuccess) sh->enqueue_error = e;
+}
+
 // One exchange over every link: pack(k) enqueues the sender's gather of
 // link k into its send buffer, unpack(k, buf) the receiver's scatter.  The
 // sender copies into the receiver's buffer of this exchange's parity once
@@ -169,17 +175,17 @@ int exchange(idp_shards* sh, Pack&& pack, Unpack&& unpack, Bytes&& bytes) {
     if (b == 0) continue;
     cudaStream_t s = sh->streams[k.src];
     pack(k, s);
-    cudaStreamWaitEvent(s, k.unpacked[par], 0);
-    cudaMemcpyAsync(k.recv[par], k.send, b, cudaMemcpyDeviceToDevice, s);
-    cudaEventRecord(k.copied, s);
+    note(sh, cudaStreamWaitEvent(s, k.unpacked[par], 0));
+    note(sh, cudaMemcpyAsync(k.recv[par], k.send, b, cudaMemcpyDeviceToDevice, s));
+    note(sh, cudaEventRecord(k.copied, s));
     ++launches;
   }
   for (idp_shards::Link& k : sh->links) {
     if (bytes(k) == 0) continue;
     cudaStream_t s = sh->streams[k.dst];
-    cudaStreamWaitEvent(s, k.copied, 0);
+    note(sh, cudaStreamWaitEvent(s, k.copied, 0));
     unpack(k, k.recv[par], s);
-    cudaEventRecord(k.unpacked[par], s);
+    note(sh, cudaEventRecord(k.unpacked[par], s));
     ++launches;
   }
   return launches;
@@ -248,12 +254,12 @@ int sharded_stage(idp_shards* sh, int stage) {
       // tau_n is global: the minimum of every shard's CFL bound, formed on
       // shard 0's stream once every shard has its own
       for (int s = 0; s < S; ++s) {
-        cudaEventRecord(sh->ev_phase[s], sh->streams[s]);
-        cudaStreamWaitEvent(sh->streams[0], sh->ev_phase[s], 0);
+        note(sh, cudaEventRecord(sh->ev_phase[s], sh->streams[s]));
+        note(sh, cudaStreamWaitEvent(sh->streams[0], sh->ev_phase[s], 0));
       }
       k_tau_allreduce<<<1, 1, 0, sh->streams[0]>>>(sh->words, S);
-      cudaEventRecord(sh->ev_tau, sh->streams[0]);
-      for (int s = 1; s < S; ++s) cudaStreamWaitEvent(sh->streams[s], sh->ev_tau, 0);
+      note(sh, cudaEventRecord(sh->ev_tau, sh->streams[0]));
+      for (int s = 1; s < S; ++s) note(sh, cudaStreamWaitEvent(sh->streams[s], sh->ev_tau, 0));
       ++launches;
       if (mixed)
         launches += exchange_nodes<float>(sh, 1, [&](int s) { return sh->ctx[s]->MB.alpha; });
@@ -552,8 +558,11 @@ idp_status idp_shards_step(idp_shards* sh, int n_steps) {
   SH_CUDA(sh, cudaEventRecord(sh->ev_start, sh->stream));
   for (cudaStream_t s : sh->streams) SH_CUDA(sh, cudaStreamWaitEvent(s, sh->ev_start, 0));
   int64_t launches = 0;
+  sh->enqueue_error = cudaSuccess;
   for (int k = 0; k < n_steps; ++k)
     for (int stage = 0; stage < 3; ++stage) launches += sharded_stage(sh, stage);
+  if (sh->enqueue_error != cudaSuccess)
+    return sfail(sh, IDP_ERR_CUDA, std::string("sharded exchange: ") + cudaGetErrorString(sh->enqueue_error));
   for (size_t s = 0; s < sh->streams.size(); ++s) {
     SH_CUDA(sh, cudaEventRecord(sh->ev_end[s], sh->streams[s]));
     SH_CUDA(sh, cudaStreamWaitEvent(sh->stream, sh->ev_end[s], 0));
