@@ -20,6 +20,7 @@ CFL 0.5, directions v_k = xi_k |U^0| (workloads.perturbation_directions, seed
 16).  Only oracle/ and the input generators are used.
 
     python tests/golden/make_adjoint_tangents.py --n 64 --steps 100 --directions 2 --jitter 0.2
+    (or one direction at a time: --direction 1 adds the second to a file holding the first)
 """
 import argparse
 import json
@@ -53,6 +54,9 @@ def main():
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--jitter", type=float, default=0.0, help="node jitter (fraction of h), seed 3; 0 = as configured")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--direction", type=int, default=None,
+                    help="compute only direction k of the seeded set and add it to the existing --out record "
+                         "(which must hold directions 0 .. k-1 of the same workload)")
     args = ap.parse_args()
     torch.set_num_threads(args.threads)
     mesh = W.vortex_mesh(args.n, jitter=args.jitter, seed=3) if args.jitter > 0 else W.vortex_mesh(args.n)
@@ -68,7 +72,16 @@ def main():
            "jitter": args.jitter, "mesh_seed": 3 if args.jitter > 0 else None,
            "n": args.n, "steps": args.steps, "cfl": 0.5, "directions_seed": 16, "J": None, "dJ_dv": [],
            "seconds": []}
-    for k, v in enumerate(dirs):
+    todo = list(enumerate(dirs))
+    if args.direction is not None:
+        with open(out) as fh:
+            prev = json.load(fh)
+        for key in ("n", "steps", "jitter", "mesh_seed", "directions_seed"):
+            assert prev[key] == rec[key], key
+        assert len(prev["dJ_dv"]) == args.direction, "directions must be added in order"
+        rec = prev
+        todo = [(args.direction, dirs[args.direction])]
+    for k, v in todo:
         t0 = time.perf_counter()
         with fwAD.dual_level():
             U = fwAD.make_dual(torch.as_tensor(U0), torch.as_tensor(v))
