@@ -63,14 +63,16 @@ typedef struct {
                                phi_min (1 - r_i) with r_i = (m_i / |Omega|)^(1/2), |Omega| the volume of
                                the node's instance (Sec. 3.9 remark; the formula is project-defined);
                                0 (default): the bounds as Alg. 1 states them */
-  int entry_table;          /* FP32-mixed only.  1 (default): when the mesh has at most 4096 distinct
+  int entry_table;          /* 1 (default): in the FP32-mixed stage, when the mesh has at most 4096 distinct
                                FP32 entries (c_ij, m_ij, |c_ij|, 1/|c_ij|) -- uniform tensor grids --
                                store each stored entry as a 16-bit index into a table of the distinct
                                values instead of six per-entry floats (the matrices of Sec. 3.1,
                                precomputed once as Sec. 3.2 asks), and, when the rows fall into at
                                most 4096 patterns, read column indices and transposed positions from
-                               the patterns (idp_row_pattern_count); 0: per-entry arrays.  Results
-                               are bitwise the same either way. */
+                               the patterns (idp_row_pattern_count; the FP64 stage reads its column
+                               indices, transposed positions and flags from patterns too, on any mesh
+                               whose rows fall into at most 4096); 0: per-entry arrays.  Results are
+                               bitwise the same either way. */
   int adjoint_store_stages; /* 1 (default): idp_adjoint_record also reserves, when the device has the
                                memory (112 B per stored entry and 200 B per node, for each of the
                                3 x checkpoint_every stages of a segment, plus 4 GiB to spare), room
@@ -163,15 +165,17 @@ idp_status idp_mesh_info(idp_ctx* ctx, int64_t* n_nodes, int64_t* nnz);
  * IDP_ERR_STATE before a mesh is uploaded. */
 idp_status idp_entry_table_size(idp_ctx* ctx, int64_t* n_values);
 
-/* Number of row patterns of the FP32-mixed stage (structured grids, with
+/* Number of row patterns of the stage (meshes with grid connectivity, with
  * idp_config.entry_table = 1): rows whose entries have the same column
- * offsets j - i, the same transposed-entry positions, flags and table codes
- * share one pattern, and the kernels read each entry's column and transposed
- * position from the pattern (a small table) instead of per-entry index
- * arrays.  *n_patterns = 0: per-entry index arrays (FP64 context, table off,
- * or more than 4096 patterns, as on renumbered or unstructured meshes).
- * Results are bitwise the same either way.  IDP_ERR_STATE before a mesh is
- * uploaded. */
+ * offsets j - i, the same transposed-entry positions, flags and (FP32-mixed)
+ * table codes share one pattern, and the kernels read each entry's column and
+ * transposed position from the pattern (a small table) instead of per-entry
+ * index arrays.  In FP64 contexts the patterns carry no table code and also
+ * serve jittered meshes, whose connectivity is still the grid's.
+ * *n_patterns = 0: per-entry index arrays (table off, an FP32-mixed context
+ * without an entry table, or more than 4096 patterns, as on renumbered or
+ * unstructured meshes).  Results are bitwise the same either way.
+ * IDP_ERR_STATE before a mesh is uploaded. */
 idp_status idp_row_pattern_count(idp_ctx* ctx, int64_t* n_patterns);
 
 /* Copies the assembled matrices back in the caller's numbering as CSR with

@@ -607,9 +607,15 @@ idp_status upload_row_patterns(idp_ctx* ctx, const std::vector<uint16_t>& code) 
   uint2* dtab;
   idp_status st;
   if ((st = upload(ctx, &drp, rpat)) || (st = upload(ctx, &dtab, tab))) return st;
-  ctx->MG.rpat = drp;
-  ctx->MG.ptab = dtab;
-  ctx->MG.pwidth = width;
+  if (ctx->mixed) {
+    ctx->MG.rpat = drp;
+    ctx->MG.ptab = dtab;
+    ctx->MG.pwidth = width;
+  } else {
+    ctx->G.rpat = drp;
+    ctx->G.ptab = dtab;
+    ctx->G.pwidth = width;
+  }
   ctx->n_row_patterns = (int64_t)index.size();
   return IDP_OK;
 }
@@ -675,6 +681,9 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
   G.lam = lam;
   G.bc = bc;
   G.relax = nullptr;
+  G.rpat = nullptr;
+  G.ptab = nullptr;
+  G.pwidth = 0;
   if (ctx->cfg.relax && (st = upload_relax(ctx, std::vector<int32_t>()))) return st;
 
   ctx->renumbered = ctx->cfg.renumber != 0;
@@ -703,6 +712,10 @@ idp_status upload_matrices(idp_ctx* ctx, const double* inflow_state) {
     // by the kernels: the diagonal bar state U_i reads a zero there
     IDP_CUDA(ctx, cudaMemset(B.d, 0, sizeof(double) * ns));
     IDP_CUDA(ctx, cudaMemset(B.dinv, 0, sizeof(double) * ns));
+    // column, transpose and flags from row patterns where the rows fall into
+    // few of them (the same indices, so bitwise the same results)
+    ctx->n_row_patterns = 0;
+    if (ctx->cfg.entry_table && (st = upload_row_patterns(ctx, std::vector<uint16_t>()))) return st;
   } else {
     // FP32 copies of the entries.  A component of c_ij below 2^-24 of the
     // largest |c| is assembly rounding of a zero (e.g. c_x between nodes of

@@ -112,9 +112,11 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
   const Side si = load_side(U, Q, n, r);
   const double h_i = Q[kQH * n + r];
   const double vxi = Q[kQVx * n + r], vyi = Q[kQVy * n + r], vzi = Q[kQVz * n + r];
+  const uint2* pat = row_pattern64(G, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const uint8_t fl = G.flags[p];
+    const Slot64 sl = slot64(G, pat, r, k, p);
+    const unsigned int fl = sl.fl;
     if (fl & kEntryDiag) {  // (f_i - f_i).c_ii = 0; the diagonal's m_i.c_ii is not used
 #pragma unroll
       for (int f = 0; f < kFields; ++f) dF[f * ns + p] = 0.0;
@@ -122,8 +124,8 @@ __device__ __forceinline__ void row_edge(const DeviceGraph& G, const double* U,
       continue;
     }
     if (!(fl & kEntryUpper)) continue;  // written by the pair's owner
-    const int64_t j = G.col[p];
-    const int64_t pt = G.tpos[p];
+    const int64_t j = sl.j;
+    const int64_t pt = sl.pt;
     const double cx = G.cx[p], cy = G.cy[p], cz = G.cz[p];
     const Side sj = load_side(U, Q, n, j);
     const double h_j = Q[kQH * n + j];
@@ -184,9 +186,11 @@ __device__ __forceinline__ double row_diag(const DeviceGraph& G, const double* U
   double sum = 0.0;
   double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0, b4 = 0.0;
   int64_t pd = base;
+  const uint2* pat = row_pattern64(G, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
+    const Slot64 sl = slot64(G, pat, r, k, p);
+    const int64_t j = sl.j;
     a = fma(Q[kQS * n + j] - s_i, mc[p], a);
     b0 += dF[p];
     b1 += dF[ns + p];
@@ -198,8 +202,8 @@ __device__ __forceinline__ double row_diag(const DeviceGraph& G, const double* U
       continue;
     }
     double v;
-    if (!(G.flags[p] & kEntryUpper)) {  // lower entry: copy from the owning row
-      const int64_t pt = G.tpos[p];
+    if (!(sl.fl & kEntryUpper)) {  // lower entry: copy from the owning row
+      const int64_t pt = sl.pt;
       v = d[pt];
       d[p] = v;
       dinv[p] = dinv[pt];
@@ -348,9 +352,10 @@ __device__ __forceinline__ void row_flux_limit(const DeviceGraph& G, const Stage
   const double inv_mi = G.inv_mi[r];
   const double scale = tau * inv_mi * (double)(len - 1);  // tau / (m_i lambda_i)
   const double scale_i = scale * inv_mi;
+  const uint2* pat = row_pattern64(G, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    const int64_t j = G.col[p];
+    const int64_t j = slot64(G, pat, r, k, p).j;
     if (j == r) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f) P[f * ns + p] = 0.0;
@@ -399,15 +404,17 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
   const double lam = G.lam[r];
   double u[kFields];
   load5(Ucur, n, r, u);
+  const uint2* pat = row_pattern64(G, r);
   {
     // loads of entry k + 1 issued before entry k's accumulation
     bool dg_n = false;
     double la_n = 0.0, lb_n = 0.0, p_n[kFields];
     auto fetch1 = [&](int k) {
       const int64_t q = base + 32 * (int64_t)k;
-      dg_n = G.col[q] == r;
+      const Slot64 sl = slot64(G, pat, r, k, q);
+      dg_n = sl.j == r;
       la_n = lold[q];
-      lb_n = lold[G.tpos[q]];
+      lb_n = lold[sl.pt];
 #pragma unroll
       for (int f = 0; f < kFields; ++f) p_n[f] = P[f * ns + q];
     };
@@ -435,8 +442,9 @@ __device__ __forceinline__ void row_limiter_pass(const DeviceGraph& G, const Sta
   double lk_n = 0.0, p_n[kFields];
   auto fetch = [&](int k) {
     const int64_t q = base + 32 * (int64_t)k;
-    diag_n = G.col[q] == r;
-    lk_n = min_k(lold[q], lold[G.tpos[q]]);
+    const Slot64 sl = slot64(G, pat, r, k, q);
+    diag_n = sl.j == r;
+    lk_n = min_k(lold[q], lold[sl.pt]);
 #pragma unroll
     for (int f = 0; f < kFields; ++f) p_n[f] = P[f * ns + q];
   };
@@ -500,10 +508,12 @@ __device__ __forceinline__ void row_final(const DeviceGraph& G, const StageConfi
   const double lam = G.lam[r];
   double u[kFields];
   load5(Ucur, n, r, u);
+  const uint2* pat = row_pattern64(G, r);
   for (int k = 0; k < len; ++k) {
     const int64_t p = base + 32 * (int64_t)k;
-    if (G.col[p] == r) continue;
-    const double lk = min_k(l[p], l[G.tpos[p]]);
+    const Slot64 sl = slot64(G, pat, r, k, p);
+    if (sl.j == r) continue;
+    const double lk = min_k(l[p], l[sl.pt]);
     const double w = lam * lk;
 #pragma unroll
     for (int f = 0; f < kFields; ++f) u[f] += w * P[f * ns + p];

@@ -37,6 +37,14 @@ struct DeviceGraph {
   const double* lam;
   const int32_t* bc;
   const double* relax;  // per-row bound relaxation r_i, or nullptr (off)
+  // Row patterns of the FP64 stage (nullptr: the col, tpos and flags streams):
+  // rows whose entries k have the same column offset j - r, the same index k'
+  // of the transposed entry in row j and the same flags share a pattern; rpat[r]
+  // is row r's and ptab[rpat[r] * pwidth + k] holds entry k as (j - r, k' |
+  // flags << 8).  Built at upload when the mesh has at most 4096 patterns.
+  const uint16_t* rpat;
+  const uint2* ptab;
+  int pwidth;
   // Row order (idp_config.renumber): caller node of each row and row of each
   // caller node, or nullptr for the caller's order.  Read where a result
   // depends on the order of rows (the adjoint's fixed-order sum of the tau
@@ -56,6 +64,33 @@ struct DeviceGraph {
 };
 
 __device__ __forceinline__ int instance_of(const DeviceGraph& G, int64_t r) { return G.inst ? G.inst[r] : 0; }
+
+// Column, transposed slot and flags of entry k (slot p) of row r, from the
+// row's pattern or from the per-slot streams.
+struct Slot64 {
+  int64_t j;
+  int64_t pt;
+  unsigned int fl;
+};
+
+__device__ __forceinline__ const uint2* row_pattern64(const DeviceGraph& G, int64_t r) {
+  return G.rpat ? G.ptab + (int64_t)G.rpat[r] * G.pwidth : nullptr;
+}
+
+__device__ __forceinline__ Slot64 slot64(const DeviceGraph& G, const uint2* pat, int64_t r, int k, int64_t p) {
+  Slot64 e;
+  if (pat) {
+    const uint2 w = __ldg(&pat[k]);
+    e.j = r + (int32_t)w.x;
+    e.pt = (int64_t)G.slice_ptr[e.j >> 5] + (e.j & 31) + 32 * (int64_t)(w.y & 0xffu);
+    e.fl = (w.y >> 8) & 0xffu;
+  } else {
+    e.j = G.col[p];
+    e.pt = G.tpos[p];
+    e.fl = G.flags[p];
+  }
+  return e;
+}
 
 // Rows of the per-step kernels of Steps 2-6: [row0, row1), launched from the
 // start of row0's slice so that a warp's rows share one slice.

@@ -470,3 +470,27 @@ def test_relaxed_bounds_parity(name, n_threads):
     s.step(1)
     s.synchronize()
     assert rel_field_err_l2(s.get_state(), ref3).max() <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["ffs10", "wallbox_jitter", "vortex17", "ffs2d_10"])
+def test_fp64_row_patterns_give_bitwise_the_same_result(name):
+    """The FP64 stage reads column, transposed slot and flags from row
+    patterns (jittered meshes too: their connectivity is the grid's); with
+    the patterns off (entry_table = 0) it reads the per-slot streams.  The
+    indices are the same, so are the results, bitwise, under the per-step
+    and the persistent schedule."""
+    mesh, U = _mesh(name)
+    out, pats = {}, {}
+    for table in (1, 0):
+        for persistent in (False, True):
+            s = _solver(mesh, entry_table=table)
+            s.set_schedule(64, False, persistent)
+            pats[table] = s.row_pattern_count()
+            s.init_state(U)
+            s.step(3)
+            s.synchronize()
+            out[(table, persistent)] = s.get_state()
+            s.close()
+    assert pats[1] > 0 and pats[0] == 0
+    for key, v in out.items():
+        np.testing.assert_array_equal(v, out[(0, False)], err_msg=str(key))
