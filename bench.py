@@ -48,8 +48,8 @@ FP64_FLOP_PER_NNZ_EXECUTED = {"node": 3.5, "edge": 45.3, "diag": 11.2, "low_orde
                               "limiter_pass": 14.6, "final": 10.6}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, % of active cycles) of
 # the same capture: the pipe also issues compares, conversions and min/max.
-FP64_PIPE_BUSY_NCU = {"node": 0.856, "edge": 0.847, "diag": 0.756, "low_order": 0.892, "flux_limit": 0.872,
-                      "limiter_pass": 0.791, "final": 0.671}
+FP64_PIPE_BUSY_NCU = {"node": 0.855, "edge": 0.854, "diag": 0.701, "low_order": 0.891, "flux_limit": 0.875,
+                      "limiter_pass": 0.821, "final": 0.848}
 # FP64 peak from the unit counts and the maximum SM clock: 152 SMs x 2 FP64
 # FMA/clk x 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s).  The roofline uses the
 # rate the library's own FMA-stream probe measures in the same run
@@ -59,10 +59,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # one pass, no replay) on the workloads of this file at full size: the step
 # channel at h = 1/120 (FP64) and the 128^3 Sod cube (FP32-mixed), one stage
 # after three warm-up steps (profiles/ holds the launch lists).
-NCU_TRAFFIC_BYTES = {"node": 0.225e9, "edge": 5.137e9, "diag": 4.469e9, "low_order": 4.073e9,
-                     "flux_limit": 4.360e9, "limiter_pass": 8.011e9, "final": 3.698e9}
-NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.200e9, "flux_limit": 1.820e9,
-                           "limiter_pass": 3.615e9, "final": 1.607e9}
+NCU_TRAFFIC_BYTES = {"node": 0.225e9, "edge": 4.843e9, "diag": 4.018e9, "low_order": 4.073e9,
+                     "flux_limit": 4.122e9, "limiter_pass": 6.944e9, "final": 3.210e9}
+NCU_TRAFFIC_BYTES_MIXED = {"node": 0.138e9, "edge": 1.729e9, "low_order": 2.198e9, "flux_limit": 1.820e9,
+                           "limiter_pass": 3.617e9, "final": 1.608e9}
 
 
 # The byte and flop model of the method per stored entry and stage (3D Q1,
